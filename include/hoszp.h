@@ -1,0 +1,166 @@
+/*
+ * hoszp.h — C ABI of libhoszp, a GB300 (sm_103a) implementation of the HoSZp
+ * homomorphic error-bounded lossy compressor (Agarwal et al., arXiv 2408.11971).
+ *
+ * The library compresses float32 fields into a blockwise stream (quantization,
+ * in-block 1-D Lorenzo, blockwise fixed-length bit-plane encoding; Sec. IV-A,
+ * Fig. 2) and runs the paper's homomorphic operators directly on that stream
+ * (Sec. IV-B workflows 1-3, Sec. V, Table 2): negation, scalar addition, scalar
+ * multiplication, element-wise addition of two streams, mean and variance.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every data pointer named d_* is DEVICE memory owned by the caller (for example a
+ *    torch tensor's data_ptr()). The library never frees caller memory.
+ *  - Calls are asynchronous on `stream`. Argument errors the host can see
+ *    (null pointers, zero capacity, bad modes, sizes) are returned immediately
+ *    as a negative hoszp_status and nothing is launched.
+ *  - Errors only the device can see (non-finite input, quantization range,
+ *    overflow, corrupt or mismatched streams, output capacity, spin-wait
+ *    timeouts) are recorded in the context's device status word; the output
+ *    is then undefined. hoszp_get_status() synchronizes and returns/clears it.
+ *  - Output sizes of stream-producing calls are written to the device word
+ *    *d_out_bytes (uint64), so no call needs a host round trip.
+ *  - One context serves one stream at a time: its workspace is reused by every
+ *    call, so two calls on one context must not overlap on the device.
+ *
+ * Stream format ("R-FMT", little-endian; section order of Fig. 3):
+ *   [header 64 B][rate u8 x nb][pad16][outlier i32 x nb][pad16]
+ *   [sign u64 x nnc][plane u64 x R]
+ *   nb  = ceil(n/64) blocks of L = 64 consecutive values (last block short),
+ *   rate_b = bit length of max |delta| in block b (0 = constant block, which
+ *            stores no sign word and no planes; Sec. IV-A step 3),
+ *   outlier_b = quantized value of the first element of block b (Sec. IV-A step 2),
+ *   sign word: bit i = 1 iff delta_i < 0 (Sec. IV-A, sign array),
+ *   plane p (p < rate_b): bit i = bit p of |delta_i|, i = 0..63, delta_0 := 0.
+ *   nnc = number of non-constant blocks, R = sum of rates.
+ */
+#ifndef HOSZP_H
+#define HOSZP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* hoszp_stream_t; /* same object as cudaStream_t */
+
+typedef enum {
+  HOSZP_OK = 0,
+  HOSZP_ERR_ARG = -1,       /* bad argument (host check) */
+  HOSZP_ERR_CAPACITY = -2,  /* output buffer too small */
+  HOSZP_ERR_FORMAT = -3,    /* stream header/size corrupt */
+  HOSZP_ERR_MISMATCH = -4,  /* two streams differ in n, block length or eps */
+  HOSZP_ERR_RANGE = -5,     /* |q| beyond the quantizer's exact range */
+  HOSZP_ERR_OVERFLOW = -6,  /* an operator's result leaves the integer range */
+  HOSZP_ERR_NONFINITE = -7, /* NaN or Inf in the input field */
+  HOSZP_ERR_TIMEOUT = -8,   /* a bounded device spin-wait gave up */
+  HOSZP_ERR_CUDA = -9       /* a CUDA runtime call failed */
+} hoszp_status;
+
+enum { HOSZP_EB_ABS = 0, HOSZP_EB_REL = 1 };
+
+/* Format constants. */
+#define HOSZP_MAGIC 0x505A5348u       /* bytes 'H','S','Z','P' */
+#define HOSZP_VERSION 1u
+#define HOSZP_BLOCK 64u               /* L: values per block (Table 6 gives 64) */
+#define HOSZP_HEADER_BYTES 64u
+#define HOSZP_QMAX_COMPRESS 8388606   /* 2^23-2: exact range of the quantizer */
+#define HOSZP_QLIM 1073741823         /* 2^30-1: integer range of every stream */
+
+/* Header, 64 bytes at offset 0 of every stream. */
+typedef struct hoszp_header {
+  uint32_t magic;     /* HOSZP_MAGIC */
+  uint16_t version;   /* HOSZP_VERSION */
+  uint8_t dtype;      /* 0 = float32 */
+  uint8_t ndims;      /* 1..3 */
+  uint32_t dims[3];   /* informational shape, row-major, product == n */
+  float eps_q;        /* bound used by the quantizer: largest float <= eps */
+  uint64_t n;         /* number of values */
+  double eps;         /* absolute error bound the caller asked for */
+  uint64_t nnc;       /* non-constant blocks */
+  uint64_t R;         /* sum of block rates = number of plane words */
+  uint32_t qbound;    /* upper bound on |q| over the stream (<= HOSZP_QLIM) */
+  uint32_t block;     /* HOSZP_BLOCK */
+} hoszp_header;
+
+typedef struct hoszp_ctx hoszp_ctx;
+
+/* Create a context on CUDA device `device`: a device status word and a workspace
+ * that grows on demand (the only memory the library allocates). Returns
+ * HOSZP_OK and *ctx, or HOSZP_ERR_ARG / HOSZP_ERR_CUDA. */
+int hoszp_ctx_create(hoszp_ctx** ctx, int device);
+/* Free the context and its workspace. Synchronizes the device. NULL is a no-op. */
+void hoszp_ctx_destroy(hoszp_ctx* ctx);
+/* Pre-size the workspace for fields of up to n values, so that later calls on
+ * that size allocate nothing. HOSZP_ERR_CUDA if the allocation fails. */
+int hoszp_ctx_reserve(hoszp_ctx* ctx, uint64_t n);
+/* Synchronize the device, return the first device-side error recorded since
+ * the last call (HOSZP_OK if none) in *status, and clear it. */
+int hoszp_get_status(hoszp_ctx* ctx, int* status);
+
+/* Worst-case stream size for n values: header + rates + outliers + one sign
+ * word and 31 planes per block (section sizes of Fig. 3 at maximum rate). */
+size_t hoszp_compress_bound(uint64_t n);
+
+/* Compression, Sec. IV-A (Eq. 3 quantization, Eq. 4 Lorenzo, BF encoding).
+ * d_x: n float32 values (device). dims/ndims: informational shape (1..3 dims,
+ * product == n). eb: error bound; eb_mode HOSZP_EB_ABS uses it as eps,
+ * HOSZP_EB_REL uses eps = eb * (max - min) of the field (a range pass on the
+ * device). Quantizer: q = floor((x + e) / (2e)) evaluated exactly, e = eps_q.
+ * Every reconstructed value then satisfies |x - x'| <= eps + ulp(x')/2.
+ * Output: stream at d_out (capacity cap bytes), its size in *d_out_bytes.
+ * Device errors: NONFINITE, RANGE (|q| > HOSZP_QMAX_COMPRESS), CAPACITY. */
+int hoszp_compress(hoszp_ctx* ctx, const float* d_x, uint64_t n, const uint32_t dims[3],
+                   int ndims, double eb, int eb_mode, void* d_out, size_t cap,
+                   uint64_t* d_out_bytes, hoszp_stream_t stream);
+
+/* Full decompression (inverse of every step, Fig. 2 caption): decode the bit
+ * planes, invert the Lorenzo prediction, x' = float(q) * (2 eps_q).
+ * d_c: stream of c_bytes bytes; d_x: room for n floats (n must equal the header's). */
+int hoszp_decompress(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, float* d_x, uint64_t n,
+                     hoszp_stream_t stream);
+
+/* Negation, Sec. V-A "Negation", workflow 1: every sign word is bit-inverted
+ * (all 64 bits) and every outlier negated; rates and planes are copied.
+ * d_out may equal d_c (in place; then only outliers and signs are touched). */
+int hoszp_negate(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, void* d_out, size_t cap,
+                 uint64_t* d_out_bytes, hoszp_stream_t stream);
+
+/* Scalar addition, Sec. V-A "Scalar Addition", workflow 1: rho_s = Eq. 3
+ * quantization of s; every outlier becomes O + rho_s. In place allowed.
+ * Errors: RANGE if |rho_s| > HOSZP_QLIM (host), OVERFLOW if qbound + |rho_s|
+ * exceeds HOSZP_QLIM (device). */
+int hoszp_add_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
+                     size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
+
+/* Scalar multiplication, Sec. V-A "Scalar Multiplication", workflow 3: decode
+ * to q, q' = floor(2 eps_q * q * rho_s + 1/2) (Eq. 3 applied to the product of
+ * the dequantized values), then Lorenzo + BF re-encode. Output stream is
+ * canonical. Errors: RANGE (rho_s), OVERFLOW (|q'| > HOSZP_QLIM), CAPACITY. */
+int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
+                     size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
+
+/* Element-wise addition, Sec. V-C, workflow 2: outliers add, signed deltas add,
+ * blockwise fixed-length re-encode (no Lorenzo inverse). Streams must agree in
+ * n, block length and eps_q (MISMATCH otherwise). OVERFLOW if the sum of the
+ * two qbounds exceeds HOSZP_QLIM. Output stream is canonical. */
+int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
+              void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
+
+/* Mean, Sec. V-B: S1 = sum of q (exact integer), mean = (S1 / n) * 2 eps_q in
+ * FP64, written to the device double *d_result. n == 0 -> HOSZP_ERR_ARG. */
+int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
+               hoszp_stream_t stream);
+
+/* Population variance, Sec. V-B: (2 eps_q)^2 * (n*S2 - S1^2) / n^2 with S1, S2
+ * exact integer sums of q and q^2, finished in FP64 into *d_result. */
+int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
+              hoszp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOSZP_H */
