@@ -1,0 +1,304 @@
+"""ctypes binding of libhoszp (see include/hoszp.h for the C ABI)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(PKG, "libhoszp.so")
+
+STATUS = {
+    0: "OK", -1: "ARG", -2: "CAPACITY", -3: "FORMAT", -4: "MISMATCH", -5: "RANGE",
+    -6: "OVERFLOW", -7: "NONFINITE", -8: "TIMEOUT", -9: "CUDA",
+}
+HEADER_BYTES = 64
+EB_MODES = {"abs": 0, "rel": 1}
+
+
+class HoszpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"hoszp {what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libhoszp.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"libhoszp.so not found at {_LIB_PATH}; build it with "
+                "`python -m paper_2408_11971_gb300.build` (needs nvcc, sm_103a)")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, U64, SZ, I, D = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int,
+                            ctypes.c_double)
+        sig = {
+            "hoszp_ctx_create": (I, [ctypes.POINTER(P), I]),
+            "hoszp_ctx_destroy": (None, [P]),
+            "hoszp_ctx_reserve": (I, [P, U64]),
+            "hoszp_get_status": (I, [P, ctypes.POINTER(I)]),
+            "hoszp_compress_bound": (SZ, [U64]),
+            "hoszp_compress": (I, [P, P, U64, P, I, D, I, P, SZ, P, P]),
+            "hoszp_decompress": (I, [P, P, SZ, P, U64, P]),
+            "hoszp_negate": (I, [P, P, SZ, P, SZ, P, P]),
+            "hoszp_add_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
+            "hoszp_mul_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
+            "hoszp_add": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
+            "hoszp_mean": (I, [P, P, SZ, P, P]),
+            "hoszp_var": (I, [P, P, SZ, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+class Context:
+    """Owns a hoszp_ctx (device status word + workspace) on one CUDA device.
+    One context serves one stream at a time."""
+
+    def __init__(self, device: int = 0):
+        lib = load_library()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        rc = lib.hoszp_ctx_create(ctypes.byref(h), self.device)
+        if rc != 0:
+            raise HoszpError(rc, "ctx_create")
+        self.handle = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.hoszp_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, n: int):
+        _check(self._lib.hoszp_ctx_reserve(self.handle, int(n)), "ctx_reserve")
+
+    def status(self) -> int:
+        st = ctypes.c_int(0)
+        _check(self._lib.hoszp_get_status(self.handle, ctypes.byref(st)), "get_status")
+        return st.value
+
+    def check(self, what: str = "device"):
+        st = self.status()
+        if st != 0:
+            raise HoszpError(st, what)
+
+
+_contexts: dict = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    torch = _torch()
+    if device is None:
+        device = torch.cuda.current_device()
+    ctx = _contexts.get(device)
+    if ctx is None:
+        ctx = _contexts[device] = Context(device)
+    return ctx
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise HoszpError(rc, what)
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_tensor(c):
+    torch = _torch()
+    if not isinstance(c, torch.Tensor) or not c.is_cuda or c.dtype != torch.uint8:
+        raise TypeError("a compressed stream is a CUDA uint8 tensor")
+    return c.contiguous()
+
+
+def _ctx(ctx, t):
+    return ctx if ctx is not None else default_context(t.device.index)
+
+
+def _finish(ctx, out, size_t, sync, check, what):
+    if not sync:
+        return out, size_t
+    if check:
+        ctx.check(what)
+    n = int(size_t.item())
+    return out[:n]
+
+
+def compress_bound(n: int) -> int:
+    return int(load_library().hoszp_compress_bound(int(n)))
+
+
+def header(c) -> dict:
+    """Header fields of a stream (reads 64 bytes to the host)."""
+    import numpy as np
+
+    h = c[:HEADER_BYTES].cpu().numpy().tobytes()
+    return dict(
+        magic=int.from_bytes(h[0:4], "little"), ndims=h[7],
+        dims=[int.from_bytes(h[8 + 4 * i:12 + 4 * i], "little") for i in range(3)],
+        eps_q=float(np.frombuffer(h[20:24], np.float32)[0]),
+        n=int.from_bytes(h[24:32], "little"), eps=float(np.frombuffer(h[32:40], np.float64)[0]),
+        nnc=int.from_bytes(h[40:48], "little"), R=int.from_bytes(h[48:56], "little"),
+        qbound=int.from_bytes(h[56:60], "little"))
+
+
+def compress(x, eb: float, mode: str = "abs", dims=None, out=None, out_bytes=None, stream=None,
+             ctx: Context | None = None, sync: bool = True, check: bool = True):
+    """Compress a float32 CUDA tensor (Sec. IV-A). Returns the stream as a uint8
+    tensor (sync=True) or (buffer, size tensor) without synchronizing."""
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32:
+        raise TypeError("compress expects a CUDA float32 tensor")
+    x = x.contiguous()
+    ctx = _ctx(ctx, x)
+    shape = tuple(x.shape) if dims is None else tuple(dims)
+    if len(shape) == 0:
+        shape = (1,)
+    if len(shape) > 3:
+        shape = (x.numel(),)
+    d3 = (ctypes.c_uint32 * 3)(*(list(shape) + [0] * (3 - len(shape))))
+    n = x.numel()
+    cap = compress_bound(n)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    if out_bytes is None:
+        out_bytes = torch.zeros(1, dtype=torch.int64, device=x.device)
+    rc = load_library().hoszp_compress(ctx.handle, _dev_ptr(x), n, d3, len(shape), float(eb),
+                                       EB_MODES[mode], _dev_ptr(out), out.numel(),
+                                       _dev_ptr(out_bytes), _stream_ptr(stream))
+    _check(rc, "compress")
+    return _finish(ctx, out, out_bytes, sync, check, "compress")
+
+
+def decompress(c, n: int | None = None, out=None, stream=None, ctx: Context | None = None,
+               check: bool = True):
+    torch = _torch()
+    c = _stream_tensor(c)
+    ctx = _ctx(ctx, c)
+    if n is None:
+        n = header(c)["n"]
+    if out is None:
+        out = torch.empty(max(int(n), 0), dtype=torch.float32, device=c.device)
+    rc = load_library().hoszp_decompress(ctx.handle, _dev_ptr(c), c.numel(), _dev_ptr(out), int(n),
+                                         _stream_ptr(stream))
+    _check(rc, "decompress")
+    if check:
+        ctx.check("decompress")
+    return out
+
+
+def _unary(fn, what, c, extra, out, out_bytes, inplace, stream, ctx, sync, check):
+    torch = _torch()
+    c = _stream_tensor(c)
+    ctx = _ctx(ctx, c)
+    if inplace:
+        out = c
+    elif out is None:
+        out = torch.empty(c.numel() if what != "mul_scalar" else max(
+            c.numel(), compress_bound(header(c)["n"])), dtype=torch.uint8, device=c.device)
+    if out_bytes is None:
+        out_bytes = torch.zeros(1, dtype=torch.int64, device=c.device)
+    rc = fn(ctx.handle, _dev_ptr(c), c.numel(), *extra, _dev_ptr(out), out.numel(),
+            _dev_ptr(out_bytes), _stream_ptr(stream))
+    _check(rc, what)
+    return _finish(ctx, out, out_bytes, sync, check, what)
+
+
+def negate(c, out=None, out_bytes=None, inplace: bool = False, stream=None, ctx=None,
+           sync: bool = True, check: bool = True):
+    """Negation in fully compressed space (Sec. V-A)."""
+    return _unary(load_library().hoszp_negate, "negate", c, (), out, out_bytes, inplace, stream,
+                  ctx, sync, check)
+
+
+def add_scalar(c, s: float, out=None, out_bytes=None, inplace: bool = False, stream=None,
+               ctx=None, sync: bool = True, check: bool = True):
+    """Scalar addition in fully compressed space (Sec. V-A)."""
+    return _unary(load_library().hoszp_add_scalar, "add_scalar", c, (ctypes.c_double(s),), out,
+                  out_bytes, inplace, stream, ctx, sync, check)
+
+
+def mul_scalar(c, s: float, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
+               check: bool = True):
+    """Scalar multiplication through the quantized integers (Sec. V-A)."""
+    return _unary(load_library().hoszp_mul_scalar, "mul_scalar", c, (ctypes.c_double(s),), out,
+                  out_bytes, False, stream, ctx, sync, check)
+
+
+def add(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
+        check: bool = True):
+    """Element-wise addition of two streams (Sec. V-C)."""
+    torch = _torch()
+    a = _stream_tensor(a)
+    b = _stream_tensor(b)
+    ctx = _ctx(ctx, a)
+    if out is None:
+        out = torch.empty(compress_bound(header(a)["n"]), dtype=torch.uint8, device=a.device)
+    if out_bytes is None:
+        out_bytes = torch.zeros(1, dtype=torch.int64, device=a.device)
+    rc = load_library().hoszp_add(ctx.handle, _dev_ptr(a), a.numel(), _dev_ptr(b), b.numel(),
+                                  _dev_ptr(out), out.numel(), _dev_ptr(out_bytes),
+                                  _stream_ptr(stream))
+    _check(rc, "add")
+    return _finish(ctx, out, out_bytes, sync, check, "add")
+
+
+def _moment(fn, what, c, out, stream, ctx, sync, check):
+    torch = _torch()
+    c = _stream_tensor(c)
+    ctx = _ctx(ctx, c)
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=c.device)
+    rc = fn(ctx.handle, _dev_ptr(c), c.numel(), _dev_ptr(out), _stream_ptr(stream))
+    _check(rc, what)
+    if not sync:
+        return out
+    if check:
+        ctx.check(what)
+    return float(out.item())
+
+
+def mean(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
+    """Mean from the quantized integers (Sec. V-B)."""
+    return _moment(load_library().hoszp_mean, "mean", c, out, stream, ctx, sync, check)
+
+
+def var(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
+    """Population variance from exact integer sums (Sec. V-B)."""
+    return _moment(load_library().hoszp_var, "var", c, out, stream, ctx, sync, check)

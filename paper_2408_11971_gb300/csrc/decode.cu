@@ -1,0 +1,239 @@
+// decode.cu — full decompression (inverse of every pipeline step, Fig. 2) and
+// the univariate reductions mean and variance (Sec. V-B, workflow 3), which
+// sum the quantized integers exactly and finish in FP64.
+#include <cfloat>
+
+#include "hz_decode.cuh"
+#include "hz_kernels.cuh"
+
+namespace hz {
+
+// ---------------------------------------------------------------- decompression
+__global__ void __launch_bounds__(CTA) k_decompress(const uint8_t* __restrict__ c, uint64_t c_bytes,
+                                                    float* __restrict__ x, uint64_t n_expect,
+                                                    Ws ws) {
+  __shared__ InTile s;
+  __shared__ unsigned int s_tile;
+  __shared__ unsigned long long s_epoch;
+  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  const Info h = parse_header(c, c_bytes);
+  int bad = 0;
+  uint64_t ntiles = 0;
+  if (!h.ok) bad = HOSZP_ERR_FORMAT;
+  else if (h.n != n_expect) bad = HOSZP_ERR_MISMATCH;
+  else ntiles = ntiles_of(h.nb);
+  const float e2 = 2.0f * h.eps_q;
+  const bool small = h.qbound < (1u << 22);
+  if (tid == 0) s_epoch = launch_epoch(ws);
+  __syncthreads();
+  const unsigned long long epoch = s_epoch;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    in_tile_begin(c, h, tile, &s, ws.desc[0], epoch, ws.status, 0, bad);
+    __syncthreads();
+    if (tile == ntiles - 1 && tid == 0 &&
+        (s.pre[0] + s.ts.agg_nc != h.nnc || s.pre[1] + s.ts.agg_r != h.R))
+      bad = HOSZP_ERR_FORMAT;
+    const BlockRef br = block_ref(c, h, tile, &s, g, j, bad);
+    const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+    int d[8], q[8];
+    octet_deltas(br, kmax, j, d);
+    octet_values(br, d, j, q);
+    const uint64_t i0 = (tile * TILE + g) * L + 8 * j;
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+    if (i0 + 8 <= h.n) {
+      float4* o = reinterpret_cast<float4*>(x + i0);
+      o[0] = make_float4(v[0], v[1], v[2], v[3]);
+      o[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; t++)
+        if (i0 + t < h.n) x[i0 + t] = v[t];
+    }
+    __syncthreads();
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
+}
+
+cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
+                              uint64_t n, Ws ws) {
+  k_decompress<<<persistent_grid(k_decompress, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, x, n, ws);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- mean / variance
+// 128-bit helpers for the exact sums.
+struct U128 {
+  unsigned long long lo, hi;
+};
+__device__ __forceinline__ void add_u64(U128& a, unsigned long long v) {
+  a.lo += v;
+  a.hi += (a.lo < v) ? 1ull : 0ull;
+}
+__device__ __forceinline__ void add_u128(U128& a, const U128& b) {
+  a.lo += b.lo;
+  a.hi += b.hi + ((a.lo < b.lo) ? 1ull : 0ull);
+}
+
+// exact unsigned 256-bit product helpers for the variance numerator
+struct U256 {
+  unsigned long long w[4];
+};
+__device__ __forceinline__ U256 mul_u128_u128(unsigned __int128 a, unsigned __int128 b) {
+  unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
+  unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
+  unsigned __int128 p00 = (unsigned __int128)a0 * b0, p01 = (unsigned __int128)a0 * b1;
+  unsigned __int128 p10 = (unsigned __int128)a1 * b0, p11 = (unsigned __int128)a1 * b1;
+  U256 r;
+  r.w[0] = (unsigned long long)p00;
+  unsigned __int128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
+  r.w[1] = (unsigned long long)mid;
+  unsigned __int128 hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (unsigned long long)p11;
+  r.w[2] = (unsigned long long)hi;
+  r.w[3] = (unsigned long long)(hi >> 64) + (unsigned long long)(p11 >> 64);
+  return r;
+}
+__device__ __forceinline__ U256 sub_u256(const U256& a, const U256& b) {  // a >= b
+  U256 r;
+  unsigned long long borrow = 0;
+  for (int i = 0; i < 4; i++) {
+    unsigned long long bi = b.w[i] + borrow;
+    unsigned long long nb = (bi < borrow) || (a.w[i] < bi) ? 1ull : 0ull;
+    r.w[i] = a.w[i] - bi;
+    borrow = nb;
+  }
+  return r;
+}
+__device__ __forceinline__ double u256_to_double(const U256& a) {
+  const double two64 = 18446744073709551616.0;
+  double d = (double)a.w[3];
+  d = d * two64 + (double)a.w[2];
+  d = d * two64 + (double)a.w[1];
+  d = d * two64 + (double)a.w[0];
+  return d;
+}
+
+template <bool VAR>
+__global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, uint64_t c_bytes,
+                                                 double* result, Ws ws) {
+  __shared__ InTile s;
+  __shared__ unsigned int s_tile;
+  __shared__ unsigned long long s_epoch;
+  __shared__ long long s_s1[CTA / 32];
+  __shared__ U128 s_s2[CTA / 32];
+  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  const Info h = parse_header(c, c_bytes);
+  int bad = 0;
+  uint64_t ntiles = 0;
+  if (!h.ok) bad = HOSZP_ERR_FORMAT;
+  else ntiles = ntiles_of(h.nb);
+  if (tid == 0) s_epoch = launch_epoch(ws);
+  __syncthreads();
+  const unsigned long long epoch = s_epoch;
+  long long s1 = 0;  // per thread: |q| <= 2^30, far fewer than 2^32 values per thread
+  U128 s2 = {0, 0};
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    in_tile_begin(c, h, tile, &s, ws.desc[0], epoch, ws.status, 0, bad);
+    __syncthreads();
+    if (tile == ntiles - 1 && tid == 0 &&
+        (s.pre[0] + s.ts.agg_nc != h.nnc || s.pre[1] + s.ts.agg_r != h.R))
+      bad = HOSZP_ERR_FORMAT;
+    const BlockRef br = block_ref(c, h, tile, &s, g, j, bad);
+    const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+    int d[8], q[8];
+    octet_deltas(br, kmax, j, d);
+    octet_values(br, d, j, q);
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      if (8 * j + t < br.len) {
+        s1 += q[t];
+        if (VAR) add_u64(s2, (unsigned long long)((long long)q[t] * (long long)q[t]));
+      }
+    }
+    __syncthreads();
+  }
+  // CTA reduction -> per-CTA partial
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    if (VAR) {
+      U128 t;
+      t.lo = __shfl_xor_sync(0xffffffffu, s2.lo, o);
+      t.hi = __shfl_xor_sync(0xffffffffu, s2.hi, o);
+      add_u128(s2, t);
+    }
+  }
+  if ((tid & 31) == 0) {
+    s_s1[tid >> 5] = s1;
+    s_s2[tid >> 5] = s2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __int128 t1 = 0;
+    U128 t2 = {0, 0};
+    for (int w = 0; w < CTA / 32; w++) {
+      t1 += s_s1[w];
+      add_u128(t2, s_s2[w]);
+    }
+    Partial p;
+    p.s1_lo = (long long)(unsigned long long)t1;
+    p.s1_hi = (long long)(t1 >> 64);
+    p.s2_lo = t2.lo;
+    p.s2_hi = t2.hi;
+    ws.partials[blockIdx.x] = p;
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && tid == 0) {
+    __int128 S1 = 0;
+    U128 S2 = {0, 0};
+    for (unsigned int b = 0; b < gridDim.x; b++) {
+      const Partial p = ws.partials[b];
+      S1 += ((__int128)p.s1_hi << 64) | (unsigned long long)p.s1_lo;
+      U128 v = {p.s2_lo, p.s2_hi};
+      add_u128(S2, v);
+    }
+    double res = 0.0;
+    if (h.ok && h.n == 0) {
+      set_status(ws.status, HOSZP_ERR_ARG);
+    } else if (h.ok) {
+      const double e2 = 2.0 * (double)h.eps_q;
+      if (!VAR) {
+        const double s1d = (double)(long long)(S1 >> 64) * 18446744073709551616.0 +
+                           (double)(unsigned long long)S1;
+        res = (s1d / (double)h.n) * e2;
+      } else {
+        // n S2 - S1^2 >= 0 exactly (Cauchy-Schwarz), in 256-bit integers
+        unsigned __int128 s2u = ((unsigned __int128)S2.hi << 64) | S2.lo;
+        unsigned __int128 a1 = (unsigned __int128)(S1 < 0 ? -S1 : S1);
+        U256 nS2 = mul_u128_u128(s2u, (unsigned __int128)h.n);
+        U256 S1sq = mul_u128_u128(a1, a1);
+        U256 D = sub_u256(nS2, S1sq);
+        const double dn = (double)h.n;
+        res = (u256_to_double(D) / (dn * dn)) * (e2 * e2);
+      }
+    }
+    *result = res;
+    launch_reset(ws);
+  }
+}
+
+cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
+                           bool variance, Ws ws) {
+  if (variance)
+    k_moments<true><<<persistent_grid(k_moments<true>, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, result, ws);
+  else
+    k_moments<false><<<persistent_grid(k_moments<false>, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, result, ws);
+  return cudaGetLastError();
+}
+
+}  // namespace hz

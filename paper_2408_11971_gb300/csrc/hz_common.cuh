@@ -1,0 +1,478 @@
+// hz_common.cuh — device building blocks shared by the libhoszp kernels.
+//
+// Thread layout used by every codec kernel ("octet" layout): a CTA of
+// HZ_CTA = 512 threads covers one tile of HZ_TILE = 64 blocks; thread tid owns
+// block g = tid / 8 of the tile and, inside it, the 8 consecutive positions
+// 8j..8j+7 with j = tid % 8. Eight lanes of a warp therefore hold one 64-value
+// block; a warp holds 4 blocks. A block's bit planes (Sec. IV-A step 3) are
+// 64-bit words whose byte j covers exactly lane j's positions, so planes move
+// between memory and registers as whole words and are redistributed with an
+// 8x8 byte transpose across the 8 lanes (3 shuffles) and an 8x8 bit transpose
+// inside each lane (3 delta swaps).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hoszp.h"
+
+#define HZ_HD __host__ __device__ __forceinline__
+
+namespace hz {
+
+constexpr int L = 64;        // values per block (Table 6)
+constexpr int TILE = 64;     // blocks per tile
+constexpr int CTA = 512;     // threads per CTA (8 per block)
+constexpr int TILE_VALUES = TILE * L;
+constexpr int MAX_RATE = 31;
+constexpr int NCHAIN = 3;    // look-back chains per launch (add uses 2 inputs + 1 output)
+
+// ---------------------------------------------------------------- stream layout (Fig. 3)
+HZ_HD uint64_t align16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
+HZ_HD uint64_t nblocks(uint64_t n) { return (n + L - 1) / L; }
+HZ_HD uint64_t off_outlier(uint64_t nb) { return HOSZP_HEADER_BYTES + align16(nb); }
+HZ_HD uint64_t off_sign(uint64_t nb) { return off_outlier(nb) + align16(4 * nb); }
+HZ_HD uint64_t off_plane(uint64_t nb, uint64_t nnc) { return off_sign(nb) + 8 * nnc; }
+HZ_HD uint64_t stream_bytes(uint64_t nb, uint64_t nnc, uint64_t R) {
+  return off_plane(nb, nnc) + 8 * R;
+}
+HZ_HD uint64_t ntiles_of(uint64_t nb) { return (nb + TILE - 1) / TILE; }
+
+// Parsed header plus derived section offsets.
+struct Info {
+  uint64_t n, nb, nnc, R, o_out, o_sign, o_plane, size;
+  float eps_q;
+  uint32_t qbound;
+  double eps;
+  uint32_t ndims, dims[3];
+  int ok;
+};
+
+// Reads and checks the 64-byte header (every field that bounds a later read).
+__device__ __forceinline__ Info parse_header(const uint8_t* c, uint64_t c_bytes) {
+  Info h;
+  h.ok = 0;
+  h.n = h.nb = h.nnc = h.R = 0;
+  if (c_bytes < HOSZP_HEADER_BYTES) return h;
+  const hoszp_header* H = reinterpret_cast<const hoszp_header*>(c);
+  hoszp_header v = *H;
+  h.n = v.n;
+  h.nnc = v.nnc;
+  h.R = v.R;
+  h.eps_q = v.eps_q;
+  h.qbound = v.qbound;
+  h.eps = v.eps;
+  h.ndims = v.ndims;
+  h.dims[0] = v.dims[0];
+  h.dims[1] = v.dims[1];
+  h.dims[2] = v.dims[2];
+  h.nb = nblocks(v.n);
+  bool ok = v.magic == HOSZP_MAGIC && v.version == HOSZP_VERSION && v.dtype == 0 &&
+            v.block == HOSZP_BLOCK && v.eps_q >= 1.17549435e-38f && v.eps_q <= 1.70141173e38f &&
+            v.qbound <= (uint32_t)HOSZP_QLIM && v.n <= (1ull << 56) && v.nnc <= h.nb &&
+            v.R <= 31ull * v.nnc;
+  if (!ok) { h.nb = 0; return h; }
+  h.o_out = off_outlier(h.nb);
+  h.o_sign = off_sign(h.nb);
+  h.o_plane = off_plane(h.nb, h.nnc);
+  h.size = stream_bytes(h.nb, h.nnc, h.R);
+  if (h.size > c_bytes) { h.nb = 0; return h; }
+  h.ok = 1;
+  return h;
+}
+
+// ---------------------------------------------------------------- errors
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// ---------------------------------------------------------------- memory ordering
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
+  return *reinterpret_cast<const volatile unsigned int*>(p);
+}
+
+// ---------------------------------------------------------------- workspace
+// Per-tile look-back descriptor: flag = (epoch << 2) | state, state 1 = the
+// tile's own aggregate is published, 2 = its inclusive prefix is published.
+struct Desc {
+  unsigned long long flag;
+  unsigned long long agg;  // (nc << 32) | r of the tile
+  unsigned long long inc_nc, inc_r;
+};
+
+struct Sync {
+  unsigned int ticket;  // next tile to hand out in this launch
+  unsigned int done;    // CTAs finished in this launch
+  unsigned long long epoch;
+};
+
+struct Partial {  // per-CTA exact sums for the reductions
+  long long s1_lo, s1_hi;
+  unsigned long long s2_lo, s2_hi;
+};
+
+// Device workspace seen by the kernels (pointers into one allocation).
+struct Ws {
+  Sync* sync;
+  int* status;
+  unsigned long long* totals;  // [0] nnc, [1] R of the output, [2] qmax, [3] ticket base
+  float* eps_q;                // bound computed on the device (relative mode)
+  double* eps;
+  Desc* desc[NCHAIN];
+  uint64_t max_tiles;
+  Partial* partials;
+  float* range_part;  // per-CTA min, max (2 floats) + nonfinite flag as float
+  uint64_t max_grid;
+  uint64_t* staging;  // plane words of a produced stream before placement
+  uint64_t staging_words;
+  hoszp_header* hdr;  // header of the stream being produced (filled in by the producer)
+};
+
+// Tile hand-out and launch bookkeeping. Every CTA calls begin() once, next()
+// per tile and end() once; the CTA that finishes last resets the counters and
+// advances the epoch, so stale descriptors of earlier launches never match.
+struct LaunchState {
+  unsigned long long epoch;
+};
+
+__device__ __forceinline__ unsigned long long launch_epoch(const Ws& ws) {
+  return *reinterpret_cast<volatile unsigned long long*>(&ws.sync->epoch);
+}
+
+// Returns true in exactly one CTA: the last to finish this launch.
+__device__ __forceinline__ bool launch_end_is_last(const Ws& ws) {
+  __shared__ unsigned int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(&ws.sync->done, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+__device__ __forceinline__ void launch_reset(const Ws& ws) {
+  // called by one thread of the last CTA after its final work
+  ws.sync->ticket = 0;
+  ws.sync->done = 0;
+  ws.sync->epoch = ws.sync->epoch + 1;
+  __threadfence();
+}
+
+// ---------------------------------------------------------------- decoupled look-back
+constexpr long long SPIN_LIMIT = 1ll << 22;  // x ~256 ns sleeps: about a second
+
+__device__ __forceinline__ void publish(Desc* d, int64_t tile, unsigned long long epoch,
+                                        int state, unsigned long long agg,
+                                        unsigned long long inc_nc, unsigned long long inc_r) {
+  if (state == 1) {
+    d[tile].agg = agg;
+  } else {
+    d[tile].agg = agg;
+    d[tile].inc_nc = inc_nc;
+    d[tile].inc_r = inc_r;
+  }
+  __threadfence();
+  st_release(&d[tile].flag, (epoch << 2) | (unsigned long long)state);
+}
+
+// Warp-wide look-back: returns the exclusive prefix (nc, r) of `tile` over the
+// chain. All 32 lanes of the calling warp must take part. Spins are bounded;
+// on timeout the status word gets HOSZP_ERR_TIMEOUT and a zero prefix is used.
+__device__ __forceinline__ void lookback(Desc* d, int64_t tile, unsigned long long epoch, int* st,
+                                         unsigned long long& pnc, unsigned long long& pr) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long acc_nc = 0, acc_r = 0;
+  int64_t base = tile - 1;
+  while (base >= 0) {
+    int64_t j = base - lane;
+    int state = 2;
+    unsigned long long a = 0, inc_nc = 0, inc_r = 0;
+    if (j >= 0) {
+      long long spins = 0;
+      for (;;) {
+        unsigned long long f = ld_acquire(&d[j].flag);
+        state = ((f >> 2) == epoch) ? (int)(f & 3) : 0;
+        if (state != 0) break;
+        if (++spins > SPIN_LIMIT) {
+          set_status(st, HOSZP_ERR_TIMEOUT);
+          state = 2;
+          break;
+        }
+        __nanosleep(256);
+      }
+      if (state != 0) {
+        a = *reinterpret_cast<volatile unsigned long long*>(&d[j].agg);
+        if (state == 2) {
+          inc_nc = *reinterpret_cast<volatile unsigned long long*>(&d[j].inc_nc);
+          inc_r = *reinterpret_cast<volatile unsigned long long*>(&d[j].inc_r);
+        }
+      }
+    }
+    unsigned int incmask = __ballot_sync(0xffffffffu, state == 2);
+    int stop = incmask ? (__ffs(incmask) - 1) : 32;  // nearest tile with an inclusive prefix
+    unsigned long long vnc = 0, vr = 0;
+    if (lane < stop) {
+      vnc = a >> 32;
+      vr = a & 0xffffffffull;
+    } else if (lane == stop) {
+      vnc = inc_nc;
+      vr = inc_r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vnc += __shfl_xor_sync(0xffffffffu, vnc, o);
+      vr += __shfl_xor_sync(0xffffffffu, vr, o);
+    }
+    acc_nc += vnc;
+    acc_r += vr;
+    if (incmask) break;
+    base -= 32;
+  }
+  pnc = acc_nc;
+  pr = acc_r;
+}
+
+// Tile-level prefix for one chain, called by the whole CTA: publishes the
+// tile's aggregate, looks back (warp `wid`), publishes the inclusive prefix and
+// returns the exclusive prefix through shared memory.
+__device__ __forceinline__ void tile_prefix(Desc* d, int64_t tile, unsigned long long epoch,
+                                            int* st, unsigned int agg_nc, unsigned int agg_r,
+                                            int wid, unsigned long long* s_out /*[2]*/) {
+  if ((int)(threadIdx.x >> 5) == wid) {
+    unsigned long long agg = ((unsigned long long)agg_nc << 32) | agg_r;
+    unsigned long long pnc = 0, pr = 0;
+    if (tile == 0) {
+      if ((threadIdx.x & 31) == 0) publish(d, tile, epoch, 2, agg, agg_nc, agg_r);
+    } else {
+      if ((threadIdx.x & 31) == 0) publish(d, tile, epoch, 1, agg, 0, 0);
+      __syncwarp();
+      lookback(d, tile, epoch, st, pnc, pr);
+      if ((threadIdx.x & 31) == 0) publish(d, tile, epoch, 2, agg, pnc + agg_nc, pr + agg_r);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_out[0] = pnc;
+      s_out[1] = pr;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- bit manipulation
+// 8x8 bit transpose of the matrix held in (lo, hi): byte i = row i, bit j of a
+// byte = column j. Afterwards byte i holds column i. Three delta swaps.
+HZ_HD void tr8x8(uint32_t& lo, uint32_t& hi) {
+  uint32_t t;
+  t = (lo ^ (lo >> 7)) & 0x00AA00AAu;
+  lo = lo ^ t ^ (t << 7);
+  t = (hi ^ (hi >> 7)) & 0x00AA00AAu;
+  hi = hi ^ t ^ (t << 7);
+  t = (lo ^ (lo >> 14)) & 0x0000CCCCu;
+  lo = lo ^ t ^ (t << 14);
+  t = (hi ^ (hi >> 14)) & 0x0000CCCCu;
+  hi = hi ^ t ^ (t << 14);
+  t = (lo ^ (hi << 4)) & 0xF0F0F0F0u;
+  lo = lo ^ t;
+  hi = hi ^ (t >> 4);
+}
+
+#ifdef __CUDACC__
+// 8x8 byte transpose across the 8 lanes of an octet: lane j holds row j
+// (bytes 0..3 in lo, 4..7 in hi); afterwards lane j holds column j. All lanes
+// of the warp must call it (full-mask shuffles; partners differ in bits 0..2).
+__device__ __forceinline__ void byte_transpose8(uint32_t& lo, uint32_t& hi, int j) {
+  // swap the off-diagonal 4x4 byte blocks (lanes j, j^4)
+  uint32_t send = (j & 4) ? lo : hi;
+  uint32_t recv = __shfl_xor_sync(0xffffffffu, send, 4);
+  if (j & 4) lo = recv; else hi = recv;
+  // swap the off-diagonal 2x2 blocks of each 4x4 block (lanes j, j^2)
+  bool b1 = (j & 2) != 0;
+  send = __byte_perm(lo, hi, b1 ? 0x5410 : 0x7632);
+  recv = __shfl_xor_sync(0xffffffffu, send, 2);
+  lo = __byte_perm(lo, recv, b1 ? 0x3254 : 0x5410);
+  hi = __byte_perm(hi, recv, b1 ? 0x3276 : 0x7610);
+  // transpose each 2x2 block (lanes j, j^1)
+  bool b0 = (j & 1) != 0;
+  send = __byte_perm(lo, hi, b0 ? 0x6420 : 0x7531);
+  recv = __shfl_xor_sync(0xffffffffu, send, 1);
+  lo = __byte_perm(lo, recv, b0 ? 0x3514 : 0x5240);
+  hi = __byte_perm(hi, recv, b0 ? 0x3716 : 0x7260);
+}
+
+// ---------------------------------------------------------------- quantization (Eq. 3)
+// Exact q = floor((x + e) / (2e)) for float x, e = eps_q (normal float), using
+// only FP32 FMA arithmetic: an estimate k rounds x * r (r ~ 1/(2e)) to an
+// integer, d = x - k*2e is formed with one rounding by an FMA, and d against
+// +-e decides q in {k-1, k, k+1}. d is exact-or-monotonically-rounded, so only
+// d == +-e is ambiguous; that case is settled exactly with an error-free
+// product (two FMAs) and Sterbenz subtractions.
+struct Quant {
+  float e, e2, r;  // eps_q, 2 eps_q, fl(1 / (2 eps_q))
+};
+
+__device__ __forceinline__ int quant_fix(float x, float kf, int k, const Quant& Q) {
+  float d = __fmaf_rn(-kf, Q.e2, x);
+  if (d < -Q.e) return k - 1;
+  if (d > Q.e) return k + 1;
+  if (d == -Q.e || d == Q.e) {
+    float p = __fmul_rn(kf, Q.e2);
+    float perr = __fmaf_rn(kf, Q.e2, -p);  // kf*e2 = p + perr exactly
+    float d1 = __fsub_rn(x, p);            // exact here
+    if (d == -Q.e) return (__fadd_rn(d1, Q.e) < perr) ? k - 1 : k;
+    return (__fsub_rn(d1, Q.e) >= perr) ? k + 1 : k;
+  }
+  return k;
+}
+
+// Returns q; sets *bad to HOSZP_ERR_NONFINITE or HOSZP_ERR_RANGE when needed.
+__device__ __forceinline__ int quantize(float x, const Quant& Q, int& bad) {
+  const float MAGIC = 12582912.0f;  // 1.5 * 2^23
+  float t = __fmul_rn(x, Q.r);
+  if (fabsf(t) < 4194300.0f) {  // |x r| < 2^22: integer rounding by the magic add
+    float y = __fmaf_rn(x, Q.r, MAGIC);
+    int k = __float_as_int(y) - 0x4B400000;
+    float kf = __fsub_rn(y, MAGIC);
+    return quant_fix(x, kf, k, Q);
+  }
+  if (!(fabsf(x) <= 3.40282347e38f)) {
+    bad = HOSZP_ERR_NONFINITE;
+    return 0;
+  }
+  if (!(fabsf(t) <= 8388612.0f)) {  // |q| >= 2^23 + 3 > HOSZP_QMAX_COMPRESS
+    bad = HOSZP_ERR_RANGE;
+    return 0;
+  }
+  int k = __float2int_rn(t);
+  int q = quant_fix(x, (float)k, k, Q);
+  if (q > HOSZP_QMAX_COMPRESS || q < -HOSZP_QMAX_COMPRESS) bad = HOSZP_ERR_RANGE;
+  return q;
+}
+
+// x' = float(q) * 2e (reverse quantization). For |q| < 2^22 the conversion is
+// done with the magic-number trick (FP32 pipe), otherwise with I2F.
+__device__ __forceinline__ float dequant_small(int q, float e2) {
+  float qf = __fsub_rn(__int_as_float(q + 0x4B400000), 12582912.0f);
+  return __fmul_rn(qf, e2);
+}
+__device__ __forceinline__ float dequant_any(int q, float e2) {
+  return __fmul_rn(__int2float_rn(q), e2);
+}
+
+// ---------------------------------------------------------------- octet codec
+// Decode the magnitudes of lane j's 8 positions from a block's planes.
+// planes: the block's first plane word; r: its rate; kmax: warp-uniform number
+// of 8-plane groups to run (>= ceil(r/8)). mag[t] for position 8j+t.
+__device__ __forceinline__ void decode_mags(const uint64_t* __restrict__ planes, int r, int kmax,
+                                            int j, uint32_t mag[8]) {
+#pragma unroll
+  for (int t = 0; t < 8; t++) mag[t] = 0;
+  for (int k = 0; k < kmax; k++) {
+    int p = 8 * k + j;
+    uint64_t w = (p < r) ? __ldg(planes + p) : 0ull;
+    uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+    byte_transpose8(lo, hi, j);
+    tr8x8(lo, hi);
+    const int sh = 8 * k;
+    mag[0] |= (lo & 0xffu) << sh;
+    mag[1] |= ((lo >> 8) & 0xffu) << sh;
+    mag[2] |= ((lo >> 16) & 0xffu) << sh;
+    mag[3] |= (lo >> 24) << sh;
+    mag[4] |= (hi & 0xffu) << sh;
+    mag[5] |= ((hi >> 8) & 0xffu) << sh;
+    mag[6] |= ((hi >> 16) & 0xffu) << sh;
+    mag[7] |= (hi >> 24) << sh;
+  }
+}
+
+// Encode: lane j holds magnitudes of its 8 positions; writes plane words
+// 8k+j (< r) of the block to planes_out. kmax warp-uniform >= ceil(r/8).
+__device__ __forceinline__ void encode_planes(const uint32_t mag[8], int r, int kmax, int j,
+                                              uint64_t* planes_out, uint64_t limit_words) {
+  for (int k = 0; k < kmax; k++) {
+    const int sh = 8 * k;
+    uint32_t b0 = (mag[0] >> sh) & 0xffu, b1 = (mag[1] >> sh) & 0xffu;
+    uint32_t b2 = (mag[2] >> sh) & 0xffu, b3 = (mag[3] >> sh) & 0xffu;
+    uint32_t b4 = (mag[4] >> sh) & 0xffu, b5 = (mag[5] >> sh) & 0xffu;
+    uint32_t b6 = (mag[6] >> sh) & 0xffu, b7 = (mag[7] >> sh) & 0xffu;
+    uint32_t lo = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+    uint32_t hi = b4 | (b5 << 8) | (b6 << 16) | (b7 << 24);
+    tr8x8(lo, hi);             // byte p' = bit 8k+p' of the 8 magnitudes
+    byte_transpose8(lo, hi, j);  // lane j: plane word 8k+j
+    int p = sh + j;
+    if (p < r && (uint64_t)p < limit_words)
+      planes_out[p] = ((uint64_t)hi << 32) | lo;
+  }
+}
+
+// Rate of a block from lane magnitudes: bit length of the octet-wide maximum.
+__device__ __forceinline__ int octet_rate(const uint32_t mag[8]) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int t = 0; t < 8; t++) m = max(m, mag[t]);
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 4));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  return 32 - __clz(m);
+}
+
+// Exclusive scan of a per-octet value across the 8 lanes of the octet.
+__device__ __forceinline__ int octet_excl_scan(int v, int j) {
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o, 8);
+    if (j >= o) x += y;
+  }
+  return x - v;
+}
+#endif  // __CUDACC__
+
+// ---------------------------------------------------------------- tile-level block scan
+// For the 64 blocks of a tile: counts of non-constant blocks and rate sums,
+// their exclusive prefixes per block, and the tile aggregate. Called by the
+// whole CTA; rate_of_block supplied in shared memory s_rate[64].
+struct TileScan {
+  unsigned int nc_excl[TILE];
+  unsigned int r_excl[TILE];
+  unsigned int agg_nc, agg_r;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void tile_scan(const uint8_t* s_rate, TileScan* ts) {
+  // warps 0 and 1 scan 32 blocks each, then combine
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    int lane = tid & 31;
+    unsigned int r = s_rate[tid];
+    unsigned int nc = r > 0 ? 1u : 0u;
+    unsigned int pr = r, pnc = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int yr = __shfl_up_sync(0xffffffffu, pr, o);
+      unsigned int ync = __shfl_up_sync(0xffffffffu, pnc, o);
+      if (lane >= o) { pr += yr; pnc += ync; }
+    }
+    ts->nc_excl[tid] = pnc - nc;
+    ts->r_excl[tid] = pr - r;
+  }
+  __syncthreads();
+  if (tid >= 32 && tid < 64) {
+    ts->nc_excl[tid] += ts->nc_excl[31] + (s_rate[31] > 0 ? 1u : 0u);
+    ts->r_excl[tid] += ts->r_excl[31] + s_rate[31];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    ts->agg_nc = ts->nc_excl[63] + (s_rate[63] > 0 ? 1u : 0u);
+    ts->agg_r = ts->r_excl[63] + s_rate[63];
+  }
+  __syncthreads();
+}
+#endif
+
+}  // namespace hz

@@ -1,0 +1,53 @@
+// hz_kernels.cuh — host-side launch wrappers implemented by the .cu files and
+// called by the C ABI (api.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hz_common.cuh"
+
+namespace hz {
+
+struct Launch {
+  int grid;  // number of SMs; each kernel multiplies by its resident CTAs per SM
+  cudaStream_t stream;
+};
+
+// compress.cu
+cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double rel, Ws ws);
+cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const uint32_t dims[3],
+                            uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
+                            uint64_t cap, Ws ws);
+// place.cu: move staged planes behind the sign section and write the header
+// Completes a produced stream: reads the totals (nnc, R, qbound) left in the
+// workspace by the producer, checks the capacity, copies the staged planes
+// behind the sign section and writes the header and the size word.
+cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
+// decode.cu
+cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
+                              uint64_t n, Ws ws);
+cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
+                           bool variance, Ws ws);
+// ops.cu
+cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, uint8_t* out,
+                          uint64_t cap, uint64_t* out_bytes, Ws ws);
+cudaError_t launch_add_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
+                              uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
+cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
+                              uint8_t* out, uint64_t cap, Ws ws);
+cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
+                       uint64_t b_bytes, uint8_t* out, uint64_t cap, Ws ws);
+
+// Persistent grid: SMs x resident CTAs per SM of `kernel` (capped at 8).
+template <typename K>
+inline int persistent_grid(K kernel, int threads, int num_sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per = 1;
+  }
+  per = per < 1 ? 1 : (per > 8 ? 8 : per);
+  return num_sms * per;
+}
+
+}  // namespace hz

@@ -1,0 +1,203 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Bit-exact: compressed bytes, decoded floats, every produced stream.
+Within 1e-12 relative: mean and variance (exact integer sums, FP64 finish).
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def hz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2408_11971_gb300 as hz
+    from paper_2408_11971_gb300 import build
+
+    build.build()
+    O.build()
+    return hz
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def close(a, b, tol=REL_TOL):
+    return abs(a - b) <= tol * max(abs(b), 1e-300)
+
+
+CASES = datagen.small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES.keys()))
+@pytest.mark.parametrize("eb,mode", [(1e-2, "rel"), (1e-4, "rel"), (0.05, "abs")])
+def test_codec_and_ops_small(hz, name, eb, mode):
+    x = CASES[name]
+    c = hz.compress(dev(x), eb=eb, mode=mode, dims=(x.size,))
+    oc = O.compress(x, dims=(x.size,), eb=eb, mode=mode)
+    assert np.array_equal(host(c), oc)
+    assert np.array_equal(host(hz.decompress(c)), O.decompress(oc))
+    assert np.array_equal(host(hz.negate(c)), O.negate(oc))
+    assert np.array_equal(host(hz.add_scalar(c, 0.5)), O.add_scalar(oc, 0.5))
+    for s in (3.14, -0.37, 1e-3):
+        assert np.array_equal(host(hz.mul_scalar(c, s)), O.mul_scalar(oc, s)), s
+    y = (x[::-1].copy() * np.float32(0.5)).astype(np.float32)
+    e = float(O.header(oc)["eps_q"])
+    cy = hz.compress(dev(y), eb=e, dims=(y.size,))
+    ocy = O.compress(y, dims=(y.size,), eb=e)
+    assert np.array_equal(host(cy), ocy)
+    assert np.array_equal(host(hz.add(c, cy)), O.add(oc, ocy))
+    if x.size > 0:
+        assert close(hz.mean(c), O.mean(oc))
+        assert close(hz.var(c), O.var(oc))
+
+
+@pytest.fixture(scope="module")
+def config1(hz):
+    x = datagen.sines_1d(1 << 20, seed=0)
+    c = hz.compress(dev(x), eb=1e-3, mode="rel")
+    oc = O.compress(x, eb=1e-3, mode="rel")
+    return x, c, oc
+
+
+def test_config1_sines_2p20(hz, config1):
+    x, c, oc = config1
+    assert np.array_equal(host(c), oc)
+    assert np.array_equal(host(hz.decompress(c)), O.decompress(oc))
+    assert np.array_equal(host(hz.negate(c)), O.negate(oc))
+    assert np.array_equal(host(hz.add_scalar(c, 0.5)), O.add_scalar(oc, 0.5))
+    assert np.array_equal(host(hz.mul_scalar(c, 2.5)), O.mul_scalar(oc, 2.5))
+    assert close(hz.mean(c), O.mean(oc))
+    assert close(hz.var(c), O.var(oc))
+
+
+def test_inplace_negate_and_add_scalar(hz, config1):
+    _, c, oc = config1
+    w = c.clone()
+    hz.negate(w, inplace=True)
+    assert np.array_equal(host(w), O.negate(oc))
+    hz.add_scalar(w, -1.25, inplace=True)
+    assert np.array_equal(host(w), O.add_scalar(O.negate(oc), -1.25))
+
+
+def test_theorem1_add_negate_is_zero(hz, config1):
+    _, c, _ = config1
+    z = hz.add(c, hz.negate(c))
+    h = hz.header(z)
+    assert h["nnc"] == 0 and h["R"] == 0
+    assert not host(hz.decompress(z)).any()
+
+
+@pytest.mark.parametrize("shape,rel", [((64, 80, 91), 1e-3), ((33, 47, 29), 1e-5),
+                                        ((100, 500, 50), 1e-4)])
+def test_grf_3d(hz, shape, rel):
+    x = datagen.grf(shape, seed=5)
+    y = datagen.grf(shape, seed=6)
+    c = hz.compress(dev(x), eb=rel, mode="rel")
+    oc = O.compress(x, eb=rel, mode="rel")
+    assert np.array_equal(host(c), oc)
+    e = float(O.header(oc)["eps_q"])
+    cy, ocy = hz.compress(dev(y), eb=e), O.compress(y, eb=e)
+    assert np.array_equal(host(cy), ocy)
+    assert np.array_equal(host(hz.add(c, cy)), O.add(oc, ocy))
+    assert np.array_equal(host(hz.decompress(c)), O.decompress(oc))
+    assert np.array_equal(host(hz.mul_scalar(c, -1.5)), O.mul_scalar(oc, -1.5))
+    assert close(hz.mean(c), O.mean(oc)) and close(hz.var(c), O.var(oc))
+
+
+def test_land_mask_fill_values(hz):
+    x = datagen.lat_bands_2d(180, 360, seed=3)
+    for rel in (1e-2, 1e-4, 1e-6):
+        c = hz.compress(dev(x), eb=rel, mode="rel")
+        oc = O.compress(x, eb=rel, mode="rel")
+        assert np.array_equal(host(c), oc)
+        assert np.array_equal(host(hz.mul_scalar(c, 0.75)), O.mul_scalar(oc, 0.75))
+        assert close(hz.mean(c), O.mean(oc)) and close(hz.var(c), O.var(oc))
+
+
+def test_wide_rates_and_quantizer_edges(hz):
+    rng = np.random.default_rng(7)
+    e = np.float32(0.5)
+    # exact bin edges, their neighbours, values near the quantizer's range limit
+    k = rng.integers(-4_000_000, 4_000_000, 20_000)
+    edges = ((2 * k - 1) * 0.5).astype(np.float32)
+    x = np.concatenate([edges, np.nextafter(edges, np.float32(np.inf)),
+                        np.nextafter(edges, np.float32(-np.inf)),
+                        rng.uniform(-8.3e6, 8.3e6, 30_000).astype(np.float32),
+                        np.float32([8388606.0, -8388606.0, 8388606.4])]).astype(np.float32)
+    c = hz.compress(dev(x), eb=float(e))
+    oc = O.compress(x, eb=float(e))
+    assert np.array_equal(host(c), oc)
+    assert O.header(oc)["R"] > 0
+    assert np.array_equal(host(hz.decompress(c)), O.decompress(oc))
+
+
+def test_errors_reported(hz):
+    HE = hz.HoszpError
+    with pytest.raises(HE) as ex:
+        hz.compress(dev(np.array([1.0, np.nan] * 100, np.float32)), eb=0.1)
+    assert ex.value.name == "NONFINITE"
+    with pytest.raises(HE) as ex:
+        hz.compress(dev(np.array([1.0, np.inf] * 100, np.float32)), eb=0.1, mode="rel")
+    assert ex.value.name == "NONFINITE"
+    with pytest.raises(HE) as ex:
+        hz.compress(dev(np.full(100, 1e10, np.float32)), eb=1e-3)
+    assert ex.value.name == "RANGE"
+    with pytest.raises(HE) as ex:
+        hz.compress(dev(np.ones(10, np.float32)), eb=-1.0)
+    assert ex.value.name == "ARG"
+    x = np.ones(1000, np.float32)
+    c = hz.compress(dev(x), eb=0.1)
+    bad = c.clone()
+    bad[0] ^= 1
+    with pytest.raises(HE) as ex:
+        hz.decompress(bad, n=1000)
+    assert ex.value.name == "FORMAT"
+    with pytest.raises(HE) as ex:
+        hz.add(c, hz.compress(dev(x), eb=0.2))
+    assert ex.value.name == "MISMATCH"
+    with pytest.raises(HE) as ex:
+        hz.mean(hz.compress(dev(np.zeros(0, np.float32)), eb=0.1, dims=(0,)))
+    assert ex.value.name == "ARG"
+    big = hz.compress(dev(np.full(64, 8e5, np.float32)), eb=0.1)
+    with pytest.raises(HE) as ex:
+        hz.mul_scalar(big, 1000.0)
+    assert ex.value.name == "OVERFLOW"
+    with pytest.raises(HE) as ex:
+        hz.add_scalar(big, 1e9)
+    assert ex.value.name in ("RANGE", "OVERFLOW")
+    # a stream whose rate section disagrees with its header
+    c2 = hz.compress(dev(datagen.sines_1d(5000, seed=1)), eb=1e-3)
+    corrupt = c2.clone()
+    corrupt[64] = (int(corrupt[64]) + 1) % 20 + 1
+    with pytest.raises(HE) as ex:
+        hz.mean(corrupt)
+    assert ex.value.name == "FORMAT"
+    # too small an output buffer
+    xs = dev(datagen.sines_1d(50_000, seed=2))
+    small = torch.empty(2_000, dtype=torch.uint8, device="cuda")
+    with pytest.raises(HE) as ex:
+        hz.compress(xs, eb=1e-4, mode="rel", out=small)
+    assert ex.value.name == "CAPACITY"
+    # the context stays usable after errors
+    assert np.array_equal(host(hz.compress(dev(x), eb=0.1)), O.compress(x, eb=0.1))
+
+
+def test_repeated_calls_are_deterministic(hz, config1):
+    x, c, oc = config1
+    for _ in range(3):
+        assert np.array_equal(host(hz.compress(dev(x), eb=1e-3, mode="rel")), oc)
+        assert close(hz.var(c), O.var(oc))
