@@ -208,8 +208,11 @@ __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, 
     } else if (h.ok) {
       const double e2 = 2.0 * (double)h.eps_q;
       if (!VAR) {
-        const double s1d = (double)(long long)(S1 >> 64) * 18446744073709551616.0 +
-                           (double)(unsigned long long)S1;
+        // sign and magnitude: hi * 2^64 + lo without cancellation
+        const unsigned __int128 m = (unsigned __int128)(S1 < 0 ? -S1 : S1);
+        const double md = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 +
+                          (double)(unsigned long long)m;
+        const double s1d = S1 < 0 ? -md : md;
         res = (s1d / (double)h.n) * e2;
       } else {
         // n S2 - S1^2 >= 0 exactly (Cauchy-Schwarz), in 256-bit integers

@@ -137,12 +137,20 @@ def test_wide_rates_and_quantizer_edges(hz):
     x = np.concatenate([edges, np.nextafter(edges, np.float32(np.inf)),
                         np.nextafter(edges, np.float32(-np.inf)),
                         rng.uniform(-8.3e6, 8.3e6, 30_000).astype(np.float32),
-                        np.float32([8388606.0, -8388606.0, 8388606.4])]).astype(np.float32)
+                        np.float32([8388606.0, -8388606.0, 8388605.4])]).astype(np.float32)
     c = hz.compress(dev(x), eb=float(e))
     oc = O.compress(x, eb=float(e))
     assert np.array_equal(host(c), oc)
     assert O.header(oc)["R"] > 0
     assert np.array_equal(host(hz.decompress(c)), O.decompress(oc))
+    # 8388606.5 / (2 * 0.5) rounds to 8388607 = HOSZP_QMAX_COMPRESS + 1
+    over = np.float32([1.0, 8388606.5])
+    with pytest.raises(O.OracleError) as eo:
+        O.compress(over, eb=0.5)
+    assert eo.value.name == "RANGE"
+    with pytest.raises(hz.HoszpError) as eg:
+        hz.compress(dev(over), eb=0.5)
+    assert eg.value.name == "RANGE"
 
 
 def test_errors_reported(hz):
