@@ -1,0 +1,450 @@
+"""Benchmark of the HoSZp hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hoszp|reference]
+
+Workload (the 3-D configuration of the benchmark set): two float32 Gaussian
+random fields A and B of 512^3 values (E(k) ~ k^-5/3, seeds 1 and 2), value-range
+relative bound 1e-4 (B is compressed with A's absolute bound so the two streams
+can be added). One step runs every row of the hot path once:
+
+    compress A, compress B        (range pass, Eq. 3, Eq. 4, BF encoding)
+    negate A, add_scalar A 0.5, mul_scalar A 3.14, add A+B  (Sec. V-A, V-C)
+    mean A, var A                 (Sec. V-B)
+    decompress A                  (inverse pipeline)
+
+value = original bytes the step's operators take as input (4N per input field,
+10 fields' worth per step) / step time, in GB/s. The line also carries the
+per-operator breakdown, the GPU decompress -> op -> recompress comparator built
+from the same library, the roofline of the dominant operator, the oracle timed
+on the host cores (cpu_baseline) and the end-to-end figure through host memory.
+Multi-GPU (torchrun): every rank runs its own pair of fields (weak scaling, no
+collective on the data path); time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("homomorphic op GB/s (original bytes) & % HBM roofline vs GPU "
+          "decompress-op-recompress")
+SHAPE = (512, 512, 512)
+REL = 1e-4
+DEFAULT_SHAPE = SHAPE
+SCALAR_ADD = 0.5
+SCALAR_MUL = 3.14
+KERNELS_PER_STEP = 15  # 2 x (range, compress, place) + negate + add_scalar + 2 mul + 2 add + mean + var + decompress
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2408_11971_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel sources have not changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel)
+        if e and e.get("csrc_sha") == csrc_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax = max(smax, float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+def oracle_step(O, a: np.ndarray, b: np.ndarray):
+    """One step of the hot path on the CPU oracle; returns seconds."""
+    t0 = time.perf_counter()
+    ca = O.compress(a, eb=REL, mode="rel")
+    e = float(O.header(ca)["eps_q"])
+    cb = O.compress(b, eb=e)
+    O.negate(ca)
+    O.add_scalar(ca, SCALAR_ADD)
+    O.mul_scalar(ca, SCALAR_MUL)
+    O.add(ca, cb)
+    O.mean(ca)
+    O.var(ca)
+    O.decompress(ca)
+    return time.perf_counter() - t0
+
+
+def run_oracle(a, b, steps: int, warmup: int):
+    import oracle as O
+
+    O.build()
+    for _ in range(warmup):
+        oracle_step(O, a, b)
+    ts = [oracle_step(O, a, b) for _ in range(steps)]
+    return sum(ts) / len(ts)
+
+
+def sample_fields(A: np.ndarray, B: np.ndarray, n: int):
+    """Bounded CPU sample: the first n values (whole 64-value blocks) of each field."""
+    n = min(n, A.size) // 64 * 64
+    return np.ascontiguousarray(A.reshape(-1)[:n]), np.ascontiguousarray(B.reshape(-1)[:n])
+
+
+def make_fields(seed_base: int):
+    import datagen
+
+    A = datagen.grf(SHAPE, seed=seed_base + 1)
+    B = datagen.grf(SHAPE, seed=seed_base + 2)
+    return A, B
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hoszp", choices=["hoszp", "reference"])
+    ap.add_argument("--oracle-sample", type=int, default=1 << 24,
+                    help="values per field in the CPU oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", type=int, nargs=3, default=list(DEFAULT_SHAPE),
+                    help="field shape (smaller cases are for profiling, not bench lines)")
+    args = ap.parse_args()
+    global SHAPE
+    SHAPE = tuple(args.shape)
+    warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    n = int(np.prod(SHAPE))
+    config = {"workload": "grf3d_%dx%dx%d_rel1e-4_fieldsAB" % SHAPE, "shape": list(SHAPE), "n": n,
+              "rel_eb": REL, "spectrum": "E(k)~k^-5/3", "fields": 2,
+              "ops": ["compress A", "compress B", "negate", "add_scalar 0.5", "mul_scalar 3.14",
+                      "add A+B", "mean", "var", "decompress"],
+              "l2": "no flush: each field is 512 MiB and each stream > L2 (129 MB)",
+              "parallelism": f"replica{world}"}
+
+    if args.impl == "reference":
+        # the reference arm is the oracle, as it stands, on the host cores
+        if rank != 0:
+            return
+        A, B = make_fields(0)
+        a, b = sample_fields(A, B, args.oracle_sample)
+        sec = run_oracle(a, b, args.steps, args.warmup)
+        val = 40.0 * a.size / sec / 1e9
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"first {a.size} values of each 512^3 field, one step of all rows"},
+                "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2408_11971_gb300 as hz
+    from paper_2408_11971_gb300 import build as hzbuild
+
+    hzbuild.build()
+    hz.load_library()
+    ctx = hz.Context(dev.index)
+    ctx.reserve(n)
+    stream = torch.cuda.current_stream(dev)
+
+    A, B = make_fields(1000 * rank)
+    xa = torch.from_numpy(A.reshape(-1)).to(dev)
+    xb = torch.from_numpy(B.reshape(-1)).to(dev)
+    cap = hz.compress_bound(n)
+    bufs = {k: torch.empty(cap, dtype=torch.uint8, device=dev)
+            for k in ("ca", "cb", "neg", "adds", "mul", "sum")}
+    sizes = {k: torch.zeros(1, dtype=torch.int64, device=dev) for k in bufs}
+    res = torch.zeros(2, dtype=torch.float64, device=dev)
+    xr = torch.empty(n, dtype=torch.float32, device=dev)
+
+    # first compression on the host's schedule: A's bound, used for B as well
+    ca = hz.compress(xa, eb=REL, mode="rel", ctx=ctx)
+    eps_q = hz.header(ca)["eps_q"]
+    cb = hz.compress(xb, eb=eps_q, ctx=ctx)
+    C = {"ca": ca.numel(), "cb": cb.numel()}
+    for k, src in (("neg", hz.negate), ("adds", lambda c, **kw: hz.add_scalar(c, SCALAR_ADD, **kw)),
+                   ("mul", lambda c, **kw: hz.mul_scalar(c, SCALAR_MUL, **kw))):
+        C[k] = src(ca, ctx=ctx).numel()
+    C["sum"] = hz.add(ca, cb, ctx=ctx).numel()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ops = ["compress A", "compress B", "negate", "add_scalar", "mul_scalar", "add", "mean", "var",
+           "decompress"]
+
+    def step(record=None):
+        def mark(i):
+            if record is not None:
+                record[i].record(stream)
+
+        ca_b, cb_b = bufs["ca"], bufs["cb"]
+        mark(0)
+        hz.compress(xa, eb=REL, mode="rel", out=ca_b, out_bytes=sizes["ca"], ctx=ctx, sync=False)
+        mark(1)
+        hz.compress(xb, eb=eps_q, out=cb_b, out_bytes=sizes["cb"], ctx=ctx, sync=False)
+        mark(2)
+        sa, sb = ca_b[:C["ca"]], cb_b[:C["cb"]]
+        hz.negate(sa, out=bufs["neg"], out_bytes=sizes["neg"], ctx=ctx, sync=False)
+        mark(3)
+        hz.add_scalar(sa, SCALAR_ADD, out=bufs["adds"], out_bytes=sizes["adds"], ctx=ctx,
+                      sync=False)
+        mark(4)
+        hz.mul_scalar(sa, SCALAR_MUL, out=bufs["mul"], out_bytes=sizes["mul"], ctx=ctx, sync=False)
+        mark(5)
+        hz.add(sa, sb, out=bufs["sum"], out_bytes=sizes["sum"], ctx=ctx, sync=False)
+        mark(6)
+        hz.mean(sa, out=res[0:1], ctx=ctx, sync=False)
+        mark(7)
+        hz.var(sa, out=res[1:2], ctx=ctx, sync=False)
+        mark(8)
+        hz.decompress(sa, n=n, out=xr, ctx=ctx, check=False)
+        mark(9)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.check("warmup")
+
+    K = args.steps
+    marks = [[ev() for _ in range(10)] for _ in range(K)]
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = ev(), ev()
+    t_start.record(stream)
+    for k in range(K):
+        step(marks[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clk.stop()
+    ctx.check("timed steps")
+    total_ms = t_start.elapsed_time(t_end)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / K
+    per_op_ms = {op: statistics.mean(marks[k][i].elapsed_time(marks[k][i + 1]) for k in range(K))
+                 for i, op in enumerate(ops)}
+
+    # algorithmic bytes per operator (reads + writes the operator must make)
+    N4 = 4 * n
+    alg = {"compress A": 2 * N4 + C["ca"], "compress B": N4 + C["cb"], "negate": 2 * C["ca"],
+           "add_scalar": 2 * C["ca"], "mul_scalar": C["ca"] + C["mul"],
+           "add": C["ca"] + C["cb"] + C["sum"], "mean": C["ca"], "var": C["ca"],
+           "decompress": C["ca"] + N4}
+    orig = {op: N4 for op in ops}
+    orig["add"] = 2 * N4
+    peak, peak_kind = measured_peak()
+    per_op = {}
+    for op in ops:
+        ms = per_op_ms[op]
+        per_op[op] = {"ms": round(ms, 4), "orig_gbs": orig[op] / ms / 1e6,
+                      "alg_gbs": alg[op] / ms / 1e6, "frac_of_measured_hbm": alg[op] / ms / 1e6 / peak}
+
+    # GPU decompress -> op -> recompress comparator (same kernels, not fused)
+    base = {}
+    tmp1 = torch.empty(n, dtype=torch.float32, device=dev)
+    tmp2 = torch.empty(n, dtype=torch.float32, device=dev)
+    tmp3 = torch.empty(n, dtype=torch.float32, device=dev)
+    outb = torch.empty(cap, dtype=torch.uint8, device=dev)
+    outs = torch.zeros(1, dtype=torch.int64, device=dev)
+    sa, sb = bufs["ca"][:C["ca"]], bufs["cb"][:C["cb"]]
+
+    def trad(op):
+        hz.decompress(sa, n=n, out=tmp1, ctx=ctx, check=False)
+        if op == "negate":
+            hz.fop_axpb(tmp1, -1.0, 0.0, out=tmp2)
+        elif op == "add_scalar":
+            hz.fop_axpb(tmp1, 1.0, SCALAR_ADD, out=tmp2)
+        elif op == "mul_scalar":
+            hz.fop_axpb(tmp1, SCALAR_MUL, 0.0, out=tmp2)
+        elif op == "add":
+            hz.decompress(sb, n=n, out=tmp3, ctx=ctx, check=False)
+            hz.fop_add(tmp1, tmp3, out=tmp2)
+        elif op in ("mean", "var"):
+            hz.fop_moments(tmp1, op == "var", out=res[0:1], ctx=ctx)
+            return
+        hz.compress(tmp2, eb=eps_q, out=outb, out_bytes=outs, ctx=ctx, sync=False)
+
+    for op in ("negate", "add_scalar", "mul_scalar", "add", "mean", "var"):
+        for _ in range(2):
+            trad(op)
+        e0, e1 = ev(), ev()
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            trad(op)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1) / reps
+        base[op] = {"ms": round(tms, 4), "speedup_homomorphic": tms / per_op_ms[op]}
+    ctx.check("baseline")
+
+    # roofline of the dominant operator (largest share of the step)
+    dom = max(ops, key=lambda o: per_op_ms[o])
+    kern_of = {"compress A": "k_compress", "compress B": "k_compress", "negate": "k_meta",
+               "add_scalar": "k_meta", "mul_scalar": "k_mul_scalar", "add": "k_add",
+               "mean": "k_moments", "var": "k_moments", "decompress": "k_decompress"}
+    achieved = alg[dom] / per_op_ms[dom] / 1e6
+    tr = ncu_traffic(kern_of[dom])
+    roofline = {"bound": "hbm", "op": dom, "kernel": kern_of[dom], "achieved": achieved,
+                "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                "frac": achieved / peak, "alg_bytes_per_launch": alg[dom],
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None)}
+
+    # end to end through host memory: pinned inputs in, results out, every step
+    e2e = None
+    if rank == 0 or world > 1:
+        ha = torch.from_numpy(A.reshape(-1)).pin_memory()
+        hb = torch.from_numpy(B.reshape(-1)).pin_memory()
+        hout = torch.empty(n, dtype=torch.float32).pin_memory()
+        hres = torch.empty(2, dtype=torch.float64).pin_memory()
+        E = max(2, min(K, 5))
+
+        def e2e_step():
+            xa.copy_(ha, non_blocking=True)
+            xb.copy_(hb, non_blocking=True)
+            step()
+            hout.copy_(xr, non_blocking=True)
+            hres.copy_(res, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(E):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / E
+        if dist is not None:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * 40.0 * n / e_ms / 1e6, "unit": "GB/s",
+               "h2d_bytes_per_step": 2 * N4, "d2h_bytes_per_step": N4 + 16, "ms_per_step": e_ms}
+    ctx.check("e2e")
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        a, b = sample_fields(A, B, args.oracle_sample)
+        sec = run_oracle(a, b, 1, 0)
+        cpu = {"value": 40.0 * a.size / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {a.size} values of fields A and B, one step of all rows",
+               "seconds": sec}
+
+    value = world * 40.0 * n / ms_step / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": config,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
+            "compressed_bytes": C, "per_op": per_op, "decompress_op_recompress": base}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

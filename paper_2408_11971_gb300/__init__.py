@@ -30,10 +30,13 @@ from ._binding import (  # noqa: F401
     mean,
     var,
     header,
+    fop_axpb,
+    fop_add,
+    fop_moments,
 )
 
 __all__ = [
     "HoszpError", "Context", "STATUS", "lib_path", "load_library", "default_context",
     "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add",
-    "mean", "var", "header",
+    "mean", "var", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

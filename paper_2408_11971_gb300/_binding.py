@@ -302,3 +302,44 @@ def mean(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = Tr
 def var(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
     """Population variance from exact integer sums (Sec. V-B)."""
     return _moment(load_library().hoszp_var, "var", c, out, stream, ctx, sync, check)
+
+
+# ---------------------------------------------------------------- traditional workflow (float ops)
+def _fop_lib():
+    lib = load_library()
+    if not getattr(lib, "_fop_ready", False):
+        P, U64, F, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_float, ctypes.c_int
+        lib.hoszp_fop_axpb.restype = I
+        lib.hoszp_fop_axpb.argtypes = [P, P, U64, F, F, P]
+        lib.hoszp_fop_add.restype = I
+        lib.hoszp_fop_add.argtypes = [P, P, P, U64, P]
+        lib.hoszp_fop_moments.restype = I
+        lib.hoszp_fop_moments.argtypes = [P, P, U64, I, P, P]
+        lib._fop_ready = True
+    return lib
+
+
+def fop_axpb(x, a: float, b: float, out=None, stream=None):
+    """y = a x + b on a float32 CUDA tensor (traditional-workflow operator)."""
+    torch = _torch()
+    out = torch.empty_like(x) if out is None else out
+    _check(_fop_lib().hoszp_fop_axpb(_dev_ptr(x), _dev_ptr(out), x.numel(), a, b,
+                                     _stream_ptr(stream)), "fop_axpb")
+    return out
+
+
+def fop_add(x, y, out=None, stream=None):
+    torch = _torch()
+    out = torch.empty_like(x) if out is None else out
+    _check(_fop_lib().hoszp_fop_add(_dev_ptr(x), _dev_ptr(y), _dev_ptr(out), x.numel(),
+                                    _stream_ptr(stream)), "fop_add")
+    return out
+
+
+def fop_moments(x, variance: bool, out=None, stream=None, ctx=None):
+    torch = _torch()
+    ctx = _ctx(ctx, x)
+    out = torch.zeros(1, dtype=torch.float64, device=x.device) if out is None else out
+    _check(_fop_lib().hoszp_fop_moments(ctx.handle, _dev_ptr(x), x.numel(), 1 if variance else 0,
+                                        _dev_ptr(out), _stream_ptr(stream)), "fop_moments")
+    return out

@@ -349,3 +349,15 @@ int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
 }
 
 }  // extern "C"
+
+namespace hz {
+// Workspace access for the traditional-workflow helpers (baseline.cu); the
+// grid they use (SMs x 4) stays within the partials the workspace holds.
+Ws ctx_workspace(hoszp_ctx* ctx) {
+  if (ensure_ws(ctx, 1, 16) != HOSZP_OK) {
+    Ws w{};
+    return w;
+  }
+  return ctx->ws;
+}
+}  // namespace hz
