@@ -26,14 +26,17 @@
  *
  * Stream format ("R-FMT", little-endian; section order of Fig. 3):
  *   [header 64 B][rate u8 x nb][pad16][outlier i32 x nb][pad16]
- *   [sign u64 x nnc][plane u64 x R]
+ *   [sign u64 x nnc][plane u64 x R][pad16]
  *   nb  = ceil(n/64) blocks of L = 64 consecutive values (last block short),
  *   rate_b = bit length of max |delta| in block b (0 = constant block, which
  *            stores no sign word and no planes; Sec. IV-A step 3),
  *   outlier_b = quantized value of the first element of block b (Sec. IV-A step 2),
  *   sign word: bit i = 1 iff delta_i < 0 (Sec. IV-A, sign array),
  *   plane p (p < rate_b): bit i = bit p of |delta_i|, i = 0..63, delta_0 := 0.
- *   nnc = number of non-constant blocks, R = sum of rates.
+ *   nnc = number of non-constant blocks, R = sum of rates. Every section starts
+ *   on a 16-byte boundary except the plane section (8-byte aligned), and the
+ *   stream length is a multiple of 16 bytes (zero padding), so sections can be
+ *   moved with 16-byte bulk copies.
  */
 #ifndef HOSZP_H
 #define HOSZP_H

@@ -93,8 +93,10 @@ static uint64_t off_rate(void) { return ORC_HDR; }
 static uint64_t off_outlier(uint64_t nb) { return ORC_HDR + align16(nb); }
 static uint64_t off_sign(uint64_t nb) { return off_outlier(nb) + align16(4 * nb); }
 static uint64_t off_plane(uint64_t nb, uint64_t nnc) { return off_sign(nb) + 8 * nnc; }
+/* the stream ends on a 16-byte boundary (8 zero bytes after the last plane
+ * word when needed), so every section can be moved in 16-byte units */
 static uint64_t stream_size(uint64_t nb, uint64_t nnc, uint64_t R) {
-  return off_plane(nb, nnc) + 8 * R;
+  return align16(off_plane(nb, nnc) + 8 * R);
 }
 
 size_t orc_bound(uint64_t n) {

@@ -72,6 +72,11 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
     o_desc[k] = off;
     off = round_up(off + tiles * sizeof(Desc), 256);
   }
+  uint64_t o_pre[2];
+  for (int k = 0; k < 2; k++) {
+    o_pre[k] = off;
+    off = round_up(off + (tiles + 1) * 16, 256);
+  }
   const uint64_t o_part = off;
   off = round_up(off + grid * sizeof(Partial), 256);
   const uint64_t o_range = off;
@@ -112,6 +117,7 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
   w.hdr = (hoszp_header*)(base + o_hdr);
   for (int k = 0; k < NCHAIN; k++) w.desc[k] = (Desc*)(base + o_desc[k]);
   w.max_tiles = tiles;
+  for (int k = 0; k < 2; k++) w.pre[k] = (unsigned long long*)(base + o_pre[k]);
   w.partials = (Partial*)(base + o_part);
   w.range_part = (float*)(base + o_range);
   w.max_grid = grid;

@@ -3,6 +3,7 @@
 // blockwise fixed-length bit-plane encoding, stream layout of Fig. 3).
 #include <cfloat>
 
+#include "hz_decode.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -94,15 +95,38 @@ cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double re
 }
 
 // ---------------------------------------------------------------- compression
+// Pipeline per CTA: the next tiles' 16 KB of input are bulk-copied into a
+// shared-memory ring while the current tile is quantized and encoded into an
+// output stage; a tile's place in the stream (look-back over the tiles before
+// it) is resolved one tile later, so the look-back latency overlaps compute.
+constexpr int CMP_STAGES = 3;
+
+struct InX {
+  float v[TILE_VALUES];
+};
+
+__device__ __forceinline__ void issue_x(InX* s, uint64_t* bar, const float* x, uint64_t n,
+                                        uint64_t t) {
+  const uint64_t first = (uint64_t)TILE_VALUES * t;
+  const uint64_t cnt = umin64(TILE_VALUES, n - first);
+  const unsigned bytes = (unsigned)((cnt * 4) & ~15ull);
+  fence_proxy_async();
+  mbar_expect_tx(bar, bytes);
+  if (bytes) bulk_g2s(s->v, x + first, bytes, bar);
+}
+
 __global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, uint64_t n,
                                                   const uint32_t dims0, const uint32_t dims1,
                                                   const uint32_t dims2, const uint32_t ndims,
                                                   float eps_q_abs, double eps_abs, int rel,
                                                   uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
-  __shared__ uint8_t s_rate[TILE];
+  extern __shared__ __align__(16) uint8_t dyn[];
+  InX* ins = reinterpret_cast<InX*>(dyn);
+  OutStage* outs = reinterpret_cast<OutStage*>(dyn + CMP_STAGES * sizeof(InX));
+  __shared__ uint64_t bars[CMP_STAGES];
+  __shared__ unsigned long long s_tiles[CMP_STAGES];
   __shared__ TileScan ts;
   __shared__ unsigned long long s_pre[2];
-  __shared__ unsigned int s_tile;
   __shared__ unsigned long long s_epoch;
   __shared__ unsigned int s_qmax[CTA / 32];
   const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
@@ -114,8 +138,6 @@ __global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, u
   Q.e = e;
   Q.e2 = 2.0f * e;
   Q.r = (e >= FLT_MIN) ? __double2float_rn(1.0 / (double)Q.e2) : 0.0f;
-  const uint64_t o_out = off_outlier(nb), o_sign = off_sign(nb);
-  int* const outlier = reinterpret_cast<int*>(out + o_out);
 
   if (tid == 0) {
     s_epoch = launch_epoch(ws);
@@ -137,35 +159,54 @@ __global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, u
       H->block = HOSZP_BLOCK;
     }
   }
+  init_bars<CMP_STAGES>(bars);
+  if (tid == 0) {
+    for (int k = 0; k < CMP_STAGES - 1; k++) {
+      const unsigned long long t = atomicAdd(&ws.sync->ticket, 1u);
+      s_tiles[k] = t;
+      if (t < ntiles) issue_x(&ins[k], &bars[k], x, n, t);
+    }
+  }
   __syncthreads();
   const unsigned long long epoch = s_epoch;
   uint32_t qmax = 0;
   int bad = 0;
-
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
+  uint64_t i = 0;
+  for (;; i++) {
+    const unsigned long long tile = s_tiles[i % CMP_STAGES];
     if (tile >= ntiles) break;
+    if (tid == 0) {
+      const int sn = (int)((i + CMP_STAGES - 1) % CMP_STAGES);
+      const unsigned long long tn = atomicAdd(&ws.sync->ticket, 1u);
+      s_tiles[sn] = tn;
+      if (tn < ntiles) issue_x(&ins[sn], &bars[sn], x, n, tn);
+    }
+    InX& in = ins[i % CMP_STAGES];
+    mbar_wait(&bars[i % CMP_STAGES], (unsigned)((i / CMP_STAGES) & 1), ws.status);
     const uint64_t b = tile * TILE + g;
-    const uint64_t i0 = b * L + 8 * j;
+    const uint64_t first = (uint64_t)TILE_VALUES * tile;
+    const uint64_t copied = umin64(TILE_VALUES, n - first) & ~3ull;
+    const int o0 = 64 * g + 8 * j;  // offset in the tile
+    const uint64_t i0 = first + o0;
     float v[8];
-    if (i0 + 8 <= n) {
-      float4 a = __ldg(reinterpret_cast<const float4*>(x + i0));
-      float4 c = __ldg(reinterpret_cast<const float4*>(x + i0 + 4));
+    if ((uint64_t)o0 + 8 <= copied) {
+      const float4 a = *reinterpret_cast<const float4*>(&in.v[o0]);
+      const float4 c = *reinterpret_cast<const float4*>(&in.v[o0 + 4]);
       v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
       v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
     } else {
 #pragma unroll
-      for (int t = 0; t < 8; t++) v[t] = (i0 + t < n) ? __ldg(x + i0 + t) : 0.0f;
+      for (int t = 0; t < 8; t++) {
+        const uint64_t o = (uint64_t)o0 + t;
+        v[t] = (o < copied) ? in.v[o] : ((i0 + t < n) ? __ldg(x + i0 + t) : 0.0f);
+      }
     }
     int q[8];
 #pragma unroll
     for (int t = 0; t < 8; t++) {
       q[t] = quantize(v[t], Q, bad);
       if (i0 + t >= n) q[t] = 0;
-      uint32_t a = (uint32_t)abs(q[t]);
-      qmax = max(qmax, a);
+      qmax = max(qmax, (uint32_t)abs(q[t]));
     }
     // Eq. 4 inside the block: delta_i = q_i - q_{i-1}, delta_0 := 0 (outlier)
     const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
@@ -179,34 +220,18 @@ __global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, u
       sb |= (d < 0 ? 1u : 0u) << t;
     }
     const int rate = octet_rate(mag);
-    if (j == 0) s_rate[g] = (b < nb) ? (uint8_t)rate : 0;
-    __syncthreads();
-    tile_scan(s_rate, &ts);
-    tile_prefix(ws.desc[0], (int64_t)tile, epoch, ws.status, ts.agg_nc, ts.agg_r, 0, s_pre);
-    __syncthreads();
-    const uint64_t NC = s_pre[0], RR = s_pre[1];
-    const int r = (b < nb) ? rate : 0;
-    if (b < nb && j == 0) {
-      out[HOSZP_HEADER_BYTES + b] = (uint8_t)rate;
-      outlier[b] = q[0];
-    }
-    const uint64_t si = NC + ts.nc_excl[g];
-    const uint64_t pi = RR + ts.r_excl[g];
-    if (r > 0) {
-      const uint64_t pos = o_sign + 8 * si + j;
-      if (pos < cap) out[pos] = (uint8_t)sb;
-      else bad = HOSZP_ERR_CAPACITY;
-    }
-    const int kmax = __reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-    const uint64_t lim = (pi < ws.staging_words) ? ws.staging_words - pi : 0;
-    if (kmax > 0) encode_planes(mag, r, kmax, j, ws.staging + pi, lim);
-    if (r > 0 && pi + r > ws.staging_words) bad = HOSZP_ERR_CAPACITY;
-    if (tile == ntiles - 1 && tid == 0) {
-      ws.totals[0] = NC + ts.agg_nc;
-      ws.totals[1] = RR + ts.agg_r;
-    }
+    OutStage& os = outs[i & 1];
+    stage_encode(os, &ts, mag, sb, rate, q[0], b < nb, g, j);
+    if (tid == 0) os.tile = tile;
+    publish_agg(ws.desc[0], tile, epoch, os);
+    if (i > 0)
+      stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, nb, out, cap, ws.staging,
+                  ws.staging_words, ntiles, ws.totals, s_pre, bad);
     __syncthreads();
   }
+  if (i > 0)
+    stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, nb, out, cap, ws.staging,
+                ws.staging_words, ntiles, ws.totals, s_pre, bad);
   // epilogue: max |q| for the header's qbound, first error, launch bookkeeping
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
@@ -223,8 +248,14 @@ __global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, u
 cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const uint32_t dims[3],
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
                             uint64_t cap, Ws ws) {
-  k_compress<<<persistent_grid(k_compress, CTA, lc.grid), CTA, 0, lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs,
-                                             eps_abs, rel ? 1 : 0, out, cap, ws);
+  const size_t smem = CMP_STAGES * sizeof(InX) + 2 * sizeof(OutStage);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_compress<<<persistent_grid(k_compress, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
+      x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs, rel ? 1 : 0, out, cap, ws);
   return cudaGetLastError();
 }
 

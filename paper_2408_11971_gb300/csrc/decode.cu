@@ -9,35 +9,29 @@
 namespace hz {
 
 // ---------------------------------------------------------------- decompression
+constexpr int DEC_STAGES = 3;
+
 __global__ void __launch_bounds__(CTA) k_decompress(const uint8_t* __restrict__ c, uint64_t c_bytes,
                                                     float* __restrict__ x, uint64_t n_expect,
+                                                    const unsigned long long* __restrict__ pre,
                                                     Ws ws) {
-  __shared__ InTile s;
-  __shared__ unsigned int s_tile;
-  __shared__ unsigned long long s_epoch;
+  extern __shared__ __align__(16) uint8_t dyn[];
+  InStage* stages = reinterpret_cast<InStage*>(dyn);
+  __shared__ uint64_t bars[DEC_STAGES];
+  __shared__ TileScan ts;
   const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
   const Info h = parse_header(c, c_bytes);
   int bad = 0;
   uint64_t ntiles = 0;
   if (!h.ok) bad = HOSZP_ERR_FORMAT;
   else if (h.n != n_expect) bad = HOSZP_ERR_MISMATCH;
-  else ntiles = ntiles_of(h.nb);
+  else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
   const float e2 = 2.0f * h.eps_q;
   const bool small = h.qbound < (1u << 22);
-  if (tid == 0) s_epoch = launch_epoch(ws);
-  __syncthreads();
-  const unsigned long long epoch = s_epoch;
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= ntiles) break;
-    in_tile_begin(c, h, tile, &s, ws.desc[0], epoch, ws.status, 0, bad);
-    __syncthreads();
-    if (tile == ntiles - 1 && tid == 0 &&
-        (s.pre[0] + s.ts.agg_nc != h.nnc || s.pre[1] + s.ts.agg_r != h.R))
-      bad = HOSZP_ERR_FORMAT;
-    const BlockRef br = block_ref(c, h, tile, &s, g, j, bad);
+  init_bars<DEC_STAGES>(bars);
+  consume_tiles<DEC_STAGES>(c, h, ntiles, pre, stages, bars, &ts, ws.status, bad,
+                            [&](uint64_t tile, const InStage& sg, const TileScan& sc) {
+    const BlockRef br = block_ref(sg, sc, h, tile, g, j);
     const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
     int d[8], q[8];
     octet_deltas(br, kmax, j, d);
@@ -55,15 +49,22 @@ __global__ void __launch_bounds__(CTA) k_decompress(const uint8_t* __restrict__ 
       for (int t = 0; t < 8; t++)
         if (i0 + t < h.n) x[i0 + t] = v[t];
     }
-    __syncthreads();
-  }
+  });
   if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
                               uint64_t n, Ws ws) {
-  k_decompress<<<persistent_grid(k_decompress, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, x, n, ws);
+  cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
+  if (e != cudaSuccess) return e;
+  const size_t smem = DEC_STAGES * sizeof(InStage);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_decompress<<<persistent_grid(k_decompress, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
+      c, c_bytes, x, n, ws.pre[0], ws);
   return cudaGetLastError();
 }
 
@@ -119,12 +120,17 @@ __device__ __forceinline__ double u256_to_double(const U256& a) {
   return d;
 }
 
+constexpr int MOM_STAGES = 3;
+
 template <bool VAR>
 __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, uint64_t c_bytes,
-                                                 double* result, Ws ws) {
-  __shared__ InTile s;
-  __shared__ unsigned int s_tile;
-  __shared__ unsigned long long s_epoch;
+                                                 double* result,
+                                                 const unsigned long long* __restrict__ pre,
+                                                 Ws ws) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  InStage* stages = reinterpret_cast<InStage*>(dyn);
+  __shared__ uint64_t bars[MOM_STAGES];
+  __shared__ TileScan ts;
   __shared__ long long s_s1[CTA / 32];
   __shared__ U128 s_s2[CTA / 32];
   const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
@@ -132,23 +138,13 @@ __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, 
   int bad = 0;
   uint64_t ntiles = 0;
   if (!h.ok) bad = HOSZP_ERR_FORMAT;
-  else ntiles = ntiles_of(h.nb);
-  if (tid == 0) s_epoch = launch_epoch(ws);
-  __syncthreads();
-  const unsigned long long epoch = s_epoch;
+  else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
   long long s1 = 0;  // per thread: |q| <= 2^30, far fewer than 2^32 values per thread
   U128 s2 = {0, 0};
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= ntiles) break;
-    in_tile_begin(c, h, tile, &s, ws.desc[0], epoch, ws.status, 0, bad);
-    __syncthreads();
-    if (tile == ntiles - 1 && tid == 0 &&
-        (s.pre[0] + s.ts.agg_nc != h.nnc || s.pre[1] + s.ts.agg_r != h.R))
-      bad = HOSZP_ERR_FORMAT;
-    const BlockRef br = block_ref(c, h, tile, &s, g, j, bad);
+  init_bars<MOM_STAGES>(bars);
+  consume_tiles<MOM_STAGES>(c, h, ntiles, pre, stages, bars, &ts, ws.status, bad,
+                            [&](uint64_t tile, const InStage& sg, const TileScan& sc) {
+    const BlockRef br = block_ref(sg, sc, h, tile, g, j);
     const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
     int d[8], q[8];
     octet_deltas(br, kmax, j, d);
@@ -160,8 +156,7 @@ __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, 
         if (VAR) add_u64(s2, (unsigned long long)((long long)q[t] * (long long)q[t]));
       }
     }
-    __syncthreads();
-  }
+  });
   // CTA reduction -> per-CTA partial
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -230,13 +225,26 @@ __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, 
   }
 }
 
+template <bool VAR>
+static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
+                                    double* result, Ws ws) {
+  const size_t smem = MOM_STAGES * sizeof(InStage);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_moments<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_moments<VAR><<<persistent_grid(k_moments<VAR>, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
+      c, c_bytes, result, ws.pre[0], ws);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
                            bool variance, Ws ws) {
-  if (variance)
-    k_moments<true><<<persistent_grid(k_moments<true>, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, result, ws);
-  else
-    k_moments<false><<<persistent_grid(k_moments<false>, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, result, ws);
-  return cudaGetLastError();
+  cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
+  if (e != cudaSuccess) return e;
+  return variance ? launch_moments_t<true>(lc, c, c_bytes, result, ws)
+                  : launch_moments_t<false>(lc, c, c_bytes, result, ws);
 }
 
 }  // namespace hz

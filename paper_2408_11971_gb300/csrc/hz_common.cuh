@@ -27,13 +27,14 @@ constexpr int MAX_RATE = 31;
 constexpr int NCHAIN = 3;    // look-back chains per launch (add uses 2 inputs + 1 output)
 
 // ---------------------------------------------------------------- stream layout (Fig. 3)
+HZ_HD uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 HZ_HD uint64_t align16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
 HZ_HD uint64_t nblocks(uint64_t n) { return (n + L - 1) / L; }
 HZ_HD uint64_t off_outlier(uint64_t nb) { return HOSZP_HEADER_BYTES + align16(nb); }
 HZ_HD uint64_t off_sign(uint64_t nb) { return off_outlier(nb) + align16(4 * nb); }
 HZ_HD uint64_t off_plane(uint64_t nb, uint64_t nnc) { return off_sign(nb) + 8 * nnc; }
 HZ_HD uint64_t stream_bytes(uint64_t nb, uint64_t nnc, uint64_t R) {
-  return off_plane(nb, nnc) + 8 * R;
+  return align16(off_plane(nb, nnc) + 8 * R);  // zero padding to 16 bytes
 }
 HZ_HD uint64_t ntiles_of(uint64_t nb) { return (nb + TILE - 1) / TILE; }
 
@@ -131,6 +132,7 @@ struct Ws {
   uint64_t* staging;  // plane words of a produced stream before placement
   uint64_t staging_words;
   hoszp_header* hdr;  // header of the stream being produced (filled in by the producer)
+  unsigned long long* pre[2];  // per-tile (nc, r) prefixes of up to two input streams
 };
 
 // Tile hand-out and launch bookkeeping. Every CTA calls begin() once, next()

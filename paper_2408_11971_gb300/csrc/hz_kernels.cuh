@@ -23,6 +23,9 @@ cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const 
 // workspace by the producer, checks the capacity, copies the staged planes
 // behind the sign section and writes the header and the size word.
 cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
+// scan.cu: per-tile (nc, r) exclusive prefixes of a stream's rates into pre[]
+cudaError_t launch_scan(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
+                        unsigned long long* pre, Ws ws);
 // decode.cu
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
                               uint64_t n, Ws ws);
@@ -40,9 +43,9 @@ cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, con
 
 // Persistent grid: SMs x resident CTAs per SM of `kernel` (capped at 8).
 template <typename K>
-inline int persistent_grid(K kernel, int threads, int num_sms) {
+inline int persistent_grid(K kernel, int threads, int num_sms, size_t smem = 0) {
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     per = 1;
   }

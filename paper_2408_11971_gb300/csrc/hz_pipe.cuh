@@ -1,0 +1,199 @@
+// hz_pipe.cuh — tile pipelines: 1-D TMA bulk copies (cp.async.bulk) of a
+// compressed tile into a shared-memory ring completed on mbarriers, and the
+// shared-memory output stage of a produced tile.
+#pragma once
+#include <cstddef>
+
+#include "hz_common.cuh"
+
+namespace hz {
+
+// ---------------------------------------------------------------- mbarrier / bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: after ~a second of polling the status word gets TIMEOUT and the
+// wait gives up (the data in the stage is then not used for a valid result).
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* st) {
+  long long spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++spins > (1ll << 24)) {
+      set_status(st, HOSZP_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// global -> shared bulk copy of `bytes` (multiple of 16, both ends 16-aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------- input stage
+// One tile of an input stream in shared memory. Sign and plane words are
+// copied from the 16-byte-aligned addresses around the tile's words; sbase and
+// pbase give the index of the tile's first word inside sign[] and plane[].
+struct __align__(16) InStage {
+  uint64_t plane[TILE * MAX_RATE + 2];
+  uint64_t sign[TILE + 2];
+  int outlier[TILE];
+  uint8_t rate[TILE];
+  uint32_t sbase, pbase;
+};
+static_assert(sizeof(uint64_t) * (TILE * MAX_RATE + 2) % 16 == 0, "plane[] keeps alignment");
+static_assert(sizeof(uint64_t) * (TILE + 2) % 16 == 0, "sign[] keeps alignment");
+static_assert(sizeof(InStage) % 16 == 0, "ring stages must stay 16-byte aligned (bulk copies)");
+static_assert(offsetof(InStage, sign) % 16 == 0 && offsetof(InStage, outlier) % 16 == 0 &&
+                  offsetof(InStage, rate) % 16 == 0,
+              "bulk-copy destinations are 16-byte aligned");
+
+// Issued by one thread: bulk-copy tile `t` of stream `c` into `s`, completing
+// on `bar`. pre[2t], pre[2t+1] = exclusive prefix (non-constant blocks, rate
+// sum) of tile t (from the rate pre-scan); pre[2t+2], pre[2t+3] those of t+1.
+__device__ __forceinline__ void issue_in_tile(InStage* s, uint64_t* bar, const uint8_t* c,
+                                              const Info& h, uint64_t t,
+                                              const unsigned long long* pre) {
+  const unsigned long long NC0 = pre[2 * t], R0 = pre[2 * t + 1];
+  const unsigned long long NC1 = pre[2 * t + 2], R1 = pre[2 * t + 3];
+  const uint64_t rate_end = align16(h.nb), out_end = align16(4 * h.nb);
+  const unsigned rb = (unsigned)umin64(TILE, rate_end - TILE * t);
+  const unsigned ob = (unsigned)umin64(4 * TILE, out_end - 4 * TILE * t);
+  const uint64_t sa = h.o_sign + 8 * NC0, se = h.o_sign + 8 * NC1;
+  const uint64_t sa16 = sa & ~15ull, se16 = align16(se);
+  const uint64_t pa = h.o_plane + 8 * R0, pe = h.o_plane + 8 * R1;
+  const uint64_t pa16 = pa & ~15ull, pe16 = align16(pe);
+  const unsigned sbytes = (NC1 > NC0) ? (unsigned)(se16 - sa16) : 0u;
+  const unsigned pbytes = (R1 > R0) ? (unsigned)(pe16 - pa16) : 0u;
+  s->sbase = (uint32_t)((sa - sa16) >> 3);
+  s->pbase = (uint32_t)((pa - pa16) >> 3);
+  fence_proxy_async();
+  mbar_expect_tx(bar, rb + ob + sbytes + pbytes);
+  bulk_g2s(s->rate, c + HOSZP_HEADER_BYTES + TILE * t, rb, bar);
+  bulk_g2s(s->outlier, c + h.o_out + 4 * TILE * t, ob, bar);
+  if (sbytes) bulk_g2s(s->sign, c + sa16, sbytes, bar);
+  if (pbytes) bulk_g2s(s->plane, c + pa16, pbytes, bar);
+}
+
+// ---------------------------------------------------------------- output stage
+// A produced tile before its place in the stream is known: rates, outliers,
+// and the tile's sign and plane words in order.
+struct __align__(16) OutStage {
+  uint64_t plane[TILE * MAX_RATE];
+  uint64_t sign[TILE];
+  int outlier[TILE];
+  uint8_t rate[TILE];
+  unsigned int agg_nc, agg_r;
+  unsigned long long tile;
+};
+static_assert(sizeof(OutStage) % 16 == 0, "output stages stay 16-byte aligned");
+
+}  // namespace hz
+
+namespace hz {
+
+// ---------------------------------------------------------------- producer helpers
+// Encode lane j's octet (magnitudes, sign byte) of block g into the output
+// stage: rates and outliers by block, sign words and planes packed in block
+// order. Whole CTA (contains barriers); ts is scratch for the rate scan.
+__device__ __forceinline__ void stage_encode(OutStage& o, TileScan* ts, const uint32_t mag[8],
+                                             uint32_t sb, int rate, int outlier, bool valid,
+                                             int g, int j) {
+  if (j == 0) {
+    o.rate[g] = valid ? (uint8_t)rate : 0;
+    o.outlier[g] = outlier;
+  }
+  __syncthreads();
+  tile_scan(o.rate, ts);
+  const int r = o.rate[g];
+  if (r > 0) reinterpret_cast<uint8_t*>(o.sign + ts->nc_excl[g])[j] = (uint8_t)sb;
+  const int kmax = __reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+  if (kmax > 0) encode_planes(mag, r, kmax, j, o.plane + ts->r_excl[g], (uint64_t)r);
+  if (threadIdx.x == 0) {
+    o.agg_nc = ts->agg_nc;
+    o.agg_r = ts->agg_r;
+  }
+}
+
+__device__ __forceinline__ void publish_agg(Desc* d, uint64_t tile, unsigned long long epoch,
+                                            const OutStage& o) {
+  if (threadIdx.x == 0) {
+    const unsigned long long agg = ((unsigned long long)o.agg_nc << 32) | o.agg_r;
+    publish(d, (int64_t)tile, epoch, tile == 0 ? 2 : 1, agg, o.agg_nc, o.agg_r);
+  }
+}
+
+// Warp 0 resolves the exclusive prefix of the staged tile and publishes its
+// inclusive prefix; then the whole CTA writes the tile to the stream:
+// rates and outliers at their block positions, sign words from index NC of
+// the sign section, planes from index R of `planes_dst` (the plane section
+// or the workspace). Bounds: capacity and staging size, errors into `bad`.
+__device__ __forceinline__ void stage_flush(const OutStage& o, Desc* d, unsigned long long epoch,
+                                            int* st, uint64_t nb, uint8_t* out, uint64_t cap,
+                                            uint64_t* planes_dst, uint64_t planes_limit,
+                                            uint64_t ntiles, unsigned long long* totals,
+                                            unsigned long long* s_pre, int& bad) {
+  const uint64_t tile = o.tile;
+  if (threadIdx.x < 32) {
+    unsigned long long pnc = 0, pr = 0;
+    if (tile > 0) {
+      lookback(d, (int64_t)tile, epoch, st, pnc, pr);
+      if (threadIdx.x == 0) {
+        const unsigned long long agg = ((unsigned long long)o.agg_nc << 32) | o.agg_r;
+        publish(d, (int64_t)tile, epoch, 2, agg, pnc + o.agg_nc, pr + o.agg_r);
+      }
+    }
+    if (threadIdx.x == 0) {
+      s_pre[0] = pnc;
+      s_pre[1] = pr;
+      if (tile == ntiles - 1) {
+        totals[0] = pnc + o.agg_nc;
+        totals[1] = pr + o.agg_r;
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t NC = s_pre[0], RR = s_pre[1];
+  const uint64_t nbt = umin64(TILE, nb - TILE * tile);
+  const int tid = threadIdx.x;
+  if ((uint64_t)tid < nbt) {
+    out[HOSZP_HEADER_BYTES + TILE * tile + tid] = o.rate[tid];
+    reinterpret_cast<int*>(out + off_outlier(nb))[TILE * tile + tid] = o.outlier[tid];
+  }
+  const uint64_t os = off_sign(nb);
+  if (os + 8 * (NC + o.agg_nc) > cap || RR + o.agg_r > planes_limit) {
+    if (tid == 0) bad = HOSZP_ERR_CAPACITY;
+    return;
+  }
+  uint64_t* sdst = reinterpret_cast<uint64_t*>(out + os) + NC;
+  for (unsigned int i = tid; i < o.agg_nc; i += blockDim.x) sdst[i] = o.sign[i];
+  uint64_t* pdst = planes_dst + RR;
+  for (unsigned int i = tid; i < o.agg_r; i += blockDim.x) pdst[i] = o.plane[i];
+}
+
+}  // namespace hz

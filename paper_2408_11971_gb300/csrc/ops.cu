@@ -171,57 +171,7 @@ cudaError_t launch_add_scalar(const Launch& lc, const uint8_t* c, uint64_t c_byt
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- shared re-encode step
-// Octet of new deltas (|d| < 2^31) -> rate, sign byte, planes; the tile scan
-// and the look-back on the output chain place them. Whole CTA.
-struct OutTile {
-  uint8_t rate[TILE];
-  TileScan ts;
-  unsigned long long pre[2];
-};
-
-__device__ __forceinline__ void encode_tile(uint64_t tile, uint64_t ntiles, uint64_t nb,
-                                            const int d[8], int outlier, int g, int j,
-                                            uint8_t* __restrict__ out, uint64_t cap, OutTile* s,
-                                            Desc* chain, unsigned long long epoch, const Ws& ws,
-                                            int& bad) {
-  const uint64_t b = tile * TILE + g;
-  uint32_t mag[8];
-  uint32_t sb = 0;
-#pragma unroll
-  for (int t = 0; t < 8; t++) {
-    mag[t] = (uint32_t)abs(d[t]);
-    sb |= (d[t] < 0 ? 1u : 0u) << t;
-  }
-  const int rate = octet_rate(mag);
-  if (j == 0) s->rate[g] = (b < nb) ? (uint8_t)rate : 0;
-  __syncthreads();
-  tile_scan(s->rate, &s->ts);
-  tile_prefix(chain, (int64_t)tile, epoch, ws.status, s->ts.agg_nc, s->ts.agg_r, 0, s->pre);
-  __syncthreads();
-  const uint64_t NC = s->pre[0], RR = s->pre[1];
-  const int r = (b < nb) ? rate : 0;
-  if (b < nb && j == 0) {
-    out[HOSZP_HEADER_BYTES + b] = (uint8_t)rate;
-    reinterpret_cast<int*>(out + off_outlier(nb))[b] = outlier;
-  }
-  const uint64_t si = NC + s->ts.nc_excl[g];
-  const uint64_t pi = RR + s->ts.r_excl[g];
-  if (r > 0) {
-    const uint64_t pos = off_sign(nb) + 8 * si + j;
-    if (pos < cap) out[pos] = (uint8_t)sb;
-    else bad = HOSZP_ERR_CAPACITY;
-  }
-  const int kmax = __reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-  const uint64_t lim = (pi < ws.staging_words) ? ws.staging_words - pi : 0;
-  if (kmax > 0) encode_planes(mag, r, kmax, j, ws.staging + pi, lim);
-  if (r > 0 && pi + r > ws.staging_words) bad = HOSZP_ERR_CAPACITY;
-  if (tile == ntiles - 1 && threadIdx.x == 0) {
-    ws.totals[0] = NC + s->ts.agg_nc;
-    ws.totals[1] = RR + s->ts.agg_r;
-  }
-}
-
+// ---------------------------------------------------------------- shared pieces
 __device__ __forceinline__ void write_template(const Info& h, uint32_t qbound_fixed,
                                                const Ws& ws) {
   hoszp_header* H = ws.hdr;
@@ -253,13 +203,34 @@ __device__ __forceinline__ void reduce_qmax(uint32_t qmax, const Ws& ws) {
   }
 }
 
+// magnitudes and sign byte of an octet of deltas
+__device__ __forceinline__ void octet_mag_sign(const int d[8], uint32_t mag[8], uint32_t& sb) {
+  sb = 0;
+#pragma unroll
+  for (int t = 0; t < 8; t++) {
+    mag[t] = (uint32_t)abs(d[t]);
+    sb |= (d[t] < 0 ? 1u : 0u) << t;
+  }
+}
+
 // ---------------------------------------------------------------- scalar multiplication
+// Input tiles arrive through a bulk-copy ring (located by the rate pre-scan);
+// each is decoded to q (workflow 3), requantized, Lorenzo + BF re-encoded into
+// an output stage, and written one tile later once its place is known.
+constexpr int MUL_STAGES = 2;
+
 __global__ void __launch_bounds__(CTA) k_mul_scalar(const uint8_t* __restrict__ c, uint64_t c_bytes,
                                                     double s, uint8_t* __restrict__ out,
-                                                    uint64_t cap, Ws ws) {
-  __shared__ InTile sin_;
-  __shared__ OutTile sout;
-  __shared__ unsigned int s_tile;
+                                                    uint64_t cap,
+                                                    const unsigned long long* __restrict__ pre,
+                                                    Ws ws) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  InStage* ins = reinterpret_cast<InStage*>(dyn);
+  OutStage* outs = reinterpret_cast<OutStage*>(dyn + MUL_STAGES * sizeof(InStage));
+  __shared__ uint64_t bars[MUL_STAGES];
+  __shared__ unsigned long long s_tiles[MUL_STAGES];
+  __shared__ TileScan ts_in, ts_out;
+  __shared__ unsigned long long s_pre[2];
   __shared__ unsigned long long s_epoch;
   __shared__ long long s_rho;
   __shared__ int s_ok;
@@ -282,23 +253,34 @@ __global__ void __launch_bounds__(CTA) k_mul_scalar(const uint8_t* __restrict__ 
     s_rho = rho;
     if (blockIdx.x == 0) write_template(h, 0, ws);
   }
+  init_bars<MUL_STAGES>(bars);
+  const uint64_t ntiles = (s_ok && prescan_ok(h, pre, ws.max_tiles)) ? ntiles_of(h.nb) : 0;
+  const MulPlan mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho);
+  if (tid == 0) {
+    for (int k = 0; k < MUL_STAGES - 1; k++) {
+      const unsigned long long t = atomicAdd(&ws.sync->ticket, 1u);
+      s_tiles[k] = t;
+      if (t < ntiles) issue_in_tile(&ins[k], &bars[k], c, h, t, pre);
+    }
+  }
   __syncthreads();
   const unsigned long long epoch = s_epoch;
-  const uint64_t ntiles = s_ok ? ntiles_of(h.nb) : 0;
-  const MulPlan mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho);
   uint32_t qmax = 0;
   bool ovf = false;
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
+  uint64_t i = 0;
+  for (;; i++) {
+    const unsigned long long tile = s_tiles[i % MUL_STAGES];
     if (tile >= ntiles) break;
-    in_tile_begin(c, h, tile, &sin_, ws.desc[0], epoch, ws.status, 0, bad);
-    __syncthreads();
-    if (tile == ntiles - 1 && tid == 0 &&
-        (sin_.pre[0] + sin_.ts.agg_nc != h.nnc || sin_.pre[1] + sin_.ts.agg_r != h.R))
-      bad = HOSZP_ERR_FORMAT;
-    const BlockRef br = block_ref(c, h, tile, &sin_, g, j, bad);
+    if (tid == 0) {
+      const int sn = (int)((i + MUL_STAGES - 1) % MUL_STAGES);
+      const unsigned long long tn = atomicAdd(&ws.sync->ticket, 1u);
+      s_tiles[sn] = tn;
+      if (tn < ntiles) issue_in_tile(&ins[sn], &bars[sn], c, h, tn, pre);
+    }
+    InStage& sg = ins[i % MUL_STAGES];
+    mbar_wait(&bars[i % MUL_STAGES], (unsigned)((i / MUL_STAGES) & 1), ws.status);
+    stage_begin(sg, &ts_in, h, tile, bad);
+    const BlockRef br = block_ref(sg, ts_in, h, tile, g, j);
     const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
     int d[8], q[8];
     octet_deltas(br, kmax, j, d);
@@ -314,13 +296,24 @@ __global__ void __launch_bounds__(CTA) k_mul_scalar(const uint8_t* __restrict__ 
     int nd[8];
 #pragma unroll
     for (int t = 0; t < 8; t++) {
-      int v = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
+      const int v = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
       nd[t] = (8 * j + t < br.len) ? v : 0;
     }
-    encode_tile(tile, ntiles, h.nb, nd, outlier, g, j, out, cap, &sout, ws.desc[1], epoch, ws,
-                bad);
+    uint32_t mag[8], sb;
+    octet_mag_sign(nd, mag, sb);
+    const int rate = octet_rate(mag);
+    OutStage& os = outs[i & 1];
+    stage_encode(os, &ts_out, mag, sb, rate, outlier, tile * TILE + g < h.nb, g, j);
+    if (tid == 0) os.tile = tile;
+    publish_agg(ws.desc[0], tile, epoch, os);
+    if (i > 0)
+      stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, h.nb, out, cap, ws.staging,
+                  ws.staging_words, ntiles, ws.totals, s_pre, bad);
     __syncthreads();
   }
+  if (i > 0)
+    stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, h.nb, out, cap, ws.staging,
+                ws.staging_words, ntiles, ws.totals, s_pre, bad);
   if (ovf) bad = HOSZP_ERR_OVERFLOW;
   reduce_qmax(qmax, ws);
   if (bad) set_status(ws.status, bad);
@@ -329,17 +322,37 @@ __global__ void __launch_bounds__(CTA) k_mul_scalar(const uint8_t* __restrict__ 
 
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               uint8_t* out, uint64_t cap, Ws ws) {
-  k_mul_scalar<<<persistent_grid(k_mul_scalar, CTA, lc.grid), CTA, 0, lc.stream>>>(c, c_bytes, s, out, cap, ws);
+  cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
+  if (e != cudaSuccess) return e;
+  const size_t smem = MUL_STAGES * sizeof(InStage) + 2 * sizeof(OutStage);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mul_scalar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_mul_scalar<<<persistent_grid(k_mul_scalar, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
+      c, c_bytes, s, out, cap, ws.pre[0], ws);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- element-wise addition
-__global__ void __launch_bounds__(CTA) k_add(const uint8_t* __restrict__ a, uint64_t a_bytes,
+// Workflow 2: both streams' tiles arrive through bulk-copy rings; the deltas
+// are decoded (no inverse Lorenzo), added, and BF re-encoded.
+constexpr int ADD_STAGES = 2;
+
+__global__ void __launch_bounds__(CTA, 2) k_add(const uint8_t* __restrict__ a, uint64_t a_bytes,
                                              const uint8_t* __restrict__ b, uint64_t b_bytes,
-                                             uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
-  __shared__ InTile sa, sb;
-  __shared__ OutTile sout;
-  __shared__ unsigned int s_tile;
+                                             uint8_t* __restrict__ out, uint64_t cap,
+                                             const unsigned long long* __restrict__ pre_a,
+                                             const unsigned long long* __restrict__ pre_b, Ws ws) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  InStage* ina = reinterpret_cast<InStage*>(dyn);
+  InStage* inb = ina + ADD_STAGES;
+  OutStage* outs = reinterpret_cast<OutStage*>(dyn + 2 * ADD_STAGES * sizeof(InStage));
+  __shared__ uint64_t bars_a[ADD_STAGES], bars_b[ADD_STAGES];
+  __shared__ unsigned long long s_tiles[ADD_STAGES];
+  __shared__ TileScan ts_a, ts_b, ts_out;
+  __shared__ unsigned long long s_pre[2];
   __shared__ unsigned long long s_epoch;
   __shared__ int s_ok;
   const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
@@ -364,61 +377,92 @@ __global__ void __launch_bounds__(CTA) k_add(const uint8_t* __restrict__ a, uint
       if (ok) atomicMax(&ws.totals[2], (unsigned long long)(ha.qbound + hb.qbound));
     }
   }
+  if (tid < 32) {
+    if (tid == 0) {
+      for (int k = 0; k < ADD_STAGES; k++) {
+        mbar_init(&bars_a[k], 1);
+        mbar_init(&bars_b[k], 1);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  const uint64_t ntiles =
+      (s_ok && prescan_ok(ha, pre_a, ws.max_tiles) && prescan_ok(hb, pre_b, ws.max_tiles)) ? ntiles_of(ha.nb) : 0;
+  if (tid == 0) {
+    for (int k = 0; k < ADD_STAGES - 1; k++) {
+      const unsigned long long t = atomicAdd(&ws.sync->ticket, 1u);
+      s_tiles[k] = t;
+      if (t < ntiles) {
+        issue_in_tile(&ina[k], &bars_a[k], a, ha, t, pre_a);
+        issue_in_tile(&inb[k], &bars_b[k], b, hb, t, pre_b);
+      }
+    }
+  }
   __syncthreads();
   const unsigned long long epoch = s_epoch;
-  const uint64_t ntiles = s_ok ? ntiles_of(ha.nb) : 0;
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
+  uint64_t i = 0;
+  for (;; i++) {
+    const unsigned long long tile = s_tiles[i % ADD_STAGES];
     if (tile >= ntiles) break;
-    // input chains: A with warp 0, B with warp 1
-    {
-      if (tid < TILE) {
-        const uint64_t bb = tile * TILE + tid;
-        uint8_t ra = (bb < ha.nb) ? a[HOSZP_HEADER_BYTES + bb] : 0;
-        uint8_t rb = (bb < hb.nb) ? b[HOSZP_HEADER_BYTES + bb] : 0;
-        if (ra > MAX_RATE || rb > MAX_RATE) {
-          bad = HOSZP_ERR_FORMAT;
-          ra = ra > MAX_RATE ? 0 : ra;
-          rb = rb > MAX_RATE ? 0 : rb;
-        }
-        sa.rate[tid] = ra;
-        sb.rate[tid] = rb;
+    if (tid == 0) {
+      const int sn = (int)((i + ADD_STAGES - 1) % ADD_STAGES);
+      const unsigned long long tn = atomicAdd(&ws.sync->ticket, 1u);
+      s_tiles[sn] = tn;
+      if (tn < ntiles) {
+        issue_in_tile(&ina[sn], &bars_a[sn], a, ha, tn, pre_a);
+        issue_in_tile(&inb[sn], &bars_b[sn], b, hb, tn, pre_b);
       }
-      __syncthreads();
-      tile_scan(sa.rate, &sa.ts);
-      tile_scan(sb.rate, &sb.ts);
-      tile_prefix(ws.desc[0], (int64_t)tile, epoch, ws.status, sa.ts.agg_nc, sa.ts.agg_r, 0,
-                  sa.pre);
-      tile_prefix(ws.desc[1], (int64_t)tile, epoch, ws.status, sb.ts.agg_nc, sb.ts.agg_r, 1,
-                  sb.pre);
-      __syncthreads();
     }
-    if (tile == ntiles - 1 && tid == 0 &&
-        (sa.pre[0] + sa.ts.agg_nc != ha.nnc || sa.pre[1] + sa.ts.agg_r != ha.R ||
-         sb.pre[0] + sb.ts.agg_nc != hb.nnc || sb.pre[1] + sb.ts.agg_r != hb.R))
-      bad = HOSZP_ERR_FORMAT;
-    const BlockRef ba = block_ref(a, ha, tile, &sa, g, j, bad);
-    const BlockRef bbr = block_ref(b, hb, tile, &sb, g, j, bad);
-    const int ka = __reduce_max_sync(0xffffffffu, (ba.rate + 7) >> 3);
-    const int kb = __reduce_max_sync(0xffffffffu, (bbr.rate + 7) >> 3);
+    const int si = (int)(i % ADD_STAGES);
+    const unsigned par = (unsigned)((i / ADD_STAGES) & 1);
+    mbar_wait(&bars_a[si], par, ws.status);
+    mbar_wait(&bars_b[si], par, ws.status);
+    stage_begin(ina[si], &ts_a, ha, tile, bad);
+    stage_begin(inb[si], &ts_b, hb, tile, bad);
+    const BlockRef ra = block_ref(ina[si], ts_a, ha, tile, g, j);
+    const BlockRef rb = block_ref(inb[si], ts_b, hb, tile, g, j);
+    const int ka = __reduce_max_sync(0xffffffffu, (ra.rate + 7) >> 3);
+    const int kb = __reduce_max_sync(0xffffffffu, (rb.rate + 7) >> 3);
     int da[8], db[8], nd[8];
-    octet_deltas(ba, ka, j, da);
-    octet_deltas(bbr, kb, j, db);
+    octet_deltas(ra, ka, j, da);
+    octet_deltas(rb, kb, j, db);
 #pragma unroll
     for (int t = 0; t < 8; t++) nd[t] = da[t] + db[t];
-    encode_tile(tile, ntiles, ha.nb, nd, ba.outlier + bbr.outlier, g, j, out, cap, &sout,
-                ws.desc[2], epoch, ws, bad);
+    uint32_t mag[8], sb;
+    octet_mag_sign(nd, mag, sb);
+    const int rate = octet_rate(mag);
+    OutStage& os = outs[i & 1];
+    stage_encode(os, &ts_out, mag, sb, rate, ra.outlier + rb.outlier, tile * TILE + g < ha.nb, g,
+                 j);
+    if (tid == 0) os.tile = tile;
+    publish_agg(ws.desc[0], tile, epoch, os);
+    if (i > 0)
+      stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, ha.nb, out, cap, ws.staging,
+                  ws.staging_words, ntiles, ws.totals, s_pre, bad);
     __syncthreads();
   }
+  if (i > 0)
+    stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, ha.nb, out, cap, ws.staging,
+                ws.staging_words, ntiles, ws.totals, s_pre, bad);
   if (bad) set_status(ws.status, bad);
   if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, Ws ws) {
-  k_add<<<persistent_grid(k_add, CTA, lc.grid), CTA, 0, lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws);
+  cudaError_t e = launch_scan(lc, a, a_bytes, ws.pre[0], ws);
+  if (e != cudaSuccess) return e;
+  e = launch_scan(lc, b, b_bytes, ws.pre[1], ws);
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * ADD_STAGES * sizeof(InStage) + 2 * sizeof(OutStage);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_add<<<persistent_grid(k_add, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
+      a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,9 @@ __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride)
       dst[i] = src[i];
     if (blockIdx.x == 0) {
-      // zero the padding after the rate and outlier sections
+      // zero the end padding and the padding after the rate and outlier sections
+      const uint64_t end = off_plane(nb, nnc) + 8 * R;
+      if (threadIdx.x == 32 && (end & 15)) *reinterpret_cast<uint64_t*>(out + end) = 0;
       const uint64_t pr = HOSZP_HEADER_BYTES + nb, pr_end = off_outlier(nb);
       const uint64_t po = off_outlier(nb) + 4 * nb, po_end = off_sign(nb);
       if (threadIdx.x < 16 && pr + threadIdx.x < pr_end) out[pr + threadIdx.x] = 0;

@@ -24,7 +24,7 @@ def parse(c) -> dict:
     o_out = HDR + _a16(nb)
     o_sign = o_out + _a16(4 * nb)
     o_plane = o_sign + 8 * nnc
-    size = o_plane + 8 * R
+    size = _a16(o_plane + 8 * R)
     return dict(
         magic=magic,
         version=int.from_bytes(h[4:6], "little"),

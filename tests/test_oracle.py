@@ -177,8 +177,9 @@ def _check_stream(x, c):
     e = s["eps_q"]
     n = x.size
     assert s["magic"] == 0x505A5348 and s["block"] == 64 and s["n"] == n
-    assert s["size"] == len(c) == 64 + (s["nb"] + 15) // 16 * 16 + (4 * s["nb"] + 15) // 16 * 16 \
-        + 8 * s["nnc"] + 8 * s["R"]
+    raw = 64 + (s["nb"] + 15) // 16 * 16 + (4 * s["nb"] + 15) // 16 * 16 + 8 * s["nnc"] + 8 * s["R"]
+    assert s["size"] == len(c) == (raw + 15) // 16 * 16
+    assert not c[raw:].any()  # end padding is zero
     idx = np.random.default_rng(1).choice(n, size=min(n, 400), replace=False) if n else []
     qs = values(s)
     for i in idx:
