@@ -170,6 +170,50 @@ def make_fields(seed_base: int):
     return A, B
 
 
+# ---------------------------------------------------------------- profiling mode
+def profile_op(op: str, shape):
+    """Runs one operator 4 times on the workload's fields, holding only the
+    buffers that operator needs (for an ncu capture of its kernels)."""
+    import torch
+
+    import paper_2408_11971_gb300 as hz
+    from paper_2408_11971_gb300 import build as hzbuild
+
+    hzbuild.build()
+    ctx = hz.Context(0)
+    A, B = make_fields(0)
+    xa = torch.from_numpy(A.reshape(-1)).cuda()
+    ca = hz.compress(xa, eb=REL, mode="rel", ctx=ctx)
+    e = hz.header(ca)["eps_q"]
+    cb = None
+    if op == "add":
+        cb = hz.compress(torch.from_numpy(B.reshape(-1)).cuda(), eb=e, ctx=ctx)
+    del B
+    if op not in ("compress", "decompress"):
+        del xa
+    torch.cuda.synchronize()
+    for _ in range(4):
+        if op == "compress":
+            hz.compress(xa, eb=REL, mode="rel", ctx=ctx)
+        elif op == "decompress":
+            hz.decompress(ca, out=xa, ctx=ctx)
+        elif op == "negate":
+            hz.negate(ca, ctx=ctx)
+        elif op == "add_scalar":
+            hz.add_scalar(ca, SCALAR_ADD, ctx=ctx)
+        elif op == "mul_scalar":
+            hz.mul_scalar(ca, SCALAR_MUL, ctx=ctx)
+        elif op == "add":
+            hz.add(ca, cb, ctx=ctx)
+        elif op == "mean":
+            hz.mean(ca, ctx=ctx)
+        elif op == "var":
+            hz.var(ca, ctx=ctx)
+    torch.cuda.synchronize()
+    ctx.check(op)
+    print(f"profile-op {op} done: stream {ca.numel()} bytes")
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -182,9 +226,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", type=int, nargs=3, default=list(DEFAULT_SHAPE),
                     help="field shape (smaller cases are for profiling, not bench lines)")
+    ap.add_argument("--profile-op", default=None,
+                    choices=["compress", "decompress", "negate", "add_scalar", "mul_scalar", "add",
+                             "mean", "var"],
+                    help="run only this operator 4 times (for ncu captures; prints no bench line)")
     args = ap.parse_args()
     global SHAPE
     SHAPE = tuple(args.shape)
+    if args.profile_op:
+        if args.impl != "hoszp":
+            raise SystemExit("--profile-op runs the library only")
     warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -218,6 +269,10 @@ def main():
         return
 
     import torch
+
+    if args.profile_op:
+        profile_op(args.profile_op, tuple(args.shape))
+        return
 
     dist = None
     if world > 1:
