@@ -7,6 +7,7 @@
 #include <new>
 
 #include "hz_kernels.cuh"
+#include "hz_ws.cuh"
 
 using namespace hz;
 
@@ -72,11 +73,13 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
     o_desc[k] = off;
     off = round_up(off + tiles * sizeof(Desc), 256);
   }
-  uint64_t o_pre[2];
-  for (int k = 0; k < 2; k++) {
+  uint64_t o_pre[3];
+  for (int k = 0; k < 3; k++) {
     o_pre[k] = off;
     off = round_up(off + (tiles + 1) * 16, 256);
   }
+  const uint64_t o_agg = off;
+  off = round_up(off + (tiles + 1) * 8, 256);
   const uint64_t o_part = off;
   off = round_up(off + grid * sizeof(Partial), 256);
   const uint64_t o_range = off;
@@ -118,6 +121,8 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
   for (int k = 0; k < NCHAIN; k++) w.desc[k] = (Desc*)(base + o_desc[k]);
   w.max_tiles = tiles;
   for (int k = 0; k < 2; k++) w.pre[k] = (unsigned long long*)(base + o_pre[k]);
+  w.opre = (unsigned long long*)(base + o_pre[2]);
+  w.agg = (unsigned long long*)(base + o_agg);
   w.partials = (Partial*)(base + o_part);
   w.range_part = (float*)(base + o_range);
   w.max_grid = grid;
@@ -240,7 +245,7 @@ int hoszp_compress(hoszp_ctx* ctx, const float* d_x, uint64_t n, const uint32_t 
     if (eq == 0.0f) return HOSZP_ERR_ARG;
   }
   DeviceGuard g(ctx->device);
-  int rc = ensure_ws(ctx, ntiles_of(nb) + 1, 24 * nb + 16);
+  int rc = ensure_ws(ctx, ntiles_of(nb) + 1, 25ull * TILE * ntiles_of(nb) + 16);
   if (rc) return rc;
   Launch lc = lc_of(ctx, stream);
   uint32_t d3[3] = {0, 0, 0};
@@ -252,7 +257,7 @@ int hoszp_compress(hoszp_ctx* ctx, const float* d_x, uint64_t n, const uint32_t 
   rc = cuda_rc(launch_compress(lc, d_x, n, d3, (uint32_t)ndims, eq, eb,
                                eb_mode == HOSZP_EB_REL, (uint8_t*)d_out, cap, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, (uint8_t*)d_out, cap, d_out_bytes, ctx->ws));
+  return cuda_rc(launch_place(lc, (uint8_t*)d_out, cap, d_out_bytes, SLOT_COMPRESS, 0, ctx->ws));
 }
 
 int hoszp_decompress(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, float* d_x, uint64_t n,
@@ -304,12 +309,16 @@ int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
   if (o < a + c_bytes && a < o + cap) return HOSZP_ERR_ARG;  // no aliasing
   DeviceGuard g(ctx->device);
   const uint64_t tiles = tiles_from_bytes(c_bytes);
-  int rc = ensure_ws(ctx, tiles, cap / 8 + 16);
+  // slot words: (1 + e) per non-constant input block + the input's plane words,
+  // where e bounds the growth of a block's rate: |2e rho| <= 2|s| when rho != 0
+  const uint32_t e_bits = (uint32_t)std::ceil(std::log2(2.0 * std::fabs(s) + 1.0)) + 1u;
+  const uint64_t nnc_bound = c_bytes / 21 + 1;  // a non-constant block takes >= 21 bytes
+  int rc = ensure_ws(ctx, tiles, nnc_bound * (1ull + e_bits) + c_bytes / 8 + 64);
   if (rc) return rc;
   Launch lc = lc_of(ctx, stream);
-  rc = cuda_rc(launch_mul_scalar(lc, a, c_bytes, s, o, cap, ctx->ws));
+  rc = cuda_rc(launch_mul_scalar(lc, a, c_bytes, s, e_bits, o, cap, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, ctx->ws));
+  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_MUL, e_bits, ctx->ws));
 }
 
 int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
@@ -325,12 +334,13 @@ int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, 
   if ((o < a + a_bytes && a < o + cap) || (o < b + b_bytes && b < o + cap)) return HOSZP_ERR_ARG;
   DeviceGuard g(ctx->device);
   const uint64_t ta = tiles_from_bytes(a_bytes), tb = tiles_from_bytes(b_bytes);
-  int rc = ensure_ws(ctx, ta > tb ? ta : tb, cap / 8 + 16);
+  // slot words: the two inputs' sign and plane words
+  int rc = ensure_ws(ctx, ta > tb ? ta : tb, (a_bytes + b_bytes) / 8 + 64);
   if (rc) return rc;
   Launch lc = lc_of(ctx, stream);
   rc = cuda_rc(launch_add(lc, a, a_bytes, b, b_bytes, o, cap, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, ctx->ws));
+  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_ADD, 0, ctx->ws));
 }
 
 static int moments(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,

@@ -3,7 +3,7 @@
 // blockwise fixed-length bit-plane encoding, stream layout of Fig. 3).
 #include <cfloat>
 
-#include "hz_decode.cuh"
+#include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -115,21 +115,17 @@ __device__ __forceinline__ void issue_x(InX* s, uint64_t* bar, const float* x, u
   if (bytes) bulk_g2s(s->v, x + first, bytes, bar);
 }
 
-__global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, uint64_t n,
-                                                  const uint32_t dims0, const uint32_t dims1,
-                                                  const uint32_t dims2, const uint32_t ndims,
-                                                  float eps_q_abs, double eps_abs, int rel,
-                                                  uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
+__global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
+    const float* __restrict__ x, uint64_t n, const uint32_t dims0, const uint32_t dims1,
+    const uint32_t dims2, const uint32_t ndims, float eps_q_abs, double eps_abs, int rel,
+    uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InX* ins = reinterpret_cast<InX*>(dyn);
-  OutStage* outs = reinterpret_cast<OutStage*>(dyn + CMP_STAGES * sizeof(InX));
-  __shared__ uint64_t bars[CMP_STAGES];
-  __shared__ unsigned long long s_tiles[CMP_STAGES];
-  __shared__ TileScan ts;
-  __shared__ unsigned long long s_pre[2];
-  __shared__ unsigned long long s_epoch;
-  __shared__ unsigned int s_qmax[CTA / 32];
-  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  __shared__ uint64_t full[CMP_STAGES], empty[CMP_STAGES];
+  __shared__ unsigned long long stage_tile[CMP_STAGES];
+  __shared__ uint8_t srate[2][TILE];
+  __shared__ unsigned int s_qmax[PRODUCER_THREADS / 32];
+  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
 
   const float e = rel ? *ws.eps_q : eps_q_abs;
   const uint64_t nb = nblocks(n);
@@ -139,123 +135,110 @@ __global__ void __launch_bounds__(CTA) k_compress(const float* __restrict__ x, u
   Q.e2 = 2.0f * e;
   Q.r = (e >= FLT_MIN) ? __double2float_rn(1.0 / (double)Q.e2) : 0.0f;
 
-  if (tid == 0) {
-    s_epoch = launch_epoch(ws);
-    if (blockIdx.x == 0) {  // header template for the placement kernel
-      hoszp_header* H = ws.hdr;
-      H->magic = HOSZP_MAGIC;
-      H->version = HOSZP_VERSION;
-      H->dtype = 0;
-      H->ndims = (uint8_t)ndims;
-      H->dims[0] = dims0;
-      H->dims[1] = dims1;
-      H->dims[2] = dims2;
-      H->eps_q = e;
-      H->n = n;
-      H->eps = rel ? *ws.eps : eps_abs;
-      H->nnc = 0;
-      H->R = 0;
-      H->qbound = 0;
-      H->block = HOSZP_BLOCK;
-    }
+  if (tid == 0 && blockIdx.x == 0) {  // header template for the placement kernel
+    hoszp_header* H = ws.hdr;
+    H->magic = HOSZP_MAGIC;
+    H->version = HOSZP_VERSION;
+    H->dtype = 0;
+    H->ndims = (uint8_t)ndims;
+    H->dims[0] = dims0;
+    H->dims[1] = dims1;
+    H->dims[2] = dims2;
+    H->eps_q = e;
+    H->n = n;
+    H->eps = rel ? *ws.eps : eps_abs;
+    H->nnc = 0;
+    H->R = 0;
+    H->qbound = 0;
+    H->block = HOSZP_BLOCK;
   }
-  init_bars<CMP_STAGES>(bars);
-  if (tid == 0) {
-    for (int k = 0; k < CMP_STAGES - 1; k++) {
-      const unsigned long long t = atomicAdd(&ws.sync->ticket, 1u);
-      s_tiles[k] = t;
-      if (t < ntiles) issue_x(&ins[k], &bars[k], x, n, t);
-    }
-  }
-  __syncthreads();
-  const unsigned long long epoch = s_epoch;
+  ring_init<CMP_STAGES>(full, empty);
+  const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   int bad = 0;
-  uint64_t i = 0;
-  for (;; i++) {
-    const unsigned long long tile = s_tiles[i % CMP_STAGES];
-    if (tile >= ntiles) break;
-    if (tid == 0) {
-      const int sn = (int)((i + CMP_STAGES - 1) % CMP_STAGES);
-      const unsigned long long tn = atomicAdd(&ws.sync->ticket, 1u);
-      s_tiles[sn] = tn;
-      if (tn < ntiles) issue_x(&ins[sn], &bars[sn], x, n, tn);
+  if (w == LOADER_WARP) {
+    if ((tid & 31) == 0) {
+      const uint64_t G = gridDim.x;
+      loader_loop<CMP_STAGES>(
+          full, empty, stage_tile, ntiles, ws.status,
+          [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
+          [&](int s, unsigned long long t) { issue_x(&ins[s], &full[s], x, n, t); });
     }
-    InX& in = ins[i % CMP_STAGES];
-    mbar_wait(&bars[i % CMP_STAGES], (unsigned)((i / CMP_STAGES) & 1), ws.status);
-    const uint64_t b = tile * TILE + g;
-    const uint64_t first = (uint64_t)TILE_VALUES * tile;
-    const uint64_t copied = umin64(TILE_VALUES, n - first) & ~3ull;
-    const int o0 = 64 * g + 8 * j;  // offset in the tile
-    const uint64_t i0 = first + o0;
-    float v[8];
-    if ((uint64_t)o0 + 8 <= copied) {
-      const float4 a = *reinterpret_cast<const float4*>(&in.v[o0]);
-      const float4 c = *reinterpret_cast<const float4*>(&in.v[o0 + 4]);
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-      v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
-    } else {
+  } else {
+    for (uint64_t k = 0;; k++) {
+      const int s = (int)(k % CMP_STAGES);
+      mbar_wait(&full[s], (unsigned)((k / CMP_STAGES) & 1), ws.status);
+      const unsigned long long tile = stage_tile[s];
+      if (tile >= ntiles) break;
+      const InX& in = ins[s];
+      const uint64_t b = tile * TILE + g;
+      const uint64_t first = (uint64_t)TILE_VALUES * tile;
+      const uint64_t copied = umin64(TILE_VALUES, n - first) & ~3ull;
+      const int o0 = 64 * g + 8 * j;  // offset in the tile
+      const uint64_t i0 = first + o0;
+      float v[8];
+      if ((uint64_t)o0 + 8 <= copied) {
+        const float4 a = *reinterpret_cast<const float4*>(&in.v[o0]);
+        const float4 c = *reinterpret_cast<const float4*>(&in.v[o0 + 4]);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          const uint64_t o = (uint64_t)o0 + t;
+          v[t] = (o < copied) ? in.v[o] : ((i0 + t < n) ? __ldg(x + i0 + t) : 0.0f);
+        }
+      }
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      int q[8];
 #pragma unroll
       for (int t = 0; t < 8; t++) {
-        const uint64_t o = (uint64_t)o0 + t;
-        v[t] = (o < copied) ? in.v[o] : ((i0 + t < n) ? __ldg(x + i0 + t) : 0.0f);
+        q[t] = quantize(v[t], Q, bad);
+        if (i0 + t >= n) q[t] = 0;
+        qmax = max(qmax, (uint32_t)abs(q[t]));
       }
-    }
-    int q[8];
+      // Eq. 4 inside the block: delta_i = q_i - q_{i-1}, delta_0 := 0 (outlier)
+      const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
+      uint32_t mag[8];
+      uint32_t sb = 0;
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
-      q[t] = quantize(v[t], Q, bad);
-      if (i0 + t >= n) q[t] = 0;
-      qmax = max(qmax, (uint32_t)abs(q[t]));
+      for (int t = 0; t < 8; t++) {
+        int d = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
+        if (i0 + t >= n) d = 0;
+        mag[t] = (uint32_t)abs(d);
+        sb |= (d < 0 ? 1u : 0u) << t;
+      }
+      const int rate = octet_rate(mag);
+      produce_tile(srate, k, tile, nb, mag, sb, rate, q[0], b < nb, g, j, out, ws.staging,
+                   slot_offset(SLOT_COMPRESS, tile, nullptr, nullptr, 0), ws.staging_words,
+                   ws.agg, S, bad);
     }
-    // Eq. 4 inside the block: delta_i = q_i - q_{i-1}, delta_0 := 0 (outlier)
-    const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
-    uint32_t mag[8];
-    uint32_t sb = 0;
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-      int d = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
-      if (i0 + t >= n) d = 0;
-      mag[t] = (uint32_t)abs(d);
-      sb |= (d < 0 ? 1u : 0u) << t;
-    }
-    const int rate = octet_rate(mag);
-    OutStage& os = outs[i & 1];
-    stage_encode(os, &ts, mag, sb, rate, q[0], b < nb, g, j);
-    if (tid == 0) os.tile = tile;
-    publish_agg(ws.desc[0], tile, epoch, os);
-    if (i > 0)
-      stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, nb, out, cap, ws.staging,
-                  ws.staging_words, ntiles, ws.totals, s_pre, bad);
-    __syncthreads();
   }
-  if (i > 0)
-    stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, nb, out, cap, ws.staging,
-                ws.staging_words, ntiles, ws.totals, s_pre, bad);
   // epilogue: max |q| for the header's qbound, first error, launch bookkeeping
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
   if ((tid & 31) == 0) s_qmax[tid >> 5] = qmax;
   __syncthreads();
   if (tid == 0) {
-    for (int w = 1; w < CTA / 32; w++) qmax = max(qmax, s_qmax[w]);
+    for (int k = 1; k < PRODUCER_THREADS / 32; k++) qmax = max(qmax, s_qmax[k]);
     atomicMax(&ws.totals[2], (unsigned long long)qmax);
   }
   if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const uint32_t dims[3],
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
                             uint64_t cap, Ws ws) {
-  const size_t smem = CMP_STAGES * sizeof(InX) + 2 * sizeof(OutStage);
+  const size_t smem = CMP_STAGES * sizeof(InX);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_compress<<<persistent_grid(k_compress, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
-      x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs, rel ? 1 : 0, out, cap, ws);
+  k_compress<<<persistent_grid(k_compress, PRODUCER_THREADS, lc.grid, smem), PRODUCER_THREADS,
+               smem, lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs,
+                                  rel ? 1 : 0, out, cap, ws);
   return cudaGetLastError();
 }
 

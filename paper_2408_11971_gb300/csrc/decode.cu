@@ -3,7 +3,7 @@
 // sum the quantized integers exactly and finish in FP64.
 #include <cfloat>
 
-#include "hz_decode.cuh"
+#include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -11,15 +11,14 @@ namespace hz {
 // ---------------------------------------------------------------- decompression
 constexpr int DEC_STAGES = 3;
 
-__global__ void __launch_bounds__(CTA) k_decompress(const uint8_t* __restrict__ c, uint64_t c_bytes,
-                                                    float* __restrict__ x, uint64_t n_expect,
-                                                    const unsigned long long* __restrict__ pre,
-                                                    Ws ws) {
+__global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
+    const uint8_t* __restrict__ c, uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect,
+    const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* stages = reinterpret_cast<InStage*>(dyn);
-  __shared__ uint64_t bars[DEC_STAGES];
-  __shared__ TileScan ts;
-  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  __shared__ uint64_t full[DEC_STAGES], empty[DEC_STAGES];
+  __shared__ unsigned long long stage_tile[DEC_STAGES];
+  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
   const Info h = parse_header(c, c_bytes);
   int bad = 0;
   uint64_t ntiles = 0;
@@ -28,28 +27,47 @@ __global__ void __launch_bounds__(CTA) k_decompress(const uint8_t* __restrict__ 
   else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
   const float e2 = 2.0f * h.eps_q;
   const bool small = h.qbound < (1u << 22);
-  init_bars<DEC_STAGES>(bars);
-  consume_tiles<DEC_STAGES>(c, h, ntiles, pre, stages, bars, &ts, ws.status, bad,
-                            [&](uint64_t tile, const InStage& sg, const TileScan& sc) {
-    const BlockRef br = block_ref(sg, sc, h, tile, g, j);
-    const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
-    int d[8], q[8];
-    octet_deltas(br, kmax, j, d);
-    octet_values(br, d, j, q);
-    const uint64_t i0 = (tile * TILE + g) * L + 8 * j;
-    float v[8];
-#pragma unroll
-    for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
-    if (i0 + 8 <= h.n) {
-      float4* o = reinterpret_cast<float4*>(x + i0);
-      o[0] = make_float4(v[0], v[1], v[2], v[3]);
-      o[1] = make_float4(v[4], v[5], v[6], v[7]);
-    } else {
-#pragma unroll
-      for (int t = 0; t < 8; t++)
-        if (i0 + t < h.n) x[i0 + t] = v[t];
+  const OctetSel S = octet_sel(j);
+  ring_init<DEC_STAGES>(full, empty);
+  if (w == LOADER_WARP) {
+    if ((tid & 31) == 0) {
+      const uint64_t G = gridDim.x;
+      loader_loop<DEC_STAGES>(full, empty, stage_tile, ntiles, ws.status,
+                              [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
+                              [&](int s, unsigned long long t) {
+                                issue_in_tile(&stages[s], &full[s], c, h, t, pre);
+                              });
     }
-  });
+  } else {
+    for (uint64_t k = 0;; k++) {
+      const int s = (int)(k % DEC_STAGES);
+      mbar_wait(&full[s], (unsigned)((k / DEC_STAGES) & 1), ws.status);
+      const unsigned long long tile = stage_tile[s];
+      if (tile >= ntiles) break;
+      const InStage& sg = stages[s];
+      const TileOff off = warp_tile_offsets(sg.rate, tile, h.nb, g, bad);
+      const BlockRef br = block_ref_w(sg, off, h, tile, g, j, bad);
+      const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+      int d[8], q[8];
+      octet_deltas(br, kmax, j, S, d);
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      octet_values(br, d, j, q);
+      const uint64_t i0 = (tile * TILE + g) * L + 8 * j;
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+      if (i0 + 8 <= h.n) {
+        float4* o = reinterpret_cast<float4*>(x + i0);
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+          if (i0 + t < h.n) x[i0 + t] = v[t];
+      }
+    }
+  }
   if (bad) set_status(ws.status, bad);
 }
 
@@ -63,8 +81,8 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
     cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_decompress<<<persistent_grid(k_decompress, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
-      c, c_bytes, x, n, ws.pre[0], ws);
+  k_decompress<<<persistent_grid(k_decompress, CONSUMER_THREADS, lc.grid, smem), CONSUMER_THREADS,
+                 smem, lc.stream>>>(c, c_bytes, x, n, ws.pre[0], ws);
   return cudaGetLastError();
 }
 
@@ -123,17 +141,16 @@ __device__ __forceinline__ double u256_to_double(const U256& a) {
 constexpr int MOM_STAGES = 3;
 
 template <bool VAR>
-__global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, uint64_t c_bytes,
-                                                 double* result,
-                                                 const unsigned long long* __restrict__ pre,
-                                                 Ws ws) {
+__global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result,
+    const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* stages = reinterpret_cast<InStage*>(dyn);
-  __shared__ uint64_t bars[MOM_STAGES];
-  __shared__ TileScan ts;
-  __shared__ long long s_s1[CTA / 32];
-  __shared__ U128 s_s2[CTA / 32];
-  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  __shared__ uint64_t full[MOM_STAGES], empty[MOM_STAGES];
+  __shared__ unsigned long long stage_tile[MOM_STAGES];
+  __shared__ long long s_s1[CONSUMER_THREADS / 32];
+  __shared__ U128 s_s2[CONSUMER_THREADS / 32];
+  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
   const Info h = parse_header(c, c_bytes);
   int bad = 0;
   uint64_t ntiles = 0;
@@ -141,22 +158,65 @@ __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, 
   else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
   long long s1 = 0;  // per thread: |q| <= 2^30, far fewer than 2^32 values per thread
   U128 s2 = {0, 0};
-  init_bars<MOM_STAGES>(bars);
-  consume_tiles<MOM_STAGES>(c, h, ntiles, pre, stages, bars, &ts, ws.status, bad,
-                            [&](uint64_t tile, const InStage& sg, const TileScan& sc) {
-    const BlockRef br = block_ref(sg, sc, h, tile, g, j);
-    const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
-    int d[8], q[8];
-    octet_deltas(br, kmax, j, d);
-    octet_values(br, d, j, q);
+  const OctetSel S = octet_sel(j);
+  // weight bytes 64 - (8j + t) of the block sum (0 at position 0)
+  uint32_t wlo = 0, whi = 0;
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
-      if (8 * j + t < br.len) {
-        s1 += q[t];
-        if (VAR) add_u64(s2, (unsigned long long)((long long)q[t] * (long long)q[t]));
+  for (int t = 0; t < 4; t++) {
+    wlo |= (uint32_t)(64 - 8 * j - t) << (8 * t);
+    whi |= (uint32_t)(64 - 8 * j - 4 - t) << (8 * t);
+  }
+  if (j == 0) wlo &= 0xffffff00u;
+  ring_init<MOM_STAGES>(full, empty);
+  if (w == LOADER_WARP) {
+    if ((tid & 31) == 0) {
+      const uint64_t G = gridDim.x;
+      loader_loop<MOM_STAGES>(full, empty, stage_tile, ntiles, ws.status,
+                              [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
+                              [&](int s, unsigned long long t) {
+                                issue_in_tile(&stages[s], &full[s], c, h, t, pre);
+                              });
+    }
+  } else {
+    for (uint64_t k = 0;; k++) {
+      const int s = (int)(k % MOM_STAGES);
+      mbar_wait(&full[s], (unsigned)((k / MOM_STAGES) & 1), ws.status);
+      const unsigned long long tile = stage_tile[s];
+      if (tile >= ntiles) break;
+      const InStage& sg = stages[s];
+      const TileOff off = warp_tile_offsets(sg.rate, tile, h.nb, g, bad);
+      const BlockRef br = block_ref_w(sg, off, h, tile, g, j, bad);
+      const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+      if (!VAR && kmax <= 2 && __all_sync(0xffffffffu, br.len == L)) {
+        const int v = octet_sum_fast(br, kmax, j, S, wlo, whi);
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+        s1 += v;
+        if (j == 0) s1 += (long long)L * br.outlier;
+        continue;
+      }
+      int d[8];
+      octet_deltas(br, kmax, j, S, d);
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      if (!VAR) {
+        s1 += octet_sum_q(br, d, j, kmax);
+      } else {
+        int q[8];
+        octet_values(br, d, j, q);
+        long long a = 0;
+        unsigned long long b = 0;  // 8 squares of |q| <= 2^30 stay below 2^63
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          const int qq = (8 * j + t < br.len) ? q[t] : 0;
+          a += qq;
+          b += (unsigned long long)((long long)qq * qq);
+        }
+        s1 += a;
+        add_u64(s2, b);
       }
     }
-  });
+  }
   // CTA reduction -> per-CTA partial
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -176,7 +236,7 @@ __global__ void __launch_bounds__(CTA) k_moments(const uint8_t* __restrict__ c, 
   if (tid == 0) {
     __int128 t1 = 0;
     U128 t2 = {0, 0};
-    for (int w = 0; w < CTA / 32; w++) {
+    for (int w = 0; w < CONSUMER_THREADS / 32; w++) {
       t1 += s_s1[w];
       add_u128(t2, s_s2[w]);
     }
@@ -234,7 +294,8 @@ static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t
     cudaFuncSetAttribute(k_moments<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_moments<VAR><<<persistent_grid(k_moments<VAR>, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
+  k_moments<VAR><<<persistent_grid(k_moments<VAR>, CONSUMER_THREADS, lc.grid, smem),
+                   CONSUMER_THREADS, smem, lc.stream>>>(
       c, c_bytes, result, ws.pre[0], ws);
   return cudaGetLastError();
 }

@@ -133,6 +133,8 @@ struct Ws {
   uint64_t staging_words;
   hoszp_header* hdr;  // header of the stream being produced (filled in by the producer)
   unsigned long long* pre[2];  // per-tile (nc, r) prefixes of up to two input streams
+  unsigned long long* agg;     // per-tile (nc << 32 | r) of a produced stream
+  unsigned long long* opre;    // per-tile (nc, r) prefixes of the produced stream
 };
 
 // Tile hand-out and launch bookkeeping. Every CTA calls begin() once, next()
@@ -285,26 +287,63 @@ HZ_HD void tr8x8(uint32_t& lo, uint32_t& hi) {
 }
 
 #ifdef __CUDACC__
+// Lane constants for byte_transpose8 (PRMT selectors; j = lane % 8).
+struct OctetSel {
+  uint32_t a0, a1, b0, b1, b2, c0, c1, c2;
+};
+__device__ __forceinline__ OctetSel octet_sel(int j) {
+  OctetSel S;
+  const bool x4 = (j & 4) != 0, x2 = (j & 2) != 0, x1 = (j & 1) != 0;
+  S.a0 = x4 ? 0x3210u : 0x7654u;
+  S.a1 = S.a0 ^ 0x4444u;
+  S.b0 = x2 ? 0x5410u : 0x7632u;
+  S.b1 = x2 ? 0x3254u : 0x5410u;
+  S.b2 = x2 ? 0x3276u : 0x7610u;
+  S.c0 = x1 ? 0x6420u : 0x7531u;
+  S.c1 = x1 ? 0x3514u : 0x5240u;
+  S.c2 = x1 ? 0x3716u : 0x7260u;
+  return S;
+}
+
 // 8x8 byte transpose across the 8 lanes of an octet: lane j holds row j
 // (bytes 0..3 in lo, 4..7 in hi); afterwards lane j holds column j. All lanes
 // of the warp must call it (full-mask shuffles; partners differ in bits 0..2).
-__device__ __forceinline__ void byte_transpose8(uint32_t& lo, uint32_t& hi, int j) {
-  // swap the off-diagonal 4x4 byte blocks (lanes j, j^4)
-  uint32_t send = (j & 4) ? lo : hi;
+// Three exchange steps (distance 4, 2, 1), each one shuffle and three byte
+// permutes with lane-constant selectors.
+__device__ __forceinline__ void byte_transpose8(uint32_t& lo, uint32_t& hi, const OctetSel& S) {
+  uint32_t send = __byte_perm(lo, hi, S.a0);
   uint32_t recv = __shfl_xor_sync(0xffffffffu, send, 4);
-  if (j & 4) lo = recv; else hi = recv;
-  // swap the off-diagonal 2x2 blocks of each 4x4 block (lanes j, j^2)
-  bool b1 = (j & 2) != 0;
-  send = __byte_perm(lo, hi, b1 ? 0x5410 : 0x7632);
+  lo = __byte_perm(lo, recv, S.a1);
+  hi = __byte_perm(hi, recv, S.a0);
+  send = __byte_perm(lo, hi, S.b0);
   recv = __shfl_xor_sync(0xffffffffu, send, 2);
-  lo = __byte_perm(lo, recv, b1 ? 0x3254 : 0x5410);
-  hi = __byte_perm(hi, recv, b1 ? 0x3276 : 0x7610);
-  // transpose each 2x2 block (lanes j, j^1)
-  bool b0 = (j & 1) != 0;
-  send = __byte_perm(lo, hi, b0 ? 0x6420 : 0x7531);
+  lo = __byte_perm(lo, recv, S.b1);
+  hi = __byte_perm(hi, recv, S.b2);
+  send = __byte_perm(lo, hi, S.c0);
   recv = __shfl_xor_sync(0xffffffffu, send, 1);
-  lo = __byte_perm(lo, recv, b0 ? 0x3514 : 0x5240);
-  hi = __byte_perm(hi, recv, b0 ? 0x3716 : 0x7260);
+  lo = __byte_perm(lo, recv, S.c1);
+  hi = __byte_perm(hi, recv, S.c2);
+}
+__device__ __forceinline__ void byte_transpose8(uint32_t& lo, uint32_t& hi, int j) {
+  byte_transpose8(lo, hi, octet_sel(j));
+}
+
+// tr8x8 with the shifts written as integer multiplies (high part for right
+// shifts), so they issue on the FMA pipe and the logic pipe only sees the
+// LOP3 operations. Same result as tr8x8.
+__device__ __forceinline__ void tr8x8_d(uint32_t& lo, uint32_t& hi) {
+  uint32_t t;
+  t = (lo ^ __umulhi(lo, 1u << 25)) & 0x00AA00AAu;  // >> 7
+  lo = lo ^ t ^ (t * 128u);
+  t = (hi ^ __umulhi(hi, 1u << 25)) & 0x00AA00AAu;
+  hi = hi ^ t ^ (t * 128u);
+  t = (lo ^ __umulhi(lo, 1u << 18)) & 0x0000CCCCu;  // >> 14
+  lo = lo ^ t ^ (t * 16384u);
+  t = (hi ^ __umulhi(hi, 1u << 18)) & 0x0000CCCCu;
+  hi = hi ^ t ^ (t * 16384u);
+  t = (lo ^ (hi * 16u)) & 0xF0F0F0F0u;
+  lo = lo ^ t;
+  hi = hi ^ __umulhi(t, 1u << 28);  // >> 4
 }
 
 // ---------------------------------------------------------------- quantization (Eq. 3)
@@ -367,35 +406,11 @@ __device__ __forceinline__ float dequant_any(int q, float e2) {
 }
 
 // ---------------------------------------------------------------- octet codec
-// Decode the magnitudes of lane j's 8 positions from a block's planes.
-// planes: the block's first plane word; r: its rate; kmax: warp-uniform number
-// of 8-plane groups to run (>= ceil(r/8)). mag[t] for position 8j+t.
-__device__ __forceinline__ void decode_mags(const uint64_t* __restrict__ planes, int r, int kmax,
-                                            int j, uint32_t mag[8]) {
-#pragma unroll
-  for (int t = 0; t < 8; t++) mag[t] = 0;
-  for (int k = 0; k < kmax; k++) {
-    int p = 8 * k + j;
-    uint64_t w = (p < r) ? __ldg(planes + p) : 0ull;
-    uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
-    byte_transpose8(lo, hi, j);
-    tr8x8(lo, hi);
-    const int sh = 8 * k;
-    mag[0] |= (lo & 0xffu) << sh;
-    mag[1] |= ((lo >> 8) & 0xffu) << sh;
-    mag[2] |= ((lo >> 16) & 0xffu) << sh;
-    mag[3] |= (lo >> 24) << sh;
-    mag[4] |= (hi & 0xffu) << sh;
-    mag[5] |= ((hi >> 8) & 0xffu) << sh;
-    mag[6] |= ((hi >> 16) & 0xffu) << sh;
-    mag[7] |= (hi >> 24) << sh;
-  }
-}
-
 // Encode: lane j holds magnitudes of its 8 positions; writes plane words
 // 8k+j (< r) of the block to planes_out. kmax warp-uniform >= ceil(r/8).
 __device__ __forceinline__ void encode_planes(const uint32_t mag[8], int r, int kmax, int j,
-                                              uint64_t* planes_out, uint64_t limit_words) {
+                                              uint64_t* planes_out, uint64_t limit_words,
+                                              const OctetSel& S) {
   for (int k = 0; k < kmax; k++) {
     const int sh = 8 * k;
     uint32_t b0 = (mag[0] >> sh) & 0xffu, b1 = (mag[1] >> sh) & 0xffu;
@@ -404,8 +419,8 @@ __device__ __forceinline__ void encode_planes(const uint32_t mag[8], int r, int 
     uint32_t b6 = (mag[6] >> sh) & 0xffu, b7 = (mag[7] >> sh) & 0xffu;
     uint32_t lo = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
     uint32_t hi = b4 | (b5 << 8) | (b6 << 16) | (b7 << 24);
-    tr8x8(lo, hi);             // byte p' = bit 8k+p' of the 8 magnitudes
-    byte_transpose8(lo, hi, j);  // lane j: plane word 8k+j
+    tr8x8_d(lo, hi);             // byte p' = bit 8k+p' of the 8 magnitudes
+    byte_transpose8(lo, hi, S);  // lane j: plane word 8k+j
     int p = sh + j;
     if (p < r && (uint64_t)p < limit_words)
       planes_out[p] = ((uint64_t)hi << 32) | lo;

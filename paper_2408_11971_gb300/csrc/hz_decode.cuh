@@ -1,8 +1,6 @@
-// hz_decode.cuh — the consumer side of a tile: a CTA walks its tiles with the
-// next tiles' compressed words already in flight into a shared-memory ring
-// (bulk copies located by the rate pre-scan), then decodes an octet's 8 deltas
-// (workflow 2) or, with the inverse Lorenzo, its 8 quantized integers
-// (workflow 3).
+// hz_decode.cuh — decoding an octet (lane j's 8 positions of a block) from a
+// tile held in shared memory: its 8 deltas (workflow 2) or, with the inverse
+// Lorenzo, its 8 quantized integers (workflow 3).
 #pragma once
 #include "hz_pipe.cuh"
 
@@ -17,25 +15,12 @@ struct BlockRef {
   int len;                 // valid positions of the block (64, fewer in the tail block)
 };
 
-__device__ __forceinline__ BlockRef block_ref(const InStage& s, const TileScan& ts, const Info& h,
-                                              uint64_t tile, int g, int j) {
-  BlockRef br;
-  const uint64_t b = tile * TILE + g;
-  br.rate = s.rate[g];  // sanitized: 0 past the end and for invalid rates
-  br.outlier = s.outlier[g];
-  br.planes = s.plane + s.pbase + ts.r_excl[g];
-  br.sign_byte = br.rate
-                     ? reinterpret_cast<const uint8_t*>(s.sign + s.sbase + ts.nc_excl[g])[j]
-                     : 0u;
-  const uint64_t rem = (b < h.nb) ? h.n - b * L : 0;
-  br.len = rem < (uint64_t)L ? (int)rem : L;
-  return br;
-}
-
-// Magnitudes of lane j's positions 8j..8j+7 from a block's planes in shared
-// memory; kmax warp-uniform >= ceil(rate/8).
-__device__ __forceinline__ void decode_mags_s(const uint64_t* planes, int r, int kmax, int j,
-                                              uint32_t mag[8]) {
+// The planes of a block, transposed: group k (planes 8k..8k+7) becomes 8
+// bytes (lo[k], hi[k]) whose byte t holds bits 8k..8k+7 of |delta| at
+// position 8j+t. kmax (warp-uniform) >= ceil(rate / 8).
+__device__ __forceinline__ void decode_groups(const uint64_t* planes, int r, int kmax,
+                                              const OctetSel& S, int j, uint32_t lo[4],
+                                              uint32_t hi[4]) {
   uint64_t w[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
@@ -43,47 +28,71 @@ __device__ __forceinline__ void decode_mags_s(const uint64_t* planes, int r, int
     w[k] = (k < kmax && p < r) ? planes[p] : 0ull;
   }
 #pragma unroll
-  for (int t = 0; t < 8; t++) mag[t] = 0;
-#pragma unroll
   for (int k = 0; k < 4; k++) {
+    lo[k] = (uint32_t)w[k];
+    hi[k] = (uint32_t)(w[k] >> 32);
     if (k < kmax) {
-      uint32_t lo = (uint32_t)w[k], hi = (uint32_t)(w[k] >> 32);
-      byte_transpose8(lo, hi, j);
-      tr8x8(lo, hi);
-      if (k == 0) {
-        mag[0] = lo & 0xffu;
-        mag[1] = (lo >> 8) & 0xffu;
-        mag[2] = (lo >> 16) & 0xffu;
-        mag[3] = lo >> 24;
-        mag[4] = hi & 0xffu;
-        mag[5] = (hi >> 8) & 0xffu;
-        mag[6] = (hi >> 16) & 0xffu;
-        mag[7] = hi >> 24;
-      } else {
-        const int sh = 8 * k;
-        mag[0] |= (lo & 0xffu) << sh;
-        mag[1] |= ((lo >> 8) & 0xffu) << sh;
-        mag[2] |= ((lo >> 16) & 0xffu) << sh;
-        mag[3] |= (lo >> 24) << sh;
-        mag[4] |= (hi & 0xffu) << sh;
-        mag[5] |= ((hi >> 8) & 0xffu) << sh;
-        mag[6] |= ((hi >> 16) & 0xffu) << sh;
-        mag[7] |= (hi >> 24) << sh;
+      byte_transpose8(lo[k], hi[k], S);
+      tr8x8_d(lo[k], hi[k]);
+    }
+  }
+}
+
+// Magnitudes of the 8 positions from the transposed groups.
+__device__ __forceinline__ void mags_from_groups(const uint32_t lo[4], const uint32_t hi[4],
+                                                 int kmax, uint32_t m[8]) {
+  if (kmax <= 1) {
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      m[t] = __byte_perm(lo[0], 0u, 0x4440u + t);
+      m[t + 4] = __byte_perm(hi[0], 0u, 0x4440u + t);
+    }
+  } else if (kmax == 2) {  // two bytes per value: interleave the groups
+    uint32_t x;
+    x = __byte_perm(lo[0], lo[1], 0x5140u);
+    m[0] = x & 0xffffu;
+    m[1] = x >> 16;
+    x = __byte_perm(lo[0], lo[1], 0x7362u);
+    m[2] = x & 0xffffu;
+    m[3] = x >> 16;
+    x = __byte_perm(hi[0], hi[1], 0x5140u);
+    m[4] = x & 0xffffu;
+    m[5] = x >> 16;
+    x = __byte_perm(hi[0], hi[1], 0x7362u);
+    m[6] = x & 0xffffu;
+    m[7] = x >> 16;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      uint32_t a = 0, b = 0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        a |= __byte_perm(lo[k], 0u, 0x4440u + t) << (8 * k);
+        b |= __byte_perm(hi[k], 0u, 0x4440u + t) << (8 * k);
       }
+      m[t] = a;
+      m[t + 4] = b;
     }
   }
 }
 
 // Signed deltas of lane j's positions; position 0 and positions past the
-// block's end are 0.
-__device__ __forceinline__ void octet_deltas(const BlockRef& br, int kmax, int j, int d[8]) {
-  uint32_t mag[8];
-  decode_mags_s(br.planes, br.rate, kmax, j, mag);
+// block's end are 0. The sign is applied as a multiply by +-1 (FMA pipe).
+__device__ __forceinline__ void octet_deltas(const BlockRef& br, int kmax, int j,
+                                             const OctetSel& S, int d[8]) {
+  uint32_t lo[4], hi[4], m[8];
+  decode_groups(br.planes, br.rate, kmax, S, j, lo, hi);
+  mags_from_groups(lo, hi, kmax, m);
 #pragma unroll
   for (int t = 0; t < 8; t++) {
-    const int pos = 8 * j + t;
-    const int v = ((br.sign_byte >> t) & 1u) ? -(int)mag[t] : (int)mag[t];
-    d[t] = (pos == 0 || pos >= br.len) ? 0 : v;
+    const int k = 1 - 2 * (int)((br.sign_byte >> t) & 1u);
+    d[t] = (int)m[t] * k;
+  }
+  if (j == 0) d[0] = 0;
+  if (br.len < L) {
+#pragma unroll
+    for (int t = 0; t < 8; t++)
+      if (8 * j + t >= br.len) d[t] = 0;
   }
 }
 
@@ -96,27 +105,80 @@ __device__ __forceinline__ void octet_values(const BlockRef& br, const int d[8],
     acc += d[t];
     s[t] = acc;
   }
-  const int excl = octet_excl_scan(acc, j);
+  const int base = br.outlier + octet_excl_scan(acc, j);
 #pragma unroll
-  for (int t = 0; t < 8; t++) q[t] = br.outlier + excl + s[t];
+  for (int t = 0; t < 8; t++) q[t] = base + s[t];
 }
 
-// Sanitize a freshly landed stage (rates past the end or above 31 become 0)
-// and scan its rates. Whole CTA; `bad` collects HOSZP_ERR_FORMAT.
-__device__ __forceinline__ void stage_begin(InStage& s, TileScan* ts, const Info& h,
-                                            uint64_t tile, int& bad) {
-  if (threadIdx.x < TILE) {
-    const uint64_t b = tile * TILE + threadIdx.x;
-    uint8_t r = s.rate[threadIdx.x];
-    if (b >= h.nb) r = 0;
-    if (r > MAX_RATE) {
-      r = 0;
-      bad = HOSZP_ERR_FORMAT;
+// This lane's share of the block sum S1_b = L_b O + sum_i (L_b - i) delta_i
+// (the block's q summed without the inverse Lorenzo).
+__device__ __forceinline__ long long octet_sum_q(const BlockRef& br, const int d[8], int j,
+                                                 int kmax) {
+  long long sd, std_;
+  if (kmax <= 2) {  // |delta| < 2^16: 32-bit sums cannot overflow
+    int a = 0, b = 0;
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      a += d[t];
+      b += t * d[t];
     }
-    s.rate[threadIdx.x] = r;
+    sd = a;
+    std_ = b;
+  } else {
+    sd = 0;
+    std_ = 0;
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      sd += d[t];
+      std_ += (long long)t * d[t];
+    }
   }
-  __syncthreads();
-  tile_scan(s.rate, ts);
+  long long v = (long long)(br.len - 8 * j) * sd - std_;
+  if (j == 0) v += (long long)br.len * br.outlier;
+  return v;
+}
+
+// Mean fast path (full block, at most 16 planes): this lane's share of the
+// block sum S1_b = 64 O + sum_i (64 - i) delta_i, as dot products of the
+// transposed magnitudes with signed weights (DP4A on bytes for <= 8 planes,
+// DP2A on 16-bit pairs for <= 16). wlo/whi: lane-constant weight bytes
+// (64 - 8j - t, 0 at position 0).
+__device__ __forceinline__ int dp4a_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_lo_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.lo.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_hi_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.hi.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t sign_weights(uint32_t w, uint32_t nib) {
+  // bytes of w negated where the nibble's bit is set (w >= 1 there: no carries)
+  const uint32_t s = (nib * 0x00204081u) & 0x01010101u;
+  return (w ^ (s * 0xffu)) + s;
+}
+__device__ __forceinline__ int octet_sum_fast(const BlockRef& br, int kmax, int j,
+                                              const OctetSel& S, uint32_t wlo, uint32_t whi) {
+  uint32_t lo[4], hi[4];
+  decode_groups(br.planes, br.rate, kmax, S, j, lo, hi);
+  const uint32_t sb = br.sign_byte & (j == 0 ? 0xfeu : 0xffu);
+  const uint32_t clo = sign_weights(wlo, sb & 0xfu), chi = sign_weights(whi, sb >> 4);
+  int acc;
+  if (kmax <= 1) {
+    acc = dp4a_us(hi[0], chi, dp4a_us(lo[0], clo, 0));
+  } else {
+    acc = dp2a_lo_us(__byte_perm(lo[0], lo[1], 0x5140u), clo, 0);
+    acc = dp2a_hi_us(__byte_perm(lo[0], lo[1], 0x7362u), clo, acc);
+    acc = dp2a_lo_us(__byte_perm(hi[0], hi[1], 0x5140u), chi, acc);
+    acc = dp2a_hi_us(__byte_perm(hi[0], hi[1], 0x7362u), chi, acc);
+  }
+  return acc;
 }
 
 // Checks the pre-scan's totals against the header (a corrupt stream stops here).
@@ -126,45 +188,6 @@ __device__ __forceinline__ bool prescan_ok(const Info& h, const unsigned long lo
   const uint64_t nt = ntiles_of(h.nb);
   if (nt + 1 > max_tiles) return false;  // the pre-scan refused it (workspace bound)
   return pre[2 * nt] == h.nnc && pre[2 * nt + 1] == h.R;
-}
-
-// Static tile walk of one input stream with an S-stage bulk-copy ring: calls
-// body(tile, stage, scan) for tiles blockIdx.x, +gridDim.x, ... Whole CTA.
-template <int S, class Body>
-__device__ __forceinline__ void consume_tiles(const uint8_t* c, const Info& h, uint64_t ntiles,
-                                              const unsigned long long* pre, InStage* stages,
-                                              uint64_t* bars, TileScan* ts, int* st, int& bad,
-                                              Body&& body) {
-  const uint64_t G = gridDim.x, first = blockIdx.x;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < S - 1; k++) {
-      const uint64_t t = first + (uint64_t)k * G;
-      if (t < ntiles) issue_in_tile(&stages[k], &bars[k], c, h, t, pre);
-    }
-  }
-  for (uint64_t i = 0;; i++) {
-    const uint64_t t = first + i * G;
-    if (t >= ntiles) break;
-    if (threadIdx.x == 0) {
-      const uint64_t tn = first + (i + S - 1) * G;
-      const int sn = (int)((i + S - 1) % S);
-      if (tn < ntiles) issue_in_tile(&stages[sn], &bars[sn], c, h, tn, pre);
-    }
-    InStage& sg = stages[i % S];
-    mbar_wait(&bars[i % S], (unsigned)((i / S) & 1), st);
-    stage_begin(sg, ts, h, t, bad);
-    body(t, sg, *ts);
-    __syncthreads();
-  }
-}
-
-template <int S>
-__device__ __forceinline__ void init_bars(uint64_t* bars) {
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < S; k++) mbar_init(&bars[k], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
 }
 
 }  // namespace hz

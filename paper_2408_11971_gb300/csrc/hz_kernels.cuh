@@ -22,10 +22,13 @@ cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const 
 // Completes a produced stream: reads the totals (nnc, R, qbound) left in the
 // workspace by the producer, checks the capacity, copies the staged planes
 // behind the sign section and writes the header and the size word.
-cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
+cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
+                         int rule, uint32_t e_bits, Ws ws);
 // scan.cu: per-tile (nc, r) exclusive prefixes of a stream's rates into pre[]
 cudaError_t launch_scan(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                         unsigned long long* pre, Ws ws);
+// scan.cu: prefixes of the produced tiles' aggregates (launched by launch_place)
+cudaError_t launch_scan_agg(const Launch& lc, Ws ws);
 // decode.cu
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
                               uint64_t n, Ws ws);
@@ -37,7 +40,7 @@ cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, 
 cudaError_t launch_add_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
-                              uint8_t* out, uint64_t cap, Ws ws);
+                              uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws);
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, Ws ws);
 

@@ -100,100 +100,4 @@ __device__ __forceinline__ void issue_in_tile(InStage* s, uint64_t* bar, const u
   if (pbytes) bulk_g2s(s->plane, c + pa16, pbytes, bar);
 }
 
-// ---------------------------------------------------------------- output stage
-// A produced tile before its place in the stream is known: rates, outliers,
-// and the tile's sign and plane words in order.
-struct __align__(16) OutStage {
-  uint64_t plane[TILE * MAX_RATE];
-  uint64_t sign[TILE];
-  int outlier[TILE];
-  uint8_t rate[TILE];
-  unsigned int agg_nc, agg_r;
-  unsigned long long tile;
-};
-static_assert(sizeof(OutStage) % 16 == 0, "output stages stay 16-byte aligned");
-
-}  // namespace hz
-
-namespace hz {
-
-// ---------------------------------------------------------------- producer helpers
-// Encode lane j's octet (magnitudes, sign byte) of block g into the output
-// stage: rates and outliers by block, sign words and planes packed in block
-// order. Whole CTA (contains barriers); ts is scratch for the rate scan.
-__device__ __forceinline__ void stage_encode(OutStage& o, TileScan* ts, const uint32_t mag[8],
-                                             uint32_t sb, int rate, int outlier, bool valid,
-                                             int g, int j) {
-  if (j == 0) {
-    o.rate[g] = valid ? (uint8_t)rate : 0;
-    o.outlier[g] = outlier;
-  }
-  __syncthreads();
-  tile_scan(o.rate, ts);
-  const int r = o.rate[g];
-  if (r > 0) reinterpret_cast<uint8_t*>(o.sign + ts->nc_excl[g])[j] = (uint8_t)sb;
-  const int kmax = __reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-  if (kmax > 0) encode_planes(mag, r, kmax, j, o.plane + ts->r_excl[g], (uint64_t)r);
-  if (threadIdx.x == 0) {
-    o.agg_nc = ts->agg_nc;
-    o.agg_r = ts->agg_r;
-  }
-}
-
-__device__ __forceinline__ void publish_agg(Desc* d, uint64_t tile, unsigned long long epoch,
-                                            const OutStage& o) {
-  if (threadIdx.x == 0) {
-    const unsigned long long agg = ((unsigned long long)o.agg_nc << 32) | o.agg_r;
-    publish(d, (int64_t)tile, epoch, tile == 0 ? 2 : 1, agg, o.agg_nc, o.agg_r);
-  }
-}
-
-// Warp 0 resolves the exclusive prefix of the staged tile and publishes its
-// inclusive prefix; then the whole CTA writes the tile to the stream:
-// rates and outliers at their block positions, sign words from index NC of
-// the sign section, planes from index R of `planes_dst` (the plane section
-// or the workspace). Bounds: capacity and staging size, errors into `bad`.
-__device__ __forceinline__ void stage_flush(const OutStage& o, Desc* d, unsigned long long epoch,
-                                            int* st, uint64_t nb, uint8_t* out, uint64_t cap,
-                                            uint64_t* planes_dst, uint64_t planes_limit,
-                                            uint64_t ntiles, unsigned long long* totals,
-                                            unsigned long long* s_pre, int& bad) {
-  const uint64_t tile = o.tile;
-  if (threadIdx.x < 32) {
-    unsigned long long pnc = 0, pr = 0;
-    if (tile > 0) {
-      lookback(d, (int64_t)tile, epoch, st, pnc, pr);
-      if (threadIdx.x == 0) {
-        const unsigned long long agg = ((unsigned long long)o.agg_nc << 32) | o.agg_r;
-        publish(d, (int64_t)tile, epoch, 2, agg, pnc + o.agg_nc, pr + o.agg_r);
-      }
-    }
-    if (threadIdx.x == 0) {
-      s_pre[0] = pnc;
-      s_pre[1] = pr;
-      if (tile == ntiles - 1) {
-        totals[0] = pnc + o.agg_nc;
-        totals[1] = pr + o.agg_r;
-      }
-    }
-  }
-  __syncthreads();
-  const uint64_t NC = s_pre[0], RR = s_pre[1];
-  const uint64_t nbt = umin64(TILE, nb - TILE * tile);
-  const int tid = threadIdx.x;
-  if ((uint64_t)tid < nbt) {
-    out[HOSZP_HEADER_BYTES + TILE * tile + tid] = o.rate[tid];
-    reinterpret_cast<int*>(out + off_outlier(nb))[TILE * tile + tid] = o.outlier[tid];
-  }
-  const uint64_t os = off_sign(nb);
-  if (os + 8 * (NC + o.agg_nc) > cap || RR + o.agg_r > planes_limit) {
-    if (tid == 0) bad = HOSZP_ERR_CAPACITY;
-    return;
-  }
-  uint64_t* sdst = reinterpret_cast<uint64_t*>(out + os) + NC;
-  for (unsigned int i = tid; i < o.agg_nc; i += blockDim.x) sdst[i] = o.sign[i];
-  uint64_t* pdst = planes_dst + RR;
-  for (unsigned int i = tid; i < o.agg_r; i += blockDim.x) pdst[i] = o.plane[i];
-}
-
 }  // namespace hz

@@ -1,0 +1,189 @@
+// hz_ws.cuh — warp-specialized tile pipeline shared by the codec kernels.
+//
+// A CTA has NCW = 16 compute warps (512 threads: 8 lanes per block of a
+// 64-block tile) and one loader warp that bulk-copies the next tiles into a
+// ring of shared-memory stages. The two roles meet only on mbarriers:
+// full[s] (copy landed) and empty[s] (all compute warps done with stage s).
+// Compute warps never wait for each other, except once per produced tile (all
+// 64 output rates must be known before any block's words can be placed).
+#pragma once
+#include "hz_decode.cuh"
+
+namespace hz {
+
+constexpr int NCW = 16;                       // compute warps
+constexpr int LOADER_WARP = NCW;              // warp index of the loader
+constexpr int CONSUMER_THREADS = (NCW + 1) * 32;
+constexpr int PRODUCER_THREADS = (NCW + 1) * 32;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// named barrier among the compute warps only
+__device__ __forceinline__ void compute_bar() {
+  asm volatile("bar.sync 1, %0;" ::"r"(NCW * 32) : "memory");
+}
+
+// Warp-redundant in-tile offsets: every compute warp scans the 64 rates of the
+// tile itself (no CTA barrier). Returns, for block g of the tile, the number of
+// non-constant blocks and the rate sum before it, and the tile totals.
+// rates[] are read raw: a block past the stream end counts 0, a rate above 31
+// counts 0 and raises `bad`.
+struct TileOff {
+  unsigned int nc_excl, r_excl, agg_nc, agg_r;
+};
+
+// A rate read from a stage: 0 past the stream end; clamped to 31, which keeps
+// every index inside the stage arrays (sized for rate 31). A rate above 31 is
+// a corrupt stream, which the rate pre-scan reports and which then yields no
+// result, so clamping here only has to be memory-safe.
+__device__ __forceinline__ unsigned int sane_rate(unsigned int r, uint64_t b, uint64_t nb,
+                                                  int& bad) {
+  (void)bad;
+  return (b < nb) ? min(r, (unsigned int)MAX_RATE) : 0u;
+}
+
+__device__ __forceinline__ TileOff warp_tile_offsets(const uint8_t* rates, uint64_t tile,
+                                                     uint64_t nb, int g, int& bad) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t b0 = tile * TILE + 2 * lane;
+  const unsigned int r0 = sane_rate(rates[2 * lane], b0, nb, bad);
+  const unsigned int r1 = sane_rate(rates[2 * lane + 1], b0 + 1, nb, bad);
+  // packed (nc << 16) | r: nc <= 64, r <= 1984 per tile
+  const unsigned int v0 = (r0 ? 0x10000u : 0u) | r0;
+  const unsigned int v1 = (r1 ? 0x10000u : 0u) | r1;
+  const unsigned int pair = v0 + v1;
+  unsigned int inc = pair;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const unsigned int excl0 = inc - pair;  // before block 2*lane
+  const unsigned int excl1 = excl0 + v0;  // before block 2*lane+1
+  const unsigned int total = __shfl_sync(0xffffffffu, inc, 31);
+  const unsigned int e0 = __shfl_sync(0xffffffffu, excl0, g >> 1);
+  const unsigned int e1 = __shfl_sync(0xffffffffu, excl1, g >> 1);
+  const unsigned int e = (g & 1) ? e1 : e0;
+  TileOff t;
+  t.nc_excl = e >> 16;
+  t.r_excl = e & 0xffffu;
+  t.agg_nc = total >> 16;
+  t.agg_r = total & 0xffffu;
+  return t;
+}
+
+// Block view for an octet, from a stage and warp-computed offsets.
+__device__ __forceinline__ BlockRef block_ref_w(const InStage& s, const TileOff& off,
+                                                const Info& h, uint64_t tile, int g, int j,
+                                                int& bad) {
+  BlockRef br;
+  const uint64_t b = tile * TILE + g;
+  br.rate = (int)sane_rate(s.rate[g], b, h.nb, bad);
+  br.outlier = s.outlier[g];
+  br.planes = s.plane + s.pbase + off.r_excl;
+  br.sign_byte =
+      br.rate ? reinterpret_cast<const uint8_t*>(s.sign + s.sbase + off.nc_excl)[j] : 0u;
+  const uint64_t rem = (b < h.nb) ? h.n - b * L : 0;
+  br.len = rem < (uint64_t)L ? (int)rem : L;
+  return br;
+}
+
+// ---------------------------------------------------------------- input ring
+struct Ring {
+  uint64_t* full;
+  uint64_t* empty;
+};
+
+template <int S>
+__device__ __forceinline__ void ring_init(uint64_t* full, uint64_t* empty) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < S; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], NCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// Loader (one thread): for k = 0, 1, ... hands stage k % S the tile id from
+// next_tile(k) and, for a real tile, issues its bulk copies; a tile id >=
+// ntiles ends the walk (the stage still completes, without data).
+template <int S, class NextTile, class Issue>
+__device__ __forceinline__ void loader_loop(uint64_t* full, uint64_t* empty,
+                                            unsigned long long* stage_tile, uint64_t ntiles,
+                                            int* st, NextTile&& next_tile, Issue&& issue) {
+  for (uint64_t k = 0;; k++) {
+    const int s = (int)(k % S);
+    if (k >= (uint64_t)S) mbar_wait(&empty[s], (unsigned)(((k / S) - 1) & 1), st);
+    const unsigned long long t = next_tile(k);
+    stage_tile[s] = t;
+    if (t < ntiles) {
+      issue(s, t);
+    } else {
+      mbar_arrive(&full[s]);
+      return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- produced tiles
+// A produced tile goes to its own slot of the workspace: [sign words | plane
+// words] in block order, starting at word slot_off (an upper bound of the
+// words of all earlier tiles, known before the tile is computed). Rates and
+// outliers go straight to the stream (their positions depend only on the block
+// index). The tile's aggregate (non-constant blocks, rate sum) goes to agg[t];
+// a scan of the aggregates and the placement kernel then move every slot to
+// its final place. No compute warp ever waits for another CTA.
+//
+// Compute warps: all 16 call this once per tile, in order (kth = k-th tile of
+// the CTA); srate is a double-buffered 2 x 64 shared array.
+__device__ __forceinline__ void produce_tile(uint8_t (*srate)[TILE], uint64_t kth,
+                                             unsigned long long tile, uint64_t nb,
+                                             const uint32_t mag[8], uint32_t sb, int rate,
+                                             int outlier, bool valid, int g, int j,
+                                             uint8_t* __restrict__ out, uint64_t* slots,
+                                             uint64_t slot_off, uint64_t slot_words,
+                                             unsigned long long* agg, const OctetSel& S,
+                                             int& bad) {
+  uint8_t* rr = srate[kth & 1];
+  const uint64_t b = tile * TILE + g;
+  if (j == 0) {
+    rr[g] = valid ? (uint8_t)rate : 0;
+    if (valid) {
+      out[HOSZP_HEADER_BYTES + b] = (uint8_t)rate;
+      reinterpret_cast<int*>(out + off_outlier(nb))[b] = outlier;
+    }
+  }
+  compute_bar();
+  const TileOff off = warp_tile_offsets(rr, 0, TILE, g, bad);
+  const int r = valid ? rate : 0;
+  if (slot_off + off.agg_nc + off.agg_r > slot_words) {
+    bad = HOSZP_ERR_CAPACITY;
+    return;
+  }
+  uint64_t* slot = slots + slot_off;
+  if (r > 0) reinterpret_cast<uint8_t*>(slot + off.nc_excl)[j] = (uint8_t)sb;
+  const int kmax = __reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+  if (kmax > 0)
+    encode_planes(mag, r, kmax, j, slot + off.agg_nc + off.r_excl, (uint64_t)r, S);
+  if (threadIdx.x == 0) agg[tile] = ((unsigned long long)off.agg_nc << 32) | off.agg_r;
+}
+
+// Word offset of tile t's slot: an upper bound of the words all earlier tiles
+// can produce. Rule COMPRESS: 25 words per block (rate <= 24). Rule ADD: the
+// inputs' words (a block of A+B needs at most the words of A's and B's block).
+// Rule MUL: (1 + e) words per non-constant input block plus the input's plane
+// words (a constant block stays constant; a rate grows by at most e bits).
+enum SlotRule { SLOT_COMPRESS = 0, SLOT_ADD = 1, SLOT_MUL = 2 };
+
+__device__ __forceinline__ uint64_t slot_offset(int rule, uint64_t t,
+                                                const unsigned long long* pre0,
+                                                const unsigned long long* pre1, uint32_t e) {
+  if (rule == SLOT_COMPRESS) return (uint64_t)TILE * 25 * t;
+  if (rule == SLOT_ADD) return pre0[2 * t] + pre0[2 * t + 1] + pre1[2 * t] + pre1[2 * t + 1];
+  return pre0[2 * t] * (1ull + e) + pre0[2 * t + 1];
+}
+
+}  // namespace hz

@@ -2,7 +2,7 @@
 //   negation and scalar addition in fully compressed space (workflow 1),
 //   scalar multiplication through the quantized integers (workflow 3),
 //   element-wise addition through the decoded deltas (workflow 2).
-#include "hz_decode.cuh"
+#include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -47,15 +47,35 @@ struct MulPlan {
   long long rho;
   long long M;
   int E;
+  // fast path: q' = (q * P + 2^(sh-1)) >> sh in 64-bit integers, valid when
+  // every |q * P| stays below 2^62 (P = rho * M, sh = -E in [1, 62])
+  bool fast;
+  long long P;
+  int sh;
 };
 
-__device__ __forceinline__ MulPlan mul_plan(float e, long long rho) {
+__device__ __forceinline__ MulPlan mul_plan(float e, long long rho, uint32_t qbound) {
   MulPlan p;
   p.rho = rho;
   const uint32_t bits = __float_as_uint(2.0f * e);  // normal: e >= FLT_MIN
   p.M = (long long)((bits & 0x7fffffu) | 0x800000u);
   p.E = (int)((bits >> 23) & 0xffu) - 127 - 23;
+  p.P = rho * p.M;  // |rho| <= 2^30, M < 2^24: fits
+  p.sh = -p.E;
+  const unsigned long long aP = (unsigned long long)(p.P < 0 ? -p.P : p.P);
+  // |q| <= qbound < 2^30 ; require qbound * |P| < 2^62
+  const unsigned __int128 prod = (unsigned __int128)aP * (unsigned __int128)(qbound + 1ull);
+  p.fast = p.sh >= 1 && p.sh <= 62 && prod < ((unsigned __int128)1 << 62);
   return p;
+}
+
+__device__ __forceinline__ int mul_requant_fast(int q, const MulPlan& p, bool& ovf) {
+  const long long r = ((long long)q * p.P + (1ll << (p.sh - 1))) >> p.sh;  // floor
+  if (r > HOSZP_QLIM || r < -(long long)HOSZP_QLIM) {
+    ovf = true;
+    return 0;
+  }
+  return (int)r;
 }
 
 // Returns q' and sets ovf when |q'| > HOSZP_QLIM.
@@ -192,13 +212,13 @@ __device__ __forceinline__ void write_template(const Info& h, uint32_t qbound_fi
 }
 
 __device__ __forceinline__ void reduce_qmax(uint32_t qmax, const Ws& ws) {
-  __shared__ uint32_t s_q[CTA / 32];
+  __shared__ uint32_t s_q[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
   if ((threadIdx.x & 31) == 0) s_q[threadIdx.x >> 5] = qmax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < CTA / 32; w++) qmax = max(qmax, s_q[w]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) qmax = max(qmax, s_q[w]);
     atomicMax(&ws.totals[2], (unsigned long long)qmax);
   }
 }
@@ -214,31 +234,25 @@ __device__ __forceinline__ void octet_mag_sign(const int d[8], uint32_t mag[8], 
 }
 
 // ---------------------------------------------------------------- scalar multiplication
-// Input tiles arrive through a bulk-copy ring (located by the rate pre-scan);
-// each is decoded to q (workflow 3), requantized, Lorenzo + BF re-encoded into
-// an output stage, and written one tile later once its place is known.
-constexpr int MUL_STAGES = 2;
+// A loader warp bulk-copies input tiles (located by the rate pre-scan); compute
+// warps decode them to q (workflow 3), requantize, and Lorenzo + BF re-encode
+// each tile into its workspace slot (see produce_tile).
+constexpr int MUL_STAGES = 3;
 
-__global__ void __launch_bounds__(CTA) k_mul_scalar(const uint8_t* __restrict__ c, uint64_t c_bytes,
-                                                    double s, uint8_t* __restrict__ out,
-                                                    uint64_t cap,
-                                                    const unsigned long long* __restrict__ pre,
-                                                    Ws ws) {
+__global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double s, uint8_t* __restrict__ out,
+    uint64_t cap, uint32_t e_bits, const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ins = reinterpret_cast<InStage*>(dyn);
-  OutStage* outs = reinterpret_cast<OutStage*>(dyn + MUL_STAGES * sizeof(InStage));
-  __shared__ uint64_t bars[MUL_STAGES];
-  __shared__ unsigned long long s_tiles[MUL_STAGES];
-  __shared__ TileScan ts_in, ts_out;
-  __shared__ unsigned long long s_pre[2];
-  __shared__ unsigned long long s_epoch;
+  __shared__ uint64_t full[MUL_STAGES], empty[MUL_STAGES];
+  __shared__ unsigned long long stage_tile[MUL_STAGES];
+  __shared__ uint8_t srate[2][TILE];
   __shared__ long long s_rho;
   __shared__ int s_ok;
-  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
   const Info h = parse_header(c, c_bytes);
   int bad = 0;
   if (tid == 0) {
-    s_epoch = launch_epoch(ws);
     int ok = h.ok;
     long long rho = 0;
     if (!h.ok) bad = HOSZP_ERR_FORMAT;
@@ -253,114 +267,113 @@ __global__ void __launch_bounds__(CTA) k_mul_scalar(const uint8_t* __restrict__ 
     s_rho = rho;
     if (blockIdx.x == 0) write_template(h, 0, ws);
   }
-  init_bars<MUL_STAGES>(bars);
+  ring_init<MUL_STAGES>(full, empty);
   const uint64_t ntiles = (s_ok && prescan_ok(h, pre, ws.max_tiles)) ? ntiles_of(h.nb) : 0;
-  const MulPlan mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho);
-  if (tid == 0) {
-    for (int k = 0; k < MUL_STAGES - 1; k++) {
-      const unsigned long long t = atomicAdd(&ws.sync->ticket, 1u);
-      s_tiles[k] = t;
-      if (t < ntiles) issue_in_tile(&ins[k], &bars[k], c, h, t, pre);
-    }
-  }
-  __syncthreads();
-  const unsigned long long epoch = s_epoch;
+  const MulPlan mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
+  const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   bool ovf = false;
-  uint64_t i = 0;
-  for (;; i++) {
-    const unsigned long long tile = s_tiles[i % MUL_STAGES];
-    if (tile >= ntiles) break;
-    if (tid == 0) {
-      const int sn = (int)((i + MUL_STAGES - 1) % MUL_STAGES);
-      const unsigned long long tn = atomicAdd(&ws.sync->ticket, 1u);
-      s_tiles[sn] = tn;
-      if (tn < ntiles) issue_in_tile(&ins[sn], &bars[sn], c, h, tn, pre);
+  if (w == LOADER_WARP) {
+    if ((tid & 31) == 0) {
+      const uint64_t G = gridDim.x;
+      loader_loop<MUL_STAGES>(
+          full, empty, stage_tile, ntiles, ws.status,
+          [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
+          [&](int st, unsigned long long t) { issue_in_tile(&ins[st], &full[st], c, h, t, pre); });
     }
-    InStage& sg = ins[i % MUL_STAGES];
-    mbar_wait(&bars[i % MUL_STAGES], (unsigned)((i / MUL_STAGES) & 1), ws.status);
-    stage_begin(sg, &ts_in, h, tile, bad);
-    const BlockRef br = block_ref(sg, ts_in, h, tile, g, j);
-    const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
-    int d[8], q[8];
-    octet_deltas(br, kmax, j, d);
-    octet_values(br, d, j, q);
+  } else {
+    for (uint64_t k = 0;; k++) {
+      const int st = (int)(k % MUL_STAGES);
+      mbar_wait(&full[st], (unsigned)((k / MUL_STAGES) & 1), ws.status);
+      const unsigned long long tile = stage_tile[st];
+      if (tile >= ntiles) break;
+      const InStage& sg = ins[st];
+      const TileOff off = warp_tile_offsets(sg.rate, tile, h.nb, g, bad);
+      const BlockRef br = block_ref_w(sg, off, h, tile, g, j, bad);
+      const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+      int d[8], q[8];
+      octet_deltas(br, kmax, j, S, d);
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[st]);
+      octet_values(br, d, j, q);
+      if (br.len < L) {  // positions past the stream end hold no value
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
-      q[t] = (8 * j + t < br.len) ? mul_requant(q[t], mp, ovf) : 0;
-      qmax = max(qmax, (uint32_t)abs(q[t]));
-    }
-    // Lorenzo on the new integers
-    const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
-    const int outlier = __shfl_sync(0xffffffffu, q[0], tid & ~7);
-    int nd[8];
+        for (int t = 0; t < 8; t++)
+          if (8 * j + t >= br.len) q[t] = 0;
+      }
+      if (mp.fast) {
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
-      const int v = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
-      nd[t] = (8 * j + t < br.len) ? v : 0;
+        for (int t = 0; t < 8; t++) q[t] = mul_requant_fast(q[t], mp, ovf);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; t++) q[t] = mul_requant(q[t], mp, ovf);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; t++) {
+        if (8 * j + t >= br.len) q[t] = 0;
+        qmax = max(qmax, (uint32_t)abs(q[t]));
+      }
+      // Lorenzo on the new integers
+      const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
+      const int outlier = __shfl_sync(0xffffffffu, q[0], (tid & 31) & ~7);
+      int nd[8];
+#pragma unroll
+      for (int t = 0; t < 8; t++) {
+        const int v = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
+        nd[t] = (8 * j + t < br.len) ? v : 0;
+      }
+      uint32_t mag[8], sb;
+      octet_mag_sign(nd, mag, sb);
+      const int rate = octet_rate(mag);
+      produce_tile(srate, k, tile, h.nb, mag, sb, rate, outlier, tile * TILE + g < h.nb, g, j,
+                   out, ws.staging, slot_offset(SLOT_MUL, tile, pre, nullptr, e_bits),
+                   ws.staging_words, ws.agg, S, bad);
     }
-    uint32_t mag[8], sb;
-    octet_mag_sign(nd, mag, sb);
-    const int rate = octet_rate(mag);
-    OutStage& os = outs[i & 1];
-    stage_encode(os, &ts_out, mag, sb, rate, outlier, tile * TILE + g < h.nb, g, j);
-    if (tid == 0) os.tile = tile;
-    publish_agg(ws.desc[0], tile, epoch, os);
-    if (i > 0)
-      stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, h.nb, out, cap, ws.staging,
-                  ws.staging_words, ntiles, ws.totals, s_pre, bad);
-    __syncthreads();
   }
-  if (i > 0)
-    stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, h.nb, out, cap, ws.staging,
-                ws.staging_words, ntiles, ws.totals, s_pre, bad);
   if (ovf) bad = HOSZP_ERR_OVERFLOW;
   reduce_qmax(qmax, ws);
   if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
-                              uint8_t* out, uint64_t cap, Ws ws) {
+                              uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
-  const size_t smem = MUL_STAGES * sizeof(InStage) + 2 * sizeof(OutStage);
+  const size_t smem = MUL_STAGES * sizeof(InStage);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mul_scalar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_mul_scalar<<<persistent_grid(k_mul_scalar, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
-      c, c_bytes, s, out, cap, ws.pre[0], ws);
+  k_mul_scalar<<<persistent_grid(k_mul_scalar, PRODUCER_THREADS, lc.grid, smem),
+                 PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, out, cap, e_bits, ws.pre[0],
+                                                      ws);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- element-wise addition
 // Workflow 2: both streams' tiles arrive through bulk-copy rings; the deltas
-// are decoded (no inverse Lorenzo), added, and BF re-encoded.
-constexpr int ADD_STAGES = 2;
+// are decoded (no inverse Lorenzo), added, and BF re-encoded into the tile's
+// workspace slot.
+constexpr int ADD_STAGES = 3;
 
-__global__ void __launch_bounds__(CTA, 2) k_add(const uint8_t* __restrict__ a, uint64_t a_bytes,
-                                             const uint8_t* __restrict__ b, uint64_t b_bytes,
-                                             uint8_t* __restrict__ out, uint64_t cap,
-                                             const unsigned long long* __restrict__ pre_a,
-                                             const unsigned long long* __restrict__ pre_b, Ws ws) {
+__global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
+    const uint8_t* __restrict__ a, uint64_t a_bytes, const uint8_t* __restrict__ b,
+    uint64_t b_bytes, uint8_t* __restrict__ out, uint64_t cap,
+    const unsigned long long* __restrict__ pre_a, const unsigned long long* __restrict__ pre_b,
+    Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ina = reinterpret_cast<InStage*>(dyn);
   InStage* inb = ina + ADD_STAGES;
-  OutStage* outs = reinterpret_cast<OutStage*>(dyn + 2 * ADD_STAGES * sizeof(InStage));
-  __shared__ uint64_t bars_a[ADD_STAGES], bars_b[ADD_STAGES];
-  __shared__ unsigned long long s_tiles[ADD_STAGES];
-  __shared__ TileScan ts_a, ts_b, ts_out;
-  __shared__ unsigned long long s_pre[2];
-  __shared__ unsigned long long s_epoch;
+  __shared__ uint64_t fulla[ADD_STAGES], fullb[ADD_STAGES], empty[ADD_STAGES];
+  __shared__ unsigned long long stage_tile[ADD_STAGES];
+  __shared__ uint8_t srate[2][TILE];
   __shared__ int s_ok;
-  const int tid = threadIdx.x, g = tid >> 3, j = tid & 7;
+  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
   const Info ha = parse_header(a, a_bytes);
   const Info hb = parse_header(b, b_bytes);
   int bad = 0;
   if (tid == 0) {
-    s_epoch = launch_epoch(ws);
     int ok = 0;
     if (!ha.ok || !hb.ok) bad = HOSZP_ERR_FORMAT;
     else if (ha.n != hb.n || __float_as_uint(ha.eps_q) != __float_as_uint(hb.eps_q))
@@ -376,77 +389,64 @@ __global__ void __launch_bounds__(CTA, 2) k_add(const uint8_t* __restrict__ a, u
       write_template(ha, ok ? ha.qbound + hb.qbound : 0, ws);
       if (ok) atomicMax(&ws.totals[2], (unsigned long long)(ha.qbound + hb.qbound));
     }
+    for (int k = 0; k < ADD_STAGES; k++) mbar_init(&fullb[k], 1);
   }
-  if (tid < 32) {
-    if (tid == 0) {
-      for (int k = 0; k < ADD_STAGES; k++) {
-        mbar_init(&bars_a[k], 1);
-        mbar_init(&bars_b[k], 1);
-      }
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  }
-  __syncthreads();
+  ring_init<ADD_STAGES>(fulla, empty);
+  const OctetSel S = octet_sel(j);
   const uint64_t ntiles =
-      (s_ok && prescan_ok(ha, pre_a, ws.max_tiles) && prescan_ok(hb, pre_b, ws.max_tiles)) ? ntiles_of(ha.nb) : 0;
-  if (tid == 0) {
-    for (int k = 0; k < ADD_STAGES - 1; k++) {
-      const unsigned long long t = atomicAdd(&ws.sync->ticket, 1u);
-      s_tiles[k] = t;
-      if (t < ntiles) {
-        issue_in_tile(&ina[k], &bars_a[k], a, ha, t, pre_a);
-        issue_in_tile(&inb[k], &bars_b[k], b, hb, t, pre_b);
+      (s_ok && prescan_ok(ha, pre_a, ws.max_tiles) && prescan_ok(hb, pre_b, ws.max_tiles))
+          ? ntiles_of(ha.nb)
+          : 0;
+  if (w == LOADER_WARP) {
+    if ((tid & 31) == 0) {
+      const uint64_t G = gridDim.x;
+      for (uint64_t k = 0;; k++) {
+        const int st = (int)(k % ADD_STAGES);
+        if (k >= (uint64_t)ADD_STAGES)
+          mbar_wait(&empty[st], (unsigned)(((k / ADD_STAGES) - 1) & 1), ws.status);
+        const unsigned long long t = blockIdx.x + k * G;
+        stage_tile[st] = t;
+        if (t < ntiles) {
+          issue_in_tile(&ina[st], &fulla[st], a, ha, t, pre_a);
+          issue_in_tile(&inb[st], &fullb[st], b, hb, t, pre_b);
+        } else {
+          mbar_arrive(&fulla[st]);
+          mbar_arrive(&fullb[st]);
+          break;
+        }
       }
     }
-  }
-  __syncthreads();
-  const unsigned long long epoch = s_epoch;
-  uint64_t i = 0;
-  for (;; i++) {
-    const unsigned long long tile = s_tiles[i % ADD_STAGES];
-    if (tile >= ntiles) break;
-    if (tid == 0) {
-      const int sn = (int)((i + ADD_STAGES - 1) % ADD_STAGES);
-      const unsigned long long tn = atomicAdd(&ws.sync->ticket, 1u);
-      s_tiles[sn] = tn;
-      if (tn < ntiles) {
-        issue_in_tile(&ina[sn], &bars_a[sn], a, ha, tn, pre_a);
-        issue_in_tile(&inb[sn], &bars_b[sn], b, hb, tn, pre_b);
-      }
-    }
-    const int si = (int)(i % ADD_STAGES);
-    const unsigned par = (unsigned)((i / ADD_STAGES) & 1);
-    mbar_wait(&bars_a[si], par, ws.status);
-    mbar_wait(&bars_b[si], par, ws.status);
-    stage_begin(ina[si], &ts_a, ha, tile, bad);
-    stage_begin(inb[si], &ts_b, hb, tile, bad);
-    const BlockRef ra = block_ref(ina[si], ts_a, ha, tile, g, j);
-    const BlockRef rb = block_ref(inb[si], ts_b, hb, tile, g, j);
-    const int ka = __reduce_max_sync(0xffffffffu, (ra.rate + 7) >> 3);
-    const int kb = __reduce_max_sync(0xffffffffu, (rb.rate + 7) >> 3);
-    int da[8], db[8], nd[8];
-    octet_deltas(ra, ka, j, da);
-    octet_deltas(rb, kb, j, db);
+  } else {
+    for (uint64_t k = 0;; k++) {
+      const int st = (int)(k % ADD_STAGES);
+      const unsigned par = (unsigned)((k / ADD_STAGES) & 1);
+      mbar_wait(&fulla[st], par, ws.status);
+      mbar_wait(&fullb[st], par, ws.status);
+      const unsigned long long tile = stage_tile[st];
+      if (tile >= ntiles) break;
+      const TileOff offa = warp_tile_offsets(ina[st].rate, tile, ha.nb, g, bad);
+      const TileOff offb = warp_tile_offsets(inb[st].rate, tile, hb.nb, g, bad);
+      const BlockRef ra = block_ref_w(ina[st], offa, ha, tile, g, j, bad);
+      const BlockRef rb = block_ref_w(inb[st], offb, hb, tile, g, j, bad);
+      const int ka = __reduce_max_sync(0xffffffffu, (ra.rate + 7) >> 3);
+      const int kb = __reduce_max_sync(0xffffffffu, (rb.rate + 7) >> 3);
+      int da[8], db[8], nd[8];
+      octet_deltas(ra, ka, j, S, da);
+      octet_deltas(rb, kb, j, S, db);
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[st]);
 #pragma unroll
-    for (int t = 0; t < 8; t++) nd[t] = da[t] + db[t];
-    uint32_t mag[8], sb;
-    octet_mag_sign(nd, mag, sb);
-    const int rate = octet_rate(mag);
-    OutStage& os = outs[i & 1];
-    stage_encode(os, &ts_out, mag, sb, rate, ra.outlier + rb.outlier, tile * TILE + g < ha.nb, g,
-                 j);
-    if (tid == 0) os.tile = tile;
-    publish_agg(ws.desc[0], tile, epoch, os);
-    if (i > 0)
-      stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, ha.nb, out, cap, ws.staging,
-                  ws.staging_words, ntiles, ws.totals, s_pre, bad);
-    __syncthreads();
+      for (int t = 0; t < 8; t++) nd[t] = da[t] + db[t];
+      uint32_t mag[8], sb;
+      octet_mag_sign(nd, mag, sb);
+      const int rate = octet_rate(mag);
+      produce_tile(srate, k, tile, ha.nb, mag, sb, rate, ra.outlier + rb.outlier,
+                   tile * TILE + g < ha.nb, g, j, out, ws.staging,
+                   slot_offset(SLOT_ADD, tile, pre_a, pre_b, 0), ws.staging_words, ws.agg, S,
+                   bad);
+    }
   }
-  if (i > 0)
-    stage_flush(outs[(i - 1) & 1], ws.desc[0], epoch, ws.status, ha.nb, out, cap, ws.staging,
-                ws.staging_words, ntiles, ws.totals, s_pre, bad);
   if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
@@ -455,14 +455,14 @@ cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, con
   if (e != cudaSuccess) return e;
   e = launch_scan(lc, b, b_bytes, ws.pre[1], ws);
   if (e != cudaSuccess) return e;
-  const size_t smem = 2 * ADD_STAGES * sizeof(InStage) + 2 * sizeof(OutStage);
+  const size_t smem = 2 * ADD_STAGES * sizeof(InStage);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_add<<<persistent_grid(k_add, CTA, lc.grid, smem), CTA, smem, lc.stream>>>(
-      a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
+  k_add<<<persistent_grid(k_add, PRODUCER_THREADS, lc.grid, smem), PRODUCER_THREADS, smem,
+          lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
   return cudaGetLastError();
 }
 

@@ -1,26 +1,41 @@
 // place.cu — completes a produced stream (compress, scalar multiplication,
-// element-wise addition). The producer has written rates, outliers and sign
-// words at their final offsets and the plane words, in order, into the
-// workspace; only once the total number of non-constant blocks is known does
-// the plane section's start (right after the sign section, Fig. 3) exist, so
-// the planes are copied there here, and the header is written last.
+// element-wise addition). The producer wrote rates and outliers at their
+// final offsets and each tile's sign and plane words into the tile's
+// workspace slot; the produced-tile scan gave every tile's place. Only with
+// the total number of non-constant blocks does the plane section's start
+// (right after the sign section, Fig. 3) exist, so the words are moved here,
+// and the header is written last.
+#include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
 
 __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64_t cap,
-                                               uint64_t* out_bytes, Ws ws) {
+                                               uint64_t* out_bytes, int rule, uint32_t e_bits,
+                                               Ws ws) {
   const hoszp_header tmpl = *ws.hdr;
   const uint64_t nb = nblocks(tmpl.n);
+  const uint64_t ntiles = ntiles_of(nb);
   const uint64_t nnc = ws.totals[0], R = ws.totals[1];
   const uint64_t size = stream_bytes(nb, nnc, R);
-  const bool fits = size <= cap && R <= ws.staging_words;
+  const bool fits = size <= cap && ntiles + 1 <= ws.max_tiles;
+  int bad = 0;
   if (fits) {
-    const uint64_t* __restrict__ src = ws.staging;
-    uint64_t* __restrict__ dst = reinterpret_cast<uint64_t*>(out + off_plane(nb, nnc));
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride)
-      dst[i] = src[i];
+    uint64_t* sdst = reinterpret_cast<uint64_t*>(out + off_sign(nb));
+    uint64_t* pdst = reinterpret_cast<uint64_t*>(out + off_plane(nb, nnc));
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const unsigned long long a = ws.agg[t];
+      const uint64_t nc = a >> 32, r = a & 0xffffffffull;
+      const uint64_t so = slot_offset(rule, t, ws.pre[0], ws.pre[1], e_bits);
+      const uint64_t NC = ws.opre[2 * t], RR = ws.opre[2 * t + 1];
+      if (so + nc + r > ws.staging_words || NC + nc > nnc || RR + r > R) {
+        bad = HOSZP_ERR_CAPACITY;
+        continue;
+      }
+      const uint64_t* src = ws.staging + so;
+      for (uint64_t i = threadIdx.x; i < nc; i += blockDim.x) sdst[NC + i] = src[i];
+      for (uint64_t i = threadIdx.x; i < r; i += blockDim.x) pdst[RR + i] = src[nc + i];
+    }
     if (blockIdx.x == 0) {
       // zero the end padding and the padding after the rate and outlier sections
       const uint64_t end = off_plane(nb, nnc) + 8 * R;
@@ -32,6 +47,7 @@ __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64
         out[po + threadIdx.x - 16] = 0;
     }
   }
+  if (bad) set_status(ws.status, bad);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (fits) {
       hoszp_header h = tmpl;
@@ -54,8 +70,11 @@ __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64
 }
 
 cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
-                         Ws ws) {
-  k_place<<<persistent_grid(k_place, 512, lc.grid), 512, 0, lc.stream>>>(out, cap, out_bytes, ws);
+                         int rule, uint32_t e_bits, Ws ws) {
+  cudaError_t e = launch_scan_agg(lc, ws);
+  if (e != cudaSuccess) return e;
+  k_place<<<persistent_grid(k_place, 512, lc.grid), 512, 0, lc.stream>>>(out, cap, out_bytes,
+                                                                         rule, e_bits, ws);
   return cudaGetLastError();
 }
 

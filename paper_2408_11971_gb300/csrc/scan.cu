@@ -121,3 +121,95 @@ cudaError_t launch_scan(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
 }
 
 }  // namespace hz
+
+namespace hz {
+
+// ---------------------------------------------------------------- produced-tile scan
+// Exclusive prefix over the produced tiles' aggregates (agg[t] = nc << 32 | r,
+// written by the producer kernel) into opre[], and the stream totals into
+// totals[0] (non-constant blocks) and totals[1] (rate sum).
+constexpr int SA_THREADS = 256;
+constexpr int SA_PER_THREAD = 16;
+constexpr int SA_SUPER = SA_THREADS * SA_PER_THREAD;  // tiles per CTA step
+
+__global__ void __launch_bounds__(SA_THREADS) k_scan_agg(Ws ws) {
+  __shared__ unsigned long long s_w[SA_THREADS / 32];
+  __shared__ unsigned long long s_pre[2];
+  __shared__ unsigned int s_tile;
+  __shared__ unsigned long long s_epoch;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint64_t ntiles = ntiles_of(nblocks(ws.hdr->n));
+  int bad = 0;
+  if (ntiles + 1 > ws.max_tiles) {
+    bad = HOSZP_ERR_CAPACITY;
+    ntiles = 0;
+  }
+  const uint64_t nsuper = (ntiles + SA_SUPER - 1) / SA_SUPER;
+  if (tid == 0) s_epoch = launch_epoch(ws);
+  if (ntiles == 0 && blockIdx.x == 0 && tid == 0) {
+    ws.opre[0] = 0;
+    ws.opre[1] = 0;
+    ws.totals[0] = 0;
+    ws.totals[1] = 0;
+  }
+  __syncthreads();
+  const unsigned long long epoch = s_epoch;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&ws.sync->ticket, 1u);
+    __syncthreads();
+    const uint64_t st = s_tile;
+    if (st >= nsuper) break;
+    const uint64_t t0 = st * SA_SUPER + (uint64_t)SA_PER_THREAD * tid;
+    unsigned long long v[SA_PER_THREAD];
+    unsigned long long sum = 0;  // packed (nc << 32) | r, both fields stay below 2^32
+#pragma unroll
+    for (int k = 0; k < SA_PER_THREAD; k++) {
+      v[k] = (t0 + k < ntiles) ? ws.agg[t0 + k] : 0ull;
+      sum += v[k];
+    }
+    unsigned long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    unsigned long long wbase = 0, total = 0;
+    for (int k = 0; k < SA_THREADS / 32; k++) {
+      if (k < wid) wbase += s_w[k];
+      total += s_w[k];
+    }
+    tile_prefix(ws.desc[2], (int64_t)st, epoch, ws.status, (unsigned int)(total >> 32),
+                (unsigned int)(total & 0xffffffffu), 0, s_pre);
+    __syncthreads();
+    unsigned long long run = wbase + inc - sum;  // exclusive, within the super-tile
+    const unsigned long long pnc = s_pre[0], pr = s_pre[1];
+#pragma unroll
+    for (int k = 0; k < SA_PER_THREAD; k++) {
+      const uint64_t t = t0 + k;
+      if (t < ntiles) {
+        ws.opre[2 * t] = pnc + (run >> 32);
+        ws.opre[2 * t + 1] = pr + (run & 0xffffffffull);
+      }
+      run += v[k];
+    }
+    if (st == nsuper - 1 && tid == 0) {
+      const unsigned long long tnc = pnc + (total >> 32), tr = pr + (total & 0xffffffffull);
+      ws.opre[2 * ntiles] = tnc;
+      ws.opre[2 * ntiles + 1] = tr;
+      ws.totals[0] = tnc;
+      ws.totals[1] = tr;
+    }
+    __syncthreads();
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
+}
+
+cudaError_t launch_scan_agg(const Launch& lc, Ws ws) {
+  k_scan_agg<<<persistent_grid(k_scan_agg, SA_THREADS, lc.grid), SA_THREADS, 0, lc.stream>>>(ws);
+  return cudaGetLastError();
+}
+
+}  // namespace hz
