@@ -99,7 +99,7 @@ cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double re
 // shared-memory ring while the current tile is quantized and encoded into an
 // output stage; a tile's place in the stream (look-back over the tiles before
 // it) is resolved one tile later, so the look-back latency overlaps compute.
-constexpr int CMP_STAGES = 3;
+constexpr int CMP_STAGES = 4;
 
 struct InX {
   float v[TILE_VALUES];
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
     uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InX* ins = reinterpret_cast<InX*>(dyn);
-  __shared__ uint64_t full[CMP_STAGES], empty[CMP_STAGES];
+  __shared__ uint64_t full[CMP_STAGES], ready[CMP_STAGES], empty[CMP_STAGES];
   __shared__ unsigned long long stage_tile[CMP_STAGES];
   __shared__ uint8_t srate[2][TILE];
   __shared__ unsigned int s_qmax[PRODUCER_THREADS / 32];
@@ -152,22 +152,22 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
     H->qbound = 0;
     H->block = HOSZP_BLOCK;
   }
-  ring_init<CMP_STAGES>(full, empty);
+  ring_init3<CMP_STAGES>(full, ready, empty);
   const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   int bad = 0;
   if (w == LOADER_WARP) {
-    if ((tid & 31) == 0) {
-      const uint64_t G = gridDim.x;
-      loader_loop<CMP_STAGES>(
-          full, empty, stage_tile, ntiles, ws.status,
-          [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
-          [&](int s, unsigned long long t) { issue_x(&ins[s], &full[s], x, n, t); });
-    }
+    const uint64_t G = gridDim.x;
+    loader_warp<CMP_STAGES>(
+        stage_tile, full, ready, empty, ntiles, ws.status,
+        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
+        [&](int sk, unsigned long long t) { issue_x(&ins[sk], &full[sk], x, n, t); },
+        [&](int, unsigned long long) {});
   } else {
+    RingPos rp{0, 0u};
     for (uint64_t k = 0;; k++) {
-      const int s = (int)(k % CMP_STAGES);
-      mbar_wait(&full[s], (unsigned)((k / CMP_STAGES) & 1), ws.status);
+      const int s = rp.s;
+      mbar_wait(&ready[s], rp.par, ws.status);
       const unsigned long long tile = stage_tile[s];
       if (tile >= ntiles) break;
       const InX& in = ins[s];
@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
       }
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      rp.next<CMP_STAGES>();
       int q[8];
 #pragma unroll
       for (int t = 0; t < 8; t++) {

@@ -9,14 +9,14 @@
 namespace hz {
 
 // ---------------------------------------------------------------- decompression
-constexpr int DEC_STAGES = 3;
+constexpr int DEC_STAGES = 6;
 
 __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
     const uint8_t* __restrict__ c, uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect,
     const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* stages = reinterpret_cast<InStage*>(dyn);
-  __shared__ uint64_t full[DEC_STAGES], empty[DEC_STAGES];
+  __shared__ uint64_t full[DEC_STAGES], ready[DEC_STAGES], empty[DEC_STAGES];
   __shared__ unsigned long long stage_tile[DEC_STAGES];
   const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
   const Info h = parse_header(c, c_bytes);
@@ -28,43 +28,41 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
   const float e2 = 2.0f * h.eps_q;
   const bool small = h.qbound < (1u << 22);
   const OctetSel S = octet_sel(j);
-  ring_init<DEC_STAGES>(full, empty);
+  ring_init3<DEC_STAGES>(full, ready, empty);
   if (w == LOADER_WARP) {
-    if ((tid & 31) == 0) {
-      const uint64_t G = gridDim.x;
-      loader_loop<DEC_STAGES>(full, empty, stage_tile, ntiles, ws.status,
-                              [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
-                              [&](int s, unsigned long long t) {
-                                issue_in_tile(&stages[s], &full[s], c, h, t, pre);
-                              });
-    }
+    const uint64_t G = gridDim.x;
+    loader_warp<DEC_STAGES>(
+        stage_tile, full, ready, empty, ntiles, ws.status,
+        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
+        [&](int sk, unsigned long long t) { issue_in_tile(&stages[sk], &full[sk], c, h, t, pre); },
+        [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
   } else {
-    for (uint64_t k = 0;; k++) {
-      const int s = (int)(k % DEC_STAGES);
-      mbar_wait(&full[s], (unsigned)((k / DEC_STAGES) & 1), ws.status);
-      const unsigned long long tile = stage_tile[s];
+    RingPos rp{0, 0u};
+    for (;;) {
+      mbar_wait(&ready[rp.s], rp.par, ws.status);
+      const unsigned long long tile = stage_tile[rp.s];
       if (tile >= ntiles) break;
-      const InStage& sg = stages[s];
-      const TileOff off = warp_tile_offsets(sg.rate, tile, h.nb, g, bad);
-      const BlockRef br = block_ref_w(sg, off, h, tile, g, j, bad);
-      const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+      const InStage& sg = stages[rp.s];
+      const BlockRef br = block_ref_s(sg, g, j);
+      const int kmax = sg.kmx[w];
       int d[8], q[8];
       octet_deltas(br, kmax, j, S, d);
       __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      if ((tid & 31) == 0) mbar_arrive(&empty[rp.s]);
+      rp.next<DEC_STAGES>();
       octet_values(br, d, j, q);
       const uint64_t i0 = (tile * TILE + g) * L + 8 * j;
       float v[8];
 #pragma unroll
       for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
-      if (i0 + 8 <= h.n) {
+      if (br.len == L) {
         float4* o = reinterpret_cast<float4*>(x + i0);
         o[0] = make_float4(v[0], v[1], v[2], v[3]);
         o[1] = make_float4(v[4], v[5], v[6], v[7]);
       } else {
 #pragma unroll
         for (int t = 0; t < 8; t++)
-          if (i0 + t < h.n) x[i0 + t] = v[t];
+          if (8 * j + t < br.len) x[i0 + t] = v[t];
       }
     }
   }
@@ -138,7 +136,7 @@ __device__ __forceinline__ double u256_to_double(const U256& a) {
   return d;
 }
 
-constexpr int MOM_STAGES = 3;
+constexpr int MOM_STAGES = 6;
 
 template <bool VAR>
 __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
@@ -146,7 +144,7 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
     const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* stages = reinterpret_cast<InStage*>(dyn);
-  __shared__ uint64_t full[MOM_STAGES], empty[MOM_STAGES];
+  __shared__ uint64_t full[MOM_STAGES], ready[MOM_STAGES], empty[MOM_STAGES];
   __shared__ unsigned long long stage_tile[MOM_STAGES];
   __shared__ long long s_s1[CONSUMER_THREADS / 32];
   __shared__ U128 s_s2[CONSUMER_THREADS / 32];
@@ -167,30 +165,29 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
     whi |= (uint32_t)(64 - 8 * j - 4 - t) << (8 * t);
   }
   if (j == 0) wlo &= 0xffffff00u;
-  ring_init<MOM_STAGES>(full, empty);
+  ring_init3<MOM_STAGES>(full, ready, empty);
   if (w == LOADER_WARP) {
-    if ((tid & 31) == 0) {
-      const uint64_t G = gridDim.x;
-      loader_loop<MOM_STAGES>(full, empty, stage_tile, ntiles, ws.status,
-                              [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
-                              [&](int s, unsigned long long t) {
-                                issue_in_tile(&stages[s], &full[s], c, h, t, pre);
-                              });
-    }
+    const uint64_t G = gridDim.x;
+    loader_warp<MOM_STAGES>(
+        stage_tile, full, ready, empty, ntiles, ws.status,
+        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
+        [&](int sk, unsigned long long t) { issue_in_tile(&stages[sk], &full[sk], c, h, t, pre); },
+        [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
   } else {
-    for (uint64_t k = 0;; k++) {
-      const int s = (int)(k % MOM_STAGES);
-      mbar_wait(&full[s], (unsigned)((k / MOM_STAGES) & 1), ws.status);
-      const unsigned long long tile = stage_tile[s];
+    RingPos rp{0, 0u};
+    for (;;) {
+      mbar_wait(&ready[rp.s], rp.par, ws.status);
+      const unsigned long long tile = stage_tile[rp.s];
       if (tile >= ntiles) break;
-      const InStage& sg = stages[s];
-      const TileOff off = warp_tile_offsets(sg.rate, tile, h.nb, g, bad);
-      const BlockRef br = block_ref_w(sg, off, h, tile, g, j, bad);
-      const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
-      if (!VAR && kmax <= 2 && __all_sync(0xffffffffu, br.len == L)) {
+      const InStage& sg = stages[rp.s];
+      const BlockRef br = block_ref_s(sg, g, j);
+      const int kmax = sg.kmx[w];
+      const bool full_tile = sg.nvalid == TILE && sg.lastlen == L;
+      if (!VAR && kmax <= 2 && full_tile) {
         const int v = octet_sum_fast(br, kmax, j, S, wlo, whi);
         __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+        if ((tid & 31) == 0) mbar_arrive(&empty[rp.s]);
+        rp.next<MOM_STAGES>();
         s1 += v;
         if (j == 0) s1 += (long long)L * br.outlier;
         continue;
@@ -198,7 +195,8 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
       int d[8];
       octet_deltas(br, kmax, j, S, d);
       __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      if ((tid & 31) == 0) mbar_arrive(&empty[rp.s]);
+      rp.next<MOM_STAGES>();
       if (!VAR) {
         s1 += octet_sum_q(br, d, j, kmax);
       } else {

@@ -63,12 +63,18 @@ struct __align__(16) InStage {
   uint64_t plane[TILE * MAX_RATE + 2];
   uint64_t sign[TILE + 2];
   int outlier[TILE];
-  uint8_t rate[TILE];
+  uint8_t rate[TILE];  // bulk-copied; then sanitized by the loader warp
   uint32_t sbase, pbase;
+  // written by the loader warp once the copy has landed (see prepare_tile):
+  uint32_t off[TILE];              // (non-constant blocks before << 16) | rate sum before
+  uint8_t kmx[TILE / 4];           // plane groups (ceil(rate/8)) to decode, per warp of 4 blocks
+  uint32_t nvalid;                 // blocks of the tile inside the stream
+  uint32_t lastlen;                // values in block nvalid-1
 };
 static_assert(sizeof(uint64_t) * (TILE * MAX_RATE + 2) % 16 == 0, "plane[] keeps alignment");
 static_assert(sizeof(uint64_t) * (TILE + 2) % 16 == 0, "sign[] keeps alignment");
 static_assert(sizeof(InStage) % 16 == 0, "ring stages must stay 16-byte aligned (bulk copies)");
+static_assert(TILE == 64, "prepare_tile scans 64 blocks with one warp (2 per lane)");
 static_assert(offsetof(InStage, sign) % 16 == 0 && offsetof(InStage, outlier) % 16 == 0 &&
                   offsetof(InStage, rate) % 16 == 0,
               "bulk-copy destinations are 16-byte aligned");

@@ -73,20 +73,51 @@ __device__ __forceinline__ TileOff warp_tile_offsets(const uint8_t* rates, uint6
   return t;
 }
 
-// Block view for an octet, from a stage and warp-computed offsets.
-__device__ __forceinline__ BlockRef block_ref_w(const InStage& s, const TileOff& off,
-                                                const Info& h, uint64_t tile, int g, int j,
-                                                int& bad) {
+// Block view for an octet of a prepared stage (see prepare_tile).
+__device__ __forceinline__ BlockRef block_ref_s(const InStage& s, int g, int j) {
   BlockRef br;
-  const uint64_t b = tile * TILE + g;
-  br.rate = (int)sane_rate(s.rate[g], b, h.nb, bad);
+  br.rate = s.rate[g];
   br.outlier = s.outlier[g];
-  br.planes = s.plane + s.pbase + off.r_excl;
-  br.sign_byte =
-      br.rate ? reinterpret_cast<const uint8_t*>(s.sign + s.sbase + off.nc_excl)[j] : 0u;
-  const uint64_t rem = (b < h.nb) ? h.n - b * L : 0;
-  br.len = rem < (uint64_t)L ? (int)rem : L;
+  const uint32_t off = s.off[g];
+  br.planes = s.plane + s.pbase + (off & 0xffffu);
+  br.sign_byte = br.rate ? reinterpret_cast<const uint8_t*>(s.sign + s.sbase + (off >> 16))[j] : 0u;
+  const int nv = (int)s.nvalid;
+  br.len = (g < nv - 1) ? L : ((g == nv - 1) ? (int)s.lastlen : 0);
   return br;
+}
+
+// Loader warp, after tile t's copy into `s` has landed: sanitize the rates
+// (0 past the stream end; clamped to 31, which keeps every index inside the
+// stage arrays -- a rate above 31 is a corrupt stream, reported by the rate
+// pre-scan, and then no result is produced), write each block's in-tile
+// offsets, the plane groups per warp of 4 blocks, and the tile's extent.
+// All 32 lanes; lane l handles blocks 2l and 2l+1.
+__device__ __forceinline__ void prepare_tile(InStage& s, uint64_t t, const Info& h) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t first = t * TILE;
+  const uint32_t nv = (uint32_t)umin64(TILE, h.nb - first);
+  const uint32_t pair = reinterpret_cast<const uint16_t*>(s.rate)[lane];
+  uint32_t r0 = pair & 0xffu, r1 = pair >> 8;
+  r0 = (2u * lane < nv) ? min(r0, (uint32_t)MAX_RATE) : 0u;
+  r1 = (2u * lane + 1 < nv) ? min(r1, (uint32_t)MAX_RATE) : 0u;
+  reinterpret_cast<uint16_t*>(s.rate)[lane] = (uint16_t)(r0 | (r1 << 8));
+  const uint32_t v0 = (r0 ? 0x10000u : 0u) | r0, v1 = (r1 ? 0x10000u : 0u) | r1;
+  const uint32_t pv = v0 + v1;
+  uint32_t inc = pv;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  s.off[2 * lane] = inc - pv;
+  s.off[2 * lane + 1] = inc - pv + v0;
+  uint32_t km = (max(r0, r1) + 7) >> 3;
+  km = max(km, __shfl_xor_sync(0xffffffffu, km, 1));
+  if ((lane & 1) == 0) s.kmx[lane >> 1] = (uint8_t)km;
+  if (lane == 0) {
+    s.nvalid = nv;
+    s.lastlen = (uint32_t)umin64(L, h.n - (first + nv - 1) * L);
+  }
 }
 
 // ---------------------------------------------------------------- input ring
@@ -107,26 +138,75 @@ __device__ __forceinline__ void ring_init(uint64_t* full, uint64_t* empty) {
   __syncthreads();
 }
 
-// Loader (one thread): for k = 0, 1, ... hands stage k % S the tile id from
-// next_tile(k) and, for a real tile, issues its bulk copies; a tile id >=
-// ntiles ends the walk (the stage still completes, without data).
-template <int S, class NextTile, class Issue>
-__device__ __forceinline__ void loader_loop(uint64_t* full, uint64_t* empty,
-                                            unsigned long long* stage_tile, uint64_t ntiles,
-                                            int* st, NextTile&& next_tile, Issue&& issue) {
-  for (uint64_t k = 0;; k++) {
-    const int s = (int)(k % S);
-    if (k >= (uint64_t)S) mbar_wait(&empty[s], (unsigned)(((k / S) - 1) & 1), st);
-    const unsigned long long t = next_tile(k);
-    stage_tile[s] = t;
-    if (t < ntiles) {
-      issue(s, t);
-    } else {
-      mbar_arrive(&full[s]);
-      return;
+// Ring of S stages with three barriers per stage: full (bulk copy landed),
+// ready (loader warp prepared it), empty (all compute warps done with it).
+template <int S, int FULL_ARRIVALS = 1>
+__device__ __forceinline__ void ring_init3(uint64_t* full, uint64_t* ready, uint64_t* empty) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < S; k++) {
+      mbar_init(&full[k], FULL_ARRIVALS);
+      mbar_init(&ready[k], 1);
+      mbar_init(&empty[k], NCW);
     }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// Loader warp (all 32 lanes): walks tiles next_tile(0), next_tile(1), ...;
+// keeps up to S-1 tiles in flight (issue(s, t) by lane 0), and prepares each
+// landed tile (prepare(s, t), whole warp) one step ahead of the compute warps,
+// which wait on ready[s]. stage_tile[s] gets the tile id; an id >= ntiles ends
+// the walk (its stage completes without data).
+template <int S, int FULL_ARRIVALS = 1, class NextTile, class Issue, class Prepare>
+__device__ __forceinline__ void loader_warp(unsigned long long* stage_tile, uint64_t* full,
+                                            uint64_t* ready, uint64_t* empty, uint64_t ntiles,
+                                            int* st, NextTile&& next_tile, Issue&& issue,
+                                            Prepare&& prepare) {
+  const int lane = threadIdx.x & 31;
+  uint32_t issued = 0;
+  bool more = true;
+  auto issue_one = [&](uint32_t k) {
+    const int sk = (int)(k % S);
+    if (k >= (uint32_t)S) mbar_wait(&empty[sk], ((k / S) - 1) & 1, st);
+    unsigned long long t = 0;
+    if (lane == 0) {
+      t = next_tile(k);
+      stage_tile[sk] = t;
+      if (t < ntiles) {
+        issue(sk, t);
+      } else {
+        for (int a = 0; a < FULL_ARRIVALS; a++) mbar_arrive(&full[sk]);
+      }
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    return t < ntiles;
+  };
+  for (; issued < (uint32_t)S - 1 && more; issued++) more = issue_one(issued);
+  for (uint32_t k = 0;; k++) {
+    const int sk = (int)(k % S);
+    mbar_wait(&full[sk], (k / S) & 1, st);
+    const unsigned long long t = stage_tile[sk];
+    if (t < ntiles) prepare(sk, t);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ready[sk]);
+    if (t >= ntiles) return;
+    if (more) more = issue_one(issued++);
   }
 }
+
+// Compute-warp side of the ring: stage index and barrier parity.
+struct RingPos {
+  int s;
+  uint32_t par;
+  template <int S>
+  __device__ __forceinline__ void next() {
+    if (++s == S) {
+      s = 0;
+      par ^= 1u;
+    }
+  }
+};
 
 // ---------------------------------------------------------------- produced tiles
 // A produced tile goes to its own slot of the workspace: [sign words | plane

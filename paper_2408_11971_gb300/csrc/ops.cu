@@ -237,14 +237,14 @@ __device__ __forceinline__ void octet_mag_sign(const int d[8], uint32_t mag[8], 
 // A loader warp bulk-copies input tiles (located by the rate pre-scan); compute
 // warps decode them to q (workflow 3), requantize, and Lorenzo + BF re-encode
 // each tile into its workspace slot (see produce_tile).
-constexpr int MUL_STAGES = 3;
+constexpr int MUL_STAGES = 5;
 
 __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
     const uint8_t* __restrict__ c, uint64_t c_bytes, double s, uint8_t* __restrict__ out,
     uint64_t cap, uint32_t e_bits, const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ins = reinterpret_cast<InStage*>(dyn);
-  __shared__ uint64_t full[MUL_STAGES], empty[MUL_STAGES];
+  __shared__ uint64_t full[MUL_STAGES], ready[MUL_STAGES], empty[MUL_STAGES];
   __shared__ unsigned long long stage_tile[MUL_STAGES];
   __shared__ uint8_t srate[2][TILE];
   __shared__ long long s_rho;
@@ -267,34 +267,34 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
     s_rho = rho;
     if (blockIdx.x == 0) write_template(h, 0, ws);
   }
-  ring_init<MUL_STAGES>(full, empty);
+  ring_init3<MUL_STAGES>(full, ready, empty);
   const uint64_t ntiles = (s_ok && prescan_ok(h, pre, ws.max_tiles)) ? ntiles_of(h.nb) : 0;
   const MulPlan mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
   const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   bool ovf = false;
   if (w == LOADER_WARP) {
-    if ((tid & 31) == 0) {
-      const uint64_t G = gridDim.x;
-      loader_loop<MUL_STAGES>(
-          full, empty, stage_tile, ntiles, ws.status,
-          [&](uint64_t k) { return (unsigned long long)(blockIdx.x + k * G); },
-          [&](int st, unsigned long long t) { issue_in_tile(&ins[st], &full[st], c, h, t, pre); });
-    }
+    const uint64_t G = gridDim.x;
+    loader_warp<MUL_STAGES>(
+        stage_tile, full, ready, empty, ntiles, ws.status,
+        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
+        [&](int sk, unsigned long long t) { issue_in_tile(&ins[sk], &full[sk], c, h, t, pre); },
+        [&](int sk, unsigned long long t) { prepare_tile(ins[sk], t, h); });
   } else {
+    RingPos rp{0, 0u};
     for (uint64_t k = 0;; k++) {
-      const int st = (int)(k % MUL_STAGES);
-      mbar_wait(&full[st], (unsigned)((k / MUL_STAGES) & 1), ws.status);
+      const int st = rp.s;
+      mbar_wait(&ready[st], rp.par, ws.status);
       const unsigned long long tile = stage_tile[st];
       if (tile >= ntiles) break;
       const InStage& sg = ins[st];
-      const TileOff off = warp_tile_offsets(sg.rate, tile, h.nb, g, bad);
-      const BlockRef br = block_ref_w(sg, off, h, tile, g, j, bad);
-      const int kmax = __reduce_max_sync(0xffffffffu, (br.rate + 7) >> 3);
+      const BlockRef br = block_ref_s(sg, g, j);
+      const int kmax = sg.kmx[w];
       int d[8], q[8];
       octet_deltas(br, kmax, j, S, d);
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[st]);
+      rp.next<MUL_STAGES>();
       octet_values(br, d, j, q);
       if (br.len < L) {  // positions past the stream end hold no value
 #pragma unroll
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ina = reinterpret_cast<InStage*>(dyn);
   InStage* inb = ina + ADD_STAGES;
-  __shared__ uint64_t fulla[ADD_STAGES], fullb[ADD_STAGES], empty[ADD_STAGES];
+  __shared__ uint64_t full[ADD_STAGES], ready[ADD_STAGES], empty[ADD_STAGES];
   __shared__ unsigned long long stage_tile[ADD_STAGES];
   __shared__ uint8_t srate[2][TILE];
   __shared__ int s_ok;
@@ -389,52 +389,42 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
       write_template(ha, ok ? ha.qbound + hb.qbound : 0, ws);
       if (ok) atomicMax(&ws.totals[2], (unsigned long long)(ha.qbound + hb.qbound));
     }
-    for (int k = 0; k < ADD_STAGES; k++) mbar_init(&fullb[k], 1);
   }
-  ring_init<ADD_STAGES>(fulla, empty);
+  ring_init3<ADD_STAGES, 2>(full, ready, empty);  // full: one arrival per stream
   const OctetSel S = octet_sel(j);
   const uint64_t ntiles =
       (s_ok && prescan_ok(ha, pre_a, ws.max_tiles) && prescan_ok(hb, pre_b, ws.max_tiles))
           ? ntiles_of(ha.nb)
           : 0;
   if (w == LOADER_WARP) {
-    if ((tid & 31) == 0) {
-      const uint64_t G = gridDim.x;
-      for (uint64_t k = 0;; k++) {
-        const int st = (int)(k % ADD_STAGES);
-        if (k >= (uint64_t)ADD_STAGES)
-          mbar_wait(&empty[st], (unsigned)(((k / ADD_STAGES) - 1) & 1), ws.status);
-        const unsigned long long t = blockIdx.x + k * G;
-        stage_tile[st] = t;
-        if (t < ntiles) {
-          issue_in_tile(&ina[st], &fulla[st], a, ha, t, pre_a);
-          issue_in_tile(&inb[st], &fullb[st], b, hb, t, pre_b);
-        } else {
-          mbar_arrive(&fulla[st]);
-          mbar_arrive(&fullb[st]);
-          break;
-        }
-      }
-    }
+    const uint64_t G = gridDim.x;
+    loader_warp<ADD_STAGES, 2>(
+        stage_tile, full, ready, empty, ntiles, ws.status,
+        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
+        [&](int sk, unsigned long long t) {
+          issue_in_tile(&ina[sk], &full[sk], a, ha, t, pre_a);
+          issue_in_tile(&inb[sk], &full[sk], b, hb, t, pre_b);
+        },
+        [&](int sk, unsigned long long t) {
+          prepare_tile(ina[sk], t, ha);
+          prepare_tile(inb[sk], t, hb);
+        });
   } else {
+    RingPos rp{0, 0u};
     for (uint64_t k = 0;; k++) {
-      const int st = (int)(k % ADD_STAGES);
-      const unsigned par = (unsigned)((k / ADD_STAGES) & 1);
-      mbar_wait(&fulla[st], par, ws.status);
-      mbar_wait(&fullb[st], par, ws.status);
+      const int st = rp.s;
+      mbar_wait(&ready[st], rp.par, ws.status);
       const unsigned long long tile = stage_tile[st];
       if (tile >= ntiles) break;
-      const TileOff offa = warp_tile_offsets(ina[st].rate, tile, ha.nb, g, bad);
-      const TileOff offb = warp_tile_offsets(inb[st].rate, tile, hb.nb, g, bad);
-      const BlockRef ra = block_ref_w(ina[st], offa, ha, tile, g, j, bad);
-      const BlockRef rb = block_ref_w(inb[st], offb, hb, tile, g, j, bad);
-      const int ka = __reduce_max_sync(0xffffffffu, (ra.rate + 7) >> 3);
-      const int kb = __reduce_max_sync(0xffffffffu, (rb.rate + 7) >> 3);
+      const BlockRef ra = block_ref_s(ina[st], g, j);
+      const BlockRef rb = block_ref_s(inb[st], g, j);
+      const int ka = ina[st].kmx[w], kb = inb[st].kmx[w];
       int da[8], db[8], nd[8];
       octet_deltas(ra, ka, j, S, da);
       octet_deltas(rb, kb, j, S, db);
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[st]);
+      rp.next<ADD_STAGES>();
 #pragma unroll
       for (int t = 0; t < 8; t++) nd[t] = da[t] + db[t];
       uint32_t mag[8], sb;
