@@ -163,6 +163,24 @@ int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result
 int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
               hoszp_stream_t stream);
 
+/* Mean of a stream without allocating: for callers that may not allocate
+ * device memory when they call -- e.g. code whose device memory is owned by a
+ * host framework's pool that forbids driver allocations while it runs, or a
+ * latency-critical loop that cannot afford the device synchronization a
+ * cudaMalloc implies -- and that therefore cannot create a hoszp_ctx. The
+ * paper has no counterpart; the result is the same as hoszp_mean's.
+ * Scratch: one file-scope device array of about 1.2 MB per device, kept for as
+ * long as the library is loaded; it bounds the stream to at most 2^28 values
+ * (larger streams: status HOSZP_ERR_CAPACITY). The first call on a device looks
+ * up the array's device address with that device current; make that first
+ * call before capturing any stream. Every call shares the array, so calls
+ * that overlap on the GPU (e.g. on two streams at once) race and must not.
+ * d_c: stream (16-byte aligned), d_result: device double, d_status: device int
+ * that receives the call's device-side status (HOSZP_OK or an error code).
+ * Host-checkable argument errors are returned immediately. */
+int hoszp_mean_noalloc(const void* d_c, size_t c_bytes, double* d_result, int* d_status,
+                       hoszp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
