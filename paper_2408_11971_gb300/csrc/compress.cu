@@ -161,7 +161,9 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
     loader_warp<CMP_STAGES>(
         stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t) { issue_x(&ins[sk], &full[sk], x, n, t); },
+        [&](int sk, unsigned long long t, uint32_t) {
+          if ((tid & 31) == 0) issue_x(&ins[sk], &full[sk], x, n, t);
+        },
         [&](int, unsigned long long) {});
   } else {
     RingPos rp{0, 0u};

@@ -31,10 +31,17 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
   ring_init3<DEC_STAGES>(full, ready, empty);
   if (w == LOADER_WARP) {
     const uint64_t G = gridDim.x;
+    __shared__ ulonglong2 s_win[32][2];
+    PreWindow pw;
+    pw.init(s_win);
     loader_warp<DEC_STAGES>(
         stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t) { issue_in_tile(&stages[sk], &full[sk], c, h, t, pre); },
+        [&](int sk, unsigned long long t, uint32_t k) {
+          unsigned long long pv[4];
+          pw.get(pre, k, blockIdx.x, G, ntiles, pv);
+          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, pv);
+        },
         [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
   } else {
     RingPos rp{0, 0u};
@@ -168,10 +175,17 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
   ring_init3<MOM_STAGES>(full, ready, empty);
   if (w == LOADER_WARP) {
     const uint64_t G = gridDim.x;
+    __shared__ ulonglong2 s_win[32][2];
+    PreWindow pw;
+    pw.init(s_win);
     loader_warp<MOM_STAGES>(
         stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t) { issue_in_tile(&stages[sk], &full[sk], c, h, t, pre); },
+        [&](int sk, unsigned long long t, uint32_t k) {
+          unsigned long long pv[4];
+          pw.get(pre, k, blockIdx.x, G, ntiles, pv);
+          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, pv);
+        },
         [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
   } else {
     RingPos rp{0, 0u};

@@ -80,13 +80,13 @@ static_assert(offsetof(InStage, sign) % 16 == 0 && offsetof(InStage, outlier) % 
               "bulk-copy destinations are 16-byte aligned");
 
 // Issued by one thread: bulk-copy tile `t` of stream `c` into `s`, completing
-// on `bar`. pre[2t], pre[2t+1] = exclusive prefix (non-constant blocks, rate
-// sum) of tile t (from the rate pre-scan); pre[2t+2], pre[2t+3] those of t+1.
+// on `bar`. pv = {nc, r} exclusive prefixes (non-constant blocks, rate sum) of
+// tile t and of tile t+1, from the rate pre-scan.
 __device__ __forceinline__ void issue_in_tile(InStage* s, uint64_t* bar, const uint8_t* c,
                                               const Info& h, uint64_t t,
-                                              const unsigned long long* pre) {
-  const unsigned long long NC0 = pre[2 * t], R0 = pre[2 * t + 1];
-  const unsigned long long NC1 = pre[2 * t + 2], R1 = pre[2 * t + 3];
+                                              const unsigned long long pv[4]) {
+  const unsigned long long NC0 = pv[0], R0 = pv[1];
+  const unsigned long long NC1 = pv[2], R1 = pv[3];
   const uint64_t rate_end = align16(h.nb), out_end = align16(4 * h.nb);
   const unsigned rb = (unsigned)umin64(TILE, rate_end - TILE * t);
   const unsigned ob = (unsigned)umin64(4 * TILE, out_end - 4 * TILE * t);
@@ -105,5 +105,39 @@ __device__ __forceinline__ void issue_in_tile(InStage* s, uint64_t* bar, const u
   if (sbytes) bulk_g2s(s->sign, c + sa16, sbytes, bar);
   if (pbytes) bulk_g2s(s->plane, c + pa16, pbytes, bar);
 }
+
+// Loader-warp window over the pre-scan's prefixes: the prefixes of the
+// loader's tiles k0 .. k0+31 (tile bid + k * G) are fetched in one warp-wide
+// load per 32 tiles into a shared-memory window, so issuing a tile needs no
+// dependent global load. All 32 lanes call get() with the same, increasing k;
+// `out` is meaningful in lane 0.
+struct PreWindow {
+  ulonglong2 (*win)[2];  // shared: [32][2] = {nc, r} of tile k and of tile k + 1
+  uint64_t k0;
+  __device__ __forceinline__ void init(ulonglong2 (*w)[2]) {
+    win = w;
+    k0 = ~0ull;
+  }
+  __device__ __forceinline__ void get(const unsigned long long* pre, uint64_t k, uint64_t bid,
+                                      uint64_t G, uint64_t ntiles, unsigned long long out[4]) {
+    const int lane = threadIdx.x & 31;
+    if (k0 == ~0ull || k >= k0 + 32) {
+      k0 = k;
+      const uint64_t t = bid + (k0 + lane) * G;
+      __syncwarp();
+      if (t < ntiles) {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(pre + 2 * t);
+        win[lane][0] = __ldg(p);
+        win[lane][1] = __ldg(p + 1);
+      }
+      __syncwarp();
+    }
+    const ulonglong2 a = win[k - k0][0], b = win[k - k0][1];
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = b.x;
+    out[3] = b.y;
+  }
+};
 
 }  // namespace hz

@@ -154,7 +154,8 @@ __device__ __forceinline__ void ring_init3(uint64_t* full, uint64_t* ready, uint
 }
 
 // Loader warp (all 32 lanes): walks tiles next_tile(0), next_tile(1), ...;
-// keeps up to S-1 tiles in flight (issue(s, t) by lane 0), and prepares each
+// keeps up to S-1 tiles in flight (issue(s, t, k): whole warp, lane 0 issues
+// the copies), and prepares each
 // landed tile (prepare(s, t), whole warp) one step ahead of the compute warps,
 // which wait on ready[s]. stage_tile[s] gets the tile id; an id >= ntiles ends
 // the walk (its stage completes without data).
@@ -169,17 +170,13 @@ __device__ __forceinline__ void loader_warp(unsigned long long* stage_tile, uint
   auto issue_one = [&](uint32_t k) {
     const int sk = (int)(k % S);
     if (k >= (uint32_t)S) mbar_wait(&empty[sk], ((k / S) - 1) & 1, st);
-    unsigned long long t = 0;
-    if (lane == 0) {
-      t = next_tile(k);
-      stage_tile[sk] = t;
-      if (t < ntiles) {
-        issue(sk, t);
-      } else {
-        for (int a = 0; a < FULL_ARRIVALS; a++) mbar_arrive(&full[sk]);
-      }
+    const unsigned long long t = next_tile(k);  // same value in every lane
+    if (lane == 0) stage_tile[sk] = t;
+    if (t < ntiles) {
+      issue(sk, t, k);  // whole warp; lane 0 issues the copies
+    } else if (lane == 0) {
+      for (int a = 0; a < FULL_ARRIVALS; a++) mbar_arrive(&full[sk]);
     }
-    t = __shfl_sync(0xffffffffu, t, 0);
     return t < ntiles;
   };
   for (; issued < (uint32_t)S - 1 && more; issued++) more = issue_one(issued);

@@ -136,32 +136,47 @@ __global__ void __launch_bounds__(512) k_meta(const uint8_t* c, uint64_t c_bytes
   const bool ok = s_ok != 0;
   const long long rho = s_rho;
   if (ok) {
+    // The stream after the header as 16-byte chunks (every section starts on
+    // a 16-byte boundary except the plane section, which starts on 8): each
+    // thread loads 4 chunks before it transforms and stores them, so enough
+    // bytes are in flight to keep HBM busy. In place, only the outlier and
+    // (negation) sign chunks are touched.
     const bool inplace = (out == c);
+    const uint64_t b_lo = inplace ? h.o_out : HOSZP_HEADER_BYTES;
+    const uint64_t b_hi = inplace ? (NEG ? align16(h.o_plane) : h.o_sign) : h.size;
+    const uint64_t nch = (b_hi - b_lo) / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(c + b_lo);
+    uint4* dst = reinterpret_cast<uint4*>(out + b_lo);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t tid0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // outliers: 4 per thread step (section is 16-byte aligned)
-    const int* src_o = reinterpret_cast<const int*>(c + h.o_out);
-    int* dst_o = reinterpret_cast<int*>(out + h.o_out);
-    for (uint64_t i = tid0; i < h.nb; i += stride) {
-      const int o = src_o[i];
-      dst_o[i] = NEG ? -o : (int)(o + rho);
-    }
-    if (NEG) {
-      const uint64_t* src_s = reinterpret_cast<const uint64_t*>(c + h.o_sign);
-      uint64_t* dst_s = reinterpret_cast<uint64_t*>(out + h.o_sign);
-      for (uint64_t i = tid0; i < h.nnc; i += stride) dst_s[i] = ~src_s[i];
-    }
-    if (!inplace) {
-      // rates (+ padding) and, for scalar addition, the sign words; then the planes
-      const uint64_t* src = reinterpret_cast<const uint64_t*>(c);
-      uint64_t* dst = reinterpret_cast<uint64_t*>(out);
-      const uint64_t r0 = HOSZP_HEADER_BYTES / 8, r1 = h.o_out / 8;
-      for (uint64_t i = r0 + tid0; i < r1; i += stride) dst[i] = src[i];
-      const uint64_t pad0 = (h.o_out + 4 * h.nb + 7) / 8, pad1 = h.o_sign / 8;
-      if ((h.nb & 1) && tid0 == 0) dst_o[h.nb] = src_o[h.nb];  // padding word half
-      for (uint64_t i = pad0 + tid0; i < pad1; i += stride) dst[i] = src[i];
-      const uint64_t w0 = (NEG ? h.o_plane : h.o_sign) / 8, w1 = h.size / 8;
-      for (uint64_t i = w0 + tid0; i < w1; i += stride) dst[i] = src[i];
+    const int r32 = (int)rho;  // |outlier| + |rho| <= HOSZP_QLIM: 32-bit arithmetic is exact
+    constexpr int U = 4;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch;
+         i0 += U * stride) {
+      uint4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (i0 + u * stride < nch) v[u] = __ldcs(src + i0 + u * stride);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint64_t i = i0 + u * stride;
+        if (i >= nch) break;
+        const uint64_t b = b_lo + 16 * i;
+        if (b >= h.o_out && b < h.o_sign) {  // 4 outliers (padding past nb unchanged)
+          const uint64_t k0 = (b - h.o_out) >> 2;
+          uint32_t* w = reinterpret_cast<uint32_t*>(&v[u]);
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (k0 + k < h.nb) w[k] = NEG ? (uint32_t)(-(int)w[k]) : (uint32_t)((int)w[k] + r32);
+        } else if (NEG && b >= h.o_sign && b < h.o_plane) {  // sign words (the 2nd may be a plane)
+          v[u].x = ~v[u].x;
+          v[u].y = ~v[u].y;
+          if (b + 8 < h.o_plane) {
+            v[u].z = ~v[u].z;
+            v[u].w = ~v[u].w;
+          }
+        }
+        __stcs(dst + i, v[u]);
+      }
     }
   }
   // the header is written by the CTA that finishes last: in place, every other
@@ -275,10 +290,17 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
   bool ovf = false;
   if (w == LOADER_WARP) {
     const uint64_t G = gridDim.x;
+    __shared__ ulonglong2 s_win[32][2];
+    PreWindow pw;
+    pw.init(s_win);
     loader_warp<MUL_STAGES>(
         stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t) { issue_in_tile(&ins[sk], &full[sk], c, h, t, pre); },
+        [&](int sk, unsigned long long t, uint32_t k) {
+          unsigned long long pv[4];
+          pw.get(pre, k, blockIdx.x, G, ntiles, pv);
+          if ((tid & 31) == 0) issue_in_tile(&ins[sk], &full[sk], c, h, t, pv);
+        },
         [&](int sk, unsigned long long t) { prepare_tile(ins[sk], t, h); });
   } else {
     RingPos rp{0, 0u};
@@ -398,12 +420,21 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
           : 0;
   if (w == LOADER_WARP) {
     const uint64_t G = gridDim.x;
+    __shared__ ulonglong2 s_wina[32][2], s_winb[32][2];
+    PreWindow pwa, pwb;
+    pwa.init(s_wina);
+    pwb.init(s_winb);
     loader_warp<ADD_STAGES, 2>(
         stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t) {
-          issue_in_tile(&ina[sk], &full[sk], a, ha, t, pre_a);
-          issue_in_tile(&inb[sk], &full[sk], b, hb, t, pre_b);
+        [&](int sk, unsigned long long t, uint32_t k) {
+          unsigned long long pa[4], pb[4];
+          pwa.get(pre_a, k, blockIdx.x, G, ntiles, pa);
+          pwb.get(pre_b, k, blockIdx.x, G, ntiles, pb);
+          if ((tid & 31) == 0) {
+            issue_in_tile(&ina[sk], &full[sk], a, ha, t, pa);
+            issue_in_tile(&inb[sk], &full[sk], b, hb, t, pb);
+          }
         },
         [&](int sk, unsigned long long t) {
           prepare_tile(ina[sk], t, ha);

@@ -23,7 +23,12 @@ __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64
   if (fits) {
     uint64_t* sdst = reinterpret_cast<uint64_t*>(out + off_sign(nb));
     uint64_t* pdst = reinterpret_cast<uint64_t*>(out + off_plane(nb, nnc));
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // one warp per tile; each lane moves up to 8 words per step with all its
+    // loads issued before its stores
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles;
+         t += nwarps) {
       const unsigned long long a = ws.agg[t];
       const uint64_t nc = a >> 32, r = a & 0xffffffffull;
       const uint64_t so = slot_offset(rule, t, ws.pre[0], ws.pre[1], e_bits);
@@ -33,8 +38,20 @@ __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64
         continue;
       }
       const uint64_t* src = ws.staging + so;
-      for (uint64_t i = threadIdx.x; i < nc; i += blockDim.x) sdst[NC + i] = src[i];
-      for (uint64_t i = threadIdx.x; i < r; i += blockDim.x) pdst[RR + i] = src[nc + i];
+      const uint64_t words = nc + r;
+      constexpr int U = 8;
+      for (uint64_t i0 = lane; i0 < words; i0 += 32 * U) {
+        uint64_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+          if (i0 + 32 * u < words) v[u] = __ldcs(src + i0 + 32 * u);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const uint64_t i = i0 + 32 * u;
+          if (i < nc) sdst[NC + i] = v[u];
+          else if (i < words) pdst[RR + i - nc] = v[u];
+        }
+      }
     }
     if (blockIdx.x == 0) {
       // zero the end padding and the padding after the rate and outlier sections
