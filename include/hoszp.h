@@ -153,6 +153,13 @@ int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
 int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
               void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
 
+/* Element-wise subtraction A - B, Sec. V-C "Element-wise Subtraction": as
+ * hoszp_add with B's signed deltas and outliers negated (O' = O_A - O_B,
+ * delta' = delta_A - delta_B). Same arguments, checks and errors as
+ * hoszp_add; the qbound of the result is qbound_A + qbound_B. */
+int hoszp_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
+              void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
+
 /* Mean, Sec. V-B: S1 = sum of q (exact integer), mean = (S1 / n) * 2 eps_q in
  * FP64, written to the device double *d_result. n == 0 -> HOSZP_ERR_ARG. */
 int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,

@@ -73,6 +73,7 @@ def _load():
     lib.orc_add_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
     lib.orc_mul_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
     lib.orc_add.argtypes = [P, SZ, P, SZ, P, SZ, P]
+    lib.orc_sub.argtypes = [P, SZ, P, SZ, P, SZ, P]
     lib.orc_sums.argtypes = [P, SZ, P, P, P, P, P, P]
     lib.orc_header.argtypes = [P, SZ, P, P, P, P, P, P]
     lib.orc_eps_q.argtypes = [ctypes.c_double, P]
@@ -212,6 +213,18 @@ def add(a, b) -> np.ndarray:
     nbytes = np.zeros(1, np.uint64)
     _check(_load().orc_add(_ptr(a), a.size, _ptr(b), b.size, _ptr(out), cap, _ptr(nbytes)),
            "add")
+    return out[: int(nbytes[0])].copy()
+
+
+def sub(a, b) -> np.ndarray:
+    """Element-wise subtraction A - B (Sec. V-C): q' = q_A - q_B, re-encoded."""
+    a = _stream(a)
+    b = _stream(b)
+    cap = bound(header(a)["n"])
+    out = np.zeros(cap, np.uint8)
+    nbytes = np.zeros(1, np.uint64)
+    _check(_load().orc_sub(_ptr(a), a.size, _ptr(b), b.size, _ptr(out), cap, _ptr(nbytes)),
+           "sub")
     return out[: int(nbytes[0])].copy()
 
 

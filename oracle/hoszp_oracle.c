@@ -525,6 +525,33 @@ int orc_add(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_bytes, 
   return rc;
 }
 
+/* Element-wise subtraction (Sec. V-C, "Element-wise Subtraction"): as the
+ * addition with B's quantized values negated, q' = q_A - q_B, re-encoded. The
+ * result bound is qbound_A + qbound_B. */
+int orc_sub(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_bytes, uint8_t* out,
+            size_t cap, uint64_t* out_bytes) {
+  orc_hdr ha, hb;
+  int rc = read_header(a, a_bytes, &ha);
+  if (rc) return rc;
+  rc = read_header(b, b_bytes, &hb);
+  if (rc) return rc;
+  if (ha.n != hb.n || float_to_bits(ha.eps_q) != float_to_bits(hb.eps_q)) return ORC_ERR_MISMATCH;
+  if ((int64_t)ha.qbound + (int64_t)hb.qbound > ORC_QLIM) return ORC_ERR_OVERFLOW;
+  uint64_t n = ha.n;
+  int64_t* qa = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  int64_t* qb = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  if (!qa || !qb) { free(qa); free(qb); return ORC_ERR_ARG; }
+  decode_q(a, a_bytes, &ha, qa);
+  decode_q(b, b_bytes, &hb, qb);
+  for (uint64_t i = 0; i < n; i++) qa[i] -= qb[i];
+  orc_hdr h = ha;
+  h.qbound = ha.qbound + hb.qbound;
+  rc = encode_q(qa, &h, out, cap, out_bytes);
+  free(qa);
+  free(qb);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* reductions (Sec. V-B): exact integer sums; the caller finishes them  */
 /* ------------------------------------------------------------------ */

@@ -27,6 +27,7 @@ from ._binding import (  # noqa: F401
     add_scalar,
     mul_scalar,
     add,
+    sub,
     mean,
     var,
     header,
@@ -37,6 +38,6 @@ from ._binding import (  # noqa: F401
 
 __all__ = [
     "HoszpError", "Context", "STATUS", "lib_path", "load_library", "default_context",
-    "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add",
+    "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add", "sub",
     "mean", "var", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

@@ -56,6 +56,7 @@ def load_library():
             "hoszp_add_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_mul_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_add": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
+            "hoszp_sub": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
         }
@@ -261,9 +262,7 @@ def mul_scalar(c, s: float, out=None, out_bytes=None, stream=None, ctx=None, syn
                   out_bytes, False, stream, ctx, sync, check)
 
 
-def add(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
-        check: bool = True):
-    """Element-wise addition of two streams (Sec. V-C)."""
+def _bivariate(fn, what, a, b, out, out_bytes, stream, ctx, sync, check):
     torch = _torch()
     a = _stream_tensor(a)
     b = _stream_tensor(b)
@@ -272,11 +271,24 @@ def add(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True
         out = torch.empty(compress_bound(header(a)["n"]), dtype=torch.uint8, device=a.device)
     if out_bytes is None:
         out_bytes = torch.zeros(1, dtype=torch.int64, device=a.device)
-    rc = load_library().hoszp_add(ctx.handle, _dev_ptr(a), a.numel(), _dev_ptr(b), b.numel(),
-                                  _dev_ptr(out), out.numel(), _dev_ptr(out_bytes),
-                                  _stream_ptr(stream))
-    _check(rc, "add")
-    return _finish(ctx, out, out_bytes, sync, check, "add")
+    rc = fn(ctx.handle, _dev_ptr(a), a.numel(), _dev_ptr(b), b.numel(), _dev_ptr(out),
+            out.numel(), _dev_ptr(out_bytes), _stream_ptr(stream))
+    _check(rc, what)
+    return _finish(ctx, out, out_bytes, sync, check, what)
+
+
+def add(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
+        check: bool = True):
+    """Element-wise addition of two streams (Sec. V-C)."""
+    return _bivariate(load_library().hoszp_add, "add", a, b, out, out_bytes, stream, ctx, sync,
+                      check)
+
+
+def sub(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
+        check: bool = True):
+    """Element-wise subtraction A - B of two streams (Sec. V-C)."""
+    return _bivariate(load_library().hoszp_sub, "sub", a, b, out, out_bytes, stream, ctx, sync,
+                      check)
 
 
 def _moment(fn, what, c, out, stream, ctx, sync, check):

@@ -321,8 +321,9 @@ int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
   return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_MUL, e_bits, ctx->ws));
 }
 
-int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
-              void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+static int add_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b,
+                   size_t b_bytes, void* d_out, size_t cap, uint64_t* d_out_bytes,
+                   hoszp_stream_t stream, bool subtract) {
   if (!ctx || !d_a || !d_b || !d_out || !d_out_bytes || a_bytes < HOSZP_HEADER_BYTES ||
       b_bytes < HOSZP_HEADER_BYTES)
     return HOSZP_ERR_ARG;
@@ -338,9 +339,19 @@ int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, 
   int rc = ensure_ws(ctx, ta > tb ? ta : tb, (a_bytes + b_bytes) / 8 + 64);
   if (rc) return rc;
   Launch lc = lc_of(ctx, stream);
-  rc = cuda_rc(launch_add(lc, a, a_bytes, b, b_bytes, o, cap, ctx->ws));
+  rc = cuda_rc(launch_add(lc, a, a_bytes, b, b_bytes, o, cap, subtract, ctx->ws));
   if (rc) return rc;
   return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_ADD, 0, ctx->ws));
+}
+
+int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
+              void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+  return add_sub(ctx, d_a, a_bytes, d_b, b_bytes, d_out, cap, d_out_bytes, stream, false);
+}
+
+int hoszp_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
+              void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+  return add_sub(ctx, d_a, a_bytes, d_b, b_bytes, d_out, cap, d_out_bytes, stream, true);
 }
 
 static int moments(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,

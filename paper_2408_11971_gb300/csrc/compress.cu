@@ -100,6 +100,7 @@ cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double re
 // output stage; a tile's place in the stream (look-back over the tiles before
 // it) is resolved one tile later, so the look-back latency overlaps compute.
 constexpr int CMP_STAGES = 4;
+constexpr int CMP_THREADS = (NCW + 1) * 32;  // compute warps + one issuer warp
 
 struct InX {
   float v[TILE_VALUES];
@@ -115,16 +116,16 @@ __device__ __forceinline__ void issue_x(InX* s, uint64_t* bar, const float* x, u
   if (bytes) bulk_g2s(s->v, x + first, bytes, bar);
 }
 
-__global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
+__global__ void __launch_bounds__(CMP_THREADS, 2) k_compress(
     const float* __restrict__ x, uint64_t n, const uint32_t dims0, const uint32_t dims1,
     const uint32_t dims2, const uint32_t ndims, float eps_q_abs, double eps_abs, int rel,
     uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InX* ins = reinterpret_cast<InX*>(dyn);
-  __shared__ uint64_t full[CMP_STAGES], ready[CMP_STAGES], empty[CMP_STAGES];
+  __shared__ uint64_t full[CMP_STAGES], empty[CMP_STAGES];
   __shared__ unsigned long long stage_tile[CMP_STAGES];
   __shared__ uint8_t srate[2][TILE];
-  __shared__ unsigned int s_qmax[PRODUCER_THREADS / 32];
+  __shared__ unsigned int s_qmax[CMP_THREADS / 32];
   const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
 
   const float e = rel ? *ws.eps_q : eps_q_abs;
@@ -152,24 +153,23 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
     H->qbound = 0;
     H->block = HOSZP_BLOCK;
   }
-  ring_init3<CMP_STAGES>(full, ready, empty);
+  ring_init<CMP_STAGES>(full, empty);
   const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   int bad = 0;
   if (w == LOADER_WARP) {
     const uint64_t G = gridDim.x;
-    loader_warp<CMP_STAGES>(
-        stage_tile, full, ready, empty, ntiles, ws.status,
+    issuer_warp<CMP_STAGES>(
+        stage_tile, full, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t) {
+        [&](int sk, unsigned long long t) {
           if ((tid & 31) == 0) issue_x(&ins[sk], &full[sk], x, n, t);
-        },
-        [&](int, unsigned long long) {});
+        });
   } else {
     RingPos rp{0, 0u};
     for (uint64_t k = 0;; k++) {
       const int s = rp.s;
-      mbar_wait(&ready[s], rp.par, ws.status);
+      mbar_wait(&full[s], rp.par, ws.status);
       const unsigned long long tile = stage_tile[s];
       if (tile >= ntiles) break;
       const InX& in = ins[s];
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_compress(
   if ((tid & 31) == 0) s_qmax[tid >> 5] = qmax;
   __syncthreads();
   if (tid == 0) {
-    for (int k = 1; k < PRODUCER_THREADS / 32; k++) qmax = max(qmax, s_qmax[k]);
+    for (int k = 1; k < CMP_THREADS / 32; k++) qmax = max(qmax, s_qmax[k]);
     atomicMax(&ws.totals[2], (unsigned long long)qmax);
   }
   if (bad) set_status(ws.status, bad);
@@ -239,8 +239,8 @@ cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const 
     cudaFuncSetAttribute(k_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_compress<<<persistent_grid(k_compress, PRODUCER_THREADS, lc.grid, smem), PRODUCER_THREADS,
-               smem, lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs,
+  k_compress<<<persistent_grid(k_compress, CMP_THREADS, lc.grid, smem), CMP_THREADS, smem,
+               lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs,
                                   rel ? 1 : 0, out, cap, ws);
   return cudaGetLastError();
 }

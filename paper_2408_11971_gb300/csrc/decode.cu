@@ -9,13 +9,15 @@
 namespace hz {
 
 // ---------------------------------------------------------------- decompression
-constexpr int DEC_STAGES = 6;
+constexpr int DEC_STAGES = 8;
+constexpr uint32_t DEC_RING = 8192;  // plane-ring words (64 KB)
 
 __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
     const uint8_t* __restrict__ c, uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect,
     const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* stages = reinterpret_cast<InStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + DEC_STAGES);
   __shared__ uint64_t full[DEC_STAGES], ready[DEC_STAGES], empty[DEC_STAGES];
   __shared__ unsigned long long stage_tile[DEC_STAGES];
   const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
@@ -29,18 +31,25 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
   const bool small = h.qbound < (1u << 22);
   const OctetSel S = octet_sel(j);
   ring_init3<DEC_STAGES>(full, ready, empty);
-  if (w == LOADER_WARP) {
+  if (w >= LOADER_WARP) {
     const uint64_t G = gridDim.x;
     __shared__ ulonglong2 s_win[32][2];
     PreWindow pw;
     pw.init(s_win);
-    loader_warp<DEC_STAGES>(
-        stage_tile, full, ready, empty, ntiles, ws.status,
+    __shared__ uint32_t s_beg[DEC_STAGES];
+    PlaneRing<DEC_STAGES, DEC_RING> pr;
+    pr.init(ring, s_beg);
+    loader_warps<DEC_STAGES>(
+        w - LOADER_WARP, stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k) {
+        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
+            auto&& release_one) {
           unsigned long long pv[4];
           pw.get(pre, k, blockIdx.x, G, ntiles, pv);
-          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, pv);
+          const TileSpan sp = tile_span(h, t, pv);
+          const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
+          const uint32_t at = pr.commit(k, p0, sp.plane_words());
+          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, sp, ring, at);
         },
         [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
   } else {
@@ -50,7 +59,7 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
       const unsigned long long tile = stage_tile[rp.s];
       if (tile >= ntiles) break;
       const InStage& sg = stages[rp.s];
-      const BlockRef br = block_ref_s(sg, g, j);
+      const BlockRef br = block_ref_s(sg, ring, g, j);
       const int kmax = sg.kmx[w];
       int d[8], q[8];
       octet_deltas(br, kmax, j, S, d);
@@ -80,7 +89,7 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
                               uint64_t n, Ws ws) {
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
-  const size_t smem = DEC_STAGES * sizeof(InStage);
+  const size_t smem = DEC_STAGES * sizeof(InStage) + DEC_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -143,7 +152,8 @@ __device__ __forceinline__ double u256_to_double(const U256& a) {
   return d;
 }
 
-constexpr int MOM_STAGES = 6;
+constexpr int MOM_STAGES = 8;
+constexpr uint32_t MOM_RING = 8192;  // plane-ring words (64 KB)
 
 template <bool VAR>
 __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
@@ -151,6 +161,7 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
     const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* stages = reinterpret_cast<InStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MOM_STAGES);
   __shared__ uint64_t full[MOM_STAGES], ready[MOM_STAGES], empty[MOM_STAGES];
   __shared__ unsigned long long stage_tile[MOM_STAGES];
   __shared__ long long s_s1[CONSUMER_THREADS / 32];
@@ -173,18 +184,25 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
   }
   if (j == 0) wlo &= 0xffffff00u;
   ring_init3<MOM_STAGES>(full, ready, empty);
-  if (w == LOADER_WARP) {
+  if (w >= LOADER_WARP) {
     const uint64_t G = gridDim.x;
     __shared__ ulonglong2 s_win[32][2];
     PreWindow pw;
     pw.init(s_win);
-    loader_warp<MOM_STAGES>(
-        stage_tile, full, ready, empty, ntiles, ws.status,
+    __shared__ uint32_t s_beg[MOM_STAGES];
+    PlaneRing<MOM_STAGES, MOM_RING> pr;
+    pr.init(ring, s_beg);
+    loader_warps<MOM_STAGES>(
+        w - LOADER_WARP, stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k) {
+        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
+            auto&& release_one) {
           unsigned long long pv[4];
           pw.get(pre, k, blockIdx.x, G, ntiles, pv);
-          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, pv);
+          const TileSpan sp = tile_span(h, t, pv);
+          const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
+          const uint32_t at = pr.commit(k, p0, sp.plane_words());
+          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, sp, ring, at);
         },
         [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
   } else {
@@ -194,7 +212,7 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
       const unsigned long long tile = stage_tile[rp.s];
       if (tile >= ntiles) break;
       const InStage& sg = stages[rp.s];
-      const BlockRef br = block_ref_s(sg, g, j);
+      const BlockRef br = block_ref_s(sg, ring, g, j);
       const int kmax = sg.kmx[w];
       const bool full_tile = sg.nvalid == TILE && sg.lastlen == L;
       if (!VAR && kmax <= 2 && full_tile) {
@@ -300,7 +318,7 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
 template <bool VAR>
 static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                                     double* result, Ws ws) {
-  const size_t smem = MOM_STAGES * sizeof(InStage);
+  const size_t smem = MOM_STAGES * sizeof(InStage) + MOM_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_moments<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,20 +1,22 @@
 // hz_ws.cuh — warp-specialized tile pipeline shared by the codec kernels.
 //
 // A CTA has NCW = 16 compute warps (512 threads: 8 lanes per block of a
-// 64-block tile) and one loader warp that bulk-copies the next tiles into a
-// ring of shared-memory stages. The two roles meet only on mbarriers:
-// full[s] (copy landed) and empty[s] (all compute warps done with stage s).
-// Compute warps never wait for each other, except once per produced tile (all
-// 64 output rates must be known before any block's words can be placed).
+// 64-block tile) and loader warps: an issuer that bulk-copies the next tiles
+// into a ring of shared-memory stages (plane words into a plane ring), and a
+// preparer that readies each landed tile for the compute warps. The roles meet
+// only on mbarriers: full[s] (copy landed), ready[s] (tile prepared) and
+// empty[s] (all compute warps done with stage s). Compute warps never wait for
+// each other, except once per produced tile (all 64 output rates must be known
+// before any block's words can be placed).
 #pragma once
 #include "hz_decode.cuh"
 
 namespace hz {
 
 constexpr int NCW = 16;                       // compute warps
-constexpr int LOADER_WARP = NCW;              // warp index of the loader
-constexpr int CONSUMER_THREADS = (NCW + 1) * 32;
-constexpr int PRODUCER_THREADS = (NCW + 1) * 32;
+constexpr int LOADER_WARP = NCW;              // warp index of the first loader warp
+constexpr int CONSUMER_THREADS = (NCW + 2) * 32;  // + issuer and preparer warps
+constexpr int PRODUCER_THREADS = (NCW + 2) * 32;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -74,12 +76,13 @@ __device__ __forceinline__ TileOff warp_tile_offsets(const uint8_t* rates, uint6
 }
 
 // Block view for an octet of a prepared stage (see prepare_tile).
-__device__ __forceinline__ BlockRef block_ref_s(const InStage& s, int g, int j) {
+__device__ __forceinline__ BlockRef block_ref_s(const InStage& s, const uint64_t* ring, int g,
+                                                int j) {
   BlockRef br;
   br.rate = s.rate[g];
   br.outlier = s.outlier[g];
   const uint32_t off = s.off[g];
-  br.planes = s.plane + s.pbase + (off & 0xffffu);
+  br.planes = ring + s.pring + s.pbase + (off & 0xffffu);
   br.sign_byte = br.rate ? reinterpret_cast<const uint8_t*>(s.sign + s.sbase + (off >> 16))[j] : 0u;
   const int nv = (int)s.nvalid;
   br.len = (g < nv - 1) ? L : ((g == nv - 1) ? (int)s.lastlen : 0);
@@ -139,56 +142,95 @@ __device__ __forceinline__ void ring_init(uint64_t* full, uint64_t* empty) {
 }
 
 // Ring of S stages with three barriers per stage: full (bulk copy landed),
-// ready (loader warp prepared it), empty (all compute warps done with it).
-template <int S, int FULL_ARRIVALS = 1>
+// ready (loader warp prepared it), empty (all EMPTY_ARRIVALS compute warps done
+// with it).
+template <int S, int FULL_ARRIVALS = 1, int EMPTY_ARRIVALS = NCW>
 __device__ __forceinline__ void ring_init3(uint64_t* full, uint64_t* ready, uint64_t* empty) {
   if (threadIdx.x == 0) {
     for (int k = 0; k < S; k++) {
       mbar_init(&full[k], FULL_ARRIVALS);
       mbar_init(&ready[k], 1);
-      mbar_init(&empty[k], NCW);
+      mbar_init(&empty[k], EMPTY_ARRIVALS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 }
 
-// Loader warp (all 32 lanes): walks tiles next_tile(0), next_tile(1), ...;
-// keeps up to S-1 tiles in flight (issue(s, t, k): whole warp, lane 0 issues
-// the copies), and prepares each
-// landed tile (prepare(s, t), whole warp) one step ahead of the compute warps,
-// which wait on ready[s]. stage_tile[s] gets the tile id; an id >= ntiles ends
-// the walk (its stage completes without data).
-template <int S, int FULL_ARRIVALS = 1, class NextTile, class Issue, class Prepare>
-__device__ __forceinline__ void loader_warp(unsigned long long* stage_tile, uint64_t* full,
-                                            uint64_t* ready, uint64_t* empty, uint64_t ntiles,
-                                            int* st, NextTile&& next_tile, Issue&& issue,
-                                            Prepare&& prepare) {
+// Loader warps of a tile pipeline: two warps, so that copying and preparing
+// never wait for each other.
+//  - issuer (role 0): walks tiles next_tile(0), next_tile(1), ...; before
+//    stage use k it waits for the release of use k - S (all compute warps
+//    arrived on empty[k % S]; releases are consumed in order, k_rel counts
+//    them), then calls issue(s, t, k, k_rel, release_one) with the whole warp
+//    (lane 0 issues the copies; a plane ring may wait for further releases
+//    through release_one). stage_tile[s] gets the tile id; an id >= ntiles ends
+//    the walk (its stage completes without data). With GROUPS compute groups
+//    taking stage uses in turn, GROUPS such end stages are made.
+//  - preparer (role 1): for each stage use in order, waits for the copy to
+//    land, prepares the tile (prepare(s, t), whole warp) and arrives on
+//    ready[s], which the compute warps wait for.
+template <int S, int FULL_ARRIVALS = 1, int GROUPS = 1, class NextTile, class Issue,
+          class Prepare>
+__device__ __forceinline__ void loader_warps(int role, unsigned long long* stage_tile,
+                                             uint64_t* full, uint64_t* ready, uint64_t* empty,
+                                             uint64_t ntiles, int* st, NextTile&& next_tile,
+                                             Issue&& issue, Prepare&& prepare) {
   const int lane = threadIdx.x & 31;
-  uint32_t issued = 0;
-  bool more = true;
-  auto issue_one = [&](uint32_t k) {
-    const int sk = (int)(k % S);
-    if (k >= (uint32_t)S) mbar_wait(&empty[sk], ((k / S) - 1) & 1, st);
-    const unsigned long long t = next_tile(k);  // same value in every lane
-    if (lane == 0) stage_tile[sk] = t;
-    if (t < ntiles) {
-      issue(sk, t, k);  // whole warp; lane 0 issues the copies
-    } else if (lane == 0) {
-      for (int a = 0; a < FULL_ARRIVALS; a++) mbar_arrive(&full[sk]);
+  if (role == 0) {
+    uint32_t k_rel = 0;  // stage uses released
+    auto release_one = [&]() {
+      mbar_wait(&empty[k_rel % S], (k_rel / S) & 1, st);
+      k_rel++;
+    };
+    int ends = 0;
+    for (uint32_t k = 0; ends < GROUPS; k++) {
+      const int sk = (int)(k % S);
+      while (k_rel + S <= k) release_one();  // the stage's previous use is done
+      const unsigned long long t = next_tile(k);  // same value in every lane
+      if (lane == 0) stage_tile[sk] = t;
+      __syncwarp();
+      if (t < ntiles) {
+        issue(sk, t, k, k_rel, release_one);
+      } else {
+        if (lane == 0)
+          for (int a = 0; a < FULL_ARRIVALS; a++) mbar_arrive(&full[sk]);
+        ends++;
+      }
     }
-    return t < ntiles;
-  };
-  for (; issued < (uint32_t)S - 1 && more; issued++) more = issue_one(issued);
+  } else {
+    int ends = 0;
+    for (uint32_t k = 0; ends < GROUPS; k++) {
+      const int sk = (int)(k % S);
+      mbar_wait(&full[sk], (k / S) & 1, st);
+      const unsigned long long t = stage_tile[sk];
+      if (t < ntiles) prepare(sk, t);
+      else ends++;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ready[sk]);
+    }
+  }
+}
+
+// Single loader warp for pipelines whose tiles need no preparation: the
+// compute warps wait on full[] directly.
+template <int S, class NextTile, class Issue>
+__device__ __forceinline__ void issuer_warp(unsigned long long* stage_tile, uint64_t* full,
+                                            uint64_t* empty, uint64_t ntiles, int* st,
+                                            NextTile&& next_tile, Issue&& issue) {
+  const int lane = threadIdx.x & 31;
   for (uint32_t k = 0;; k++) {
     const int sk = (int)(k % S);
-    mbar_wait(&full[sk], (k / S) & 1, st);
-    const unsigned long long t = stage_tile[sk];
-    if (t < ntiles) prepare(sk, t);
+    if (k >= (uint32_t)S) mbar_wait(&empty[sk], ((k / S) - 1) & 1, st);
+    const unsigned long long t = next_tile(k);
+    if (lane == 0) stage_tile[sk] = t;
     __syncwarp();
-    if (lane == 0) mbar_arrive(&ready[sk]);
-    if (t >= ntiles) return;
-    if (more) more = issue_one(issued++);
+    if (t < ntiles) {
+      issue(sk, t);
+    } else {
+      if (lane == 0) mbar_arrive(&full[sk]);
+      return;
+    }
   }
 }
 

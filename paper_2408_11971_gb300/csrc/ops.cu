@@ -252,13 +252,15 @@ __device__ __forceinline__ void octet_mag_sign(const int d[8], uint32_t mag[8], 
 // A loader warp bulk-copies input tiles (located by the rate pre-scan); compute
 // warps decode them to q (workflow 3), requantize, and Lorenzo + BF re-encode
 // each tile into its workspace slot (see produce_tile).
-constexpr int MUL_STAGES = 5;
+constexpr int MUL_STAGES = 8;
+constexpr uint32_t MUL_RING = 8192;  // plane-ring words (64 KB)
 
 __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
     const uint8_t* __restrict__ c, uint64_t c_bytes, double s, uint8_t* __restrict__ out,
     uint64_t cap, uint32_t e_bits, const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ins = reinterpret_cast<InStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(ins + MUL_STAGES);
   __shared__ uint64_t full[MUL_STAGES], ready[MUL_STAGES], empty[MUL_STAGES];
   __shared__ unsigned long long stage_tile[MUL_STAGES];
   __shared__ uint8_t srate[2][TILE];
@@ -288,18 +290,25 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
   const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   bool ovf = false;
-  if (w == LOADER_WARP) {
+  if (w >= LOADER_WARP) {
     const uint64_t G = gridDim.x;
     __shared__ ulonglong2 s_win[32][2];
     PreWindow pw;
     pw.init(s_win);
-    loader_warp<MUL_STAGES>(
-        stage_tile, full, ready, empty, ntiles, ws.status,
+    __shared__ uint32_t s_beg[MUL_STAGES];
+    PlaneRing<MUL_STAGES, MUL_RING> pr;
+    pr.init(ring, s_beg);
+    loader_warps<MUL_STAGES>(
+        w - LOADER_WARP, stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k) {
+        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
+            auto&& release_one) {
           unsigned long long pv[4];
           pw.get(pre, k, blockIdx.x, G, ntiles, pv);
-          if ((tid & 31) == 0) issue_in_tile(&ins[sk], &full[sk], c, h, t, pv);
+          const TileSpan sp = tile_span(h, t, pv);
+          const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
+          const uint32_t at = pr.commit(k, p0, sp.plane_words());
+          if ((tid & 31) == 0) issue_in_tile(&ins[sk], &full[sk], c, h, t, sp, ring, at);
         },
         [&](int sk, unsigned long long t) { prepare_tile(ins[sk], t, h); });
   } else {
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
       const unsigned long long tile = stage_tile[st];
       if (tile >= ntiles) break;
       const InStage& sg = ins[st];
-      const BlockRef br = block_ref_s(sg, g, j);
+      const BlockRef br = block_ref_s(sg, ring, g, j);
       const int kmax = sg.kmx[w];
       int d[8], q[8];
       octet_deltas(br, kmax, j, S, d);
@@ -361,7 +370,7 @@ cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_byt
                               uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
-  const size_t smem = MUL_STAGES * sizeof(InStage);
+  const size_t smem = MUL_STAGES * sizeof(InStage) + MUL_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mul_scalar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -374,12 +383,37 @@ cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_byt
 }
 
 // ---------------------------------------------------------------- element-wise addition
-// Workflow 2: both streams' tiles arrive through bulk-copy rings; the deltas
-// are decoded (no inverse Lorenzo), added, and BF re-encoded into the tile's
-// workspace slot.
-constexpr int ADD_STAGES = 3;
+// Workflow 2 on the bit-planes themselves. A block's deltas are stored
+// bit-sliced (plane p holds bit p of |delta_i| at bit i; the sign word holds
+// the signs), so the 64 additions delta_A,i + delta_B,i of a block are done
+// plane by plane with 32 positions per 32-bit word:
+//   two's complement of each input:  x = (m XOR s) + s   (carry chain, carry-in s)
+//   sum:                             z = x + y           (full adder per plane)
+//   back to sign and magnitude:      s' = top plane of z; m' = (z XOR s') + s'
+// over W = max(rate_A, rate_B) + 2 planes (|delta_A + delta_B| < 2^(max+1)).
+// The result's rate is the highest nonzero plane of m'. Element-wise
+// subtraction is the same with the second input's signs inverted (negation
+// flips every sign bit; a zero magnitude stays zero whatever its sign).
+//
+// CTA: two groups of 4 compute warps taking the tiles in turn (thread = one
+// 32-position half of one of the tile's 64 blocks) and a loader warp that
+// bulk-copies both inputs' tiles.
+constexpr int ADD_STAGES = 5;
+constexpr uint32_t ADD_RING = 4096;  // plane-ring words per input (32 KB)
+constexpr int ADD_GROUPS = 2;
+constexpr int ADD_GW = 4;  // warps per group
+constexpr int ADD_NCW = ADD_GROUPS * ADD_GW;
+constexpr int ADD_THREADS = (ADD_NCW + 2) * 32;  // + issuer and preparer warps
+constexpr int ADD_ZW = 2 * 32 + 1;  // zbuf words per block: 32 planes x 2 halves, +1 against conflicts
 
-__global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
+__device__ __forceinline__ void add_bar(int grp) {
+  if (grp == 0) asm volatile("bar.sync 1, %0;" ::"n"(ADD_GW * 32) : "memory");
+  else asm volatile("bar.sync 2, %0;" ::"n"(ADD_GW * 32) : "memory");
+}
+static_assert(ADD_GROUPS == 2, "add_bar names one barrier per group");
+
+template <bool SUB>
+__global__ void __launch_bounds__(ADD_THREADS, 2) k_add(
     const uint8_t* __restrict__ a, uint64_t a_bytes, const uint8_t* __restrict__ b,
     uint64_t b_bytes, uint8_t* __restrict__ out, uint64_t cap,
     const unsigned long long* __restrict__ pre_a, const unsigned long long* __restrict__ pre_b,
@@ -387,11 +421,14 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ina = reinterpret_cast<InStage*>(dyn);
   InStage* inb = ina + ADD_STAGES;
+  uint64_t* ringa = reinterpret_cast<uint64_t*>(inb + ADD_STAGES);
+  uint64_t* ringb = ringa + ADD_RING;
+  uint32_t* zbuf = reinterpret_cast<uint32_t*>(ringb + ADD_RING);  // [groups][64][ADD_ZW]
   __shared__ uint64_t full[ADD_STAGES], ready[ADD_STAGES], empty[ADD_STAGES];
   __shared__ unsigned long long stage_tile[ADD_STAGES];
-  __shared__ uint8_t srate[2][TILE];
+  __shared__ uint8_t srate[ADD_GROUPS][2][TILE];
   __shared__ int s_ok;
-  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
+  const int tid = threadIdx.x, w = tid >> 5;
   const Info ha = parse_header(a, a_bytes);
   const Info hb = parse_header(b, b_bytes);
   int bad = 0;
@@ -412,28 +449,39 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
       if (ok) atomicMax(&ws.totals[2], (unsigned long long)(ha.qbound + hb.qbound));
     }
   }
-  ring_init3<ADD_STAGES, 2>(full, ready, empty);  // full: one arrival per stream
-  const OctetSel S = octet_sel(j);
+  // full: one arrival per stream; empty: the 4 warps of the group that took the stage
+  ring_init3<ADD_STAGES, 2, ADD_GW>(full, ready, empty);
   const uint64_t ntiles =
       (s_ok && prescan_ok(ha, pre_a, ws.max_tiles) && prescan_ok(hb, pre_b, ws.max_tiles))
           ? ntiles_of(ha.nb)
           : 0;
-  if (w == LOADER_WARP) {
+  if (w >= ADD_NCW) {
     const uint64_t G = gridDim.x;
     __shared__ ulonglong2 s_wina[32][2], s_winb[32][2];
     PreWindow pwa, pwb;
     pwa.init(s_wina);
     pwb.init(s_winb);
-    loader_warp<ADD_STAGES, 2>(
-        stage_tile, full, ready, empty, ntiles, ws.status,
+    __shared__ uint32_t s_bega[ADD_STAGES], s_begb[ADD_STAGES];
+    PlaneRing<ADD_STAGES, ADD_RING> pra, prb;
+    pra.init(ringa, s_bega);
+    prb.init(ringb, s_begb);
+    loader_warps<ADD_STAGES, 2, ADD_GROUPS>(
+        w - ADD_NCW, stage_tile, full, ready, empty, ntiles, ws.status,
         [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k) {
+        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
+            auto&& release_one) {
           unsigned long long pa[4], pb[4];
           pwa.get(pre_a, k, blockIdx.x, G, ntiles, pa);
           pwb.get(pre_b, k, blockIdx.x, G, ntiles, pb);
+          const TileSpan spa = tile_span(ha, t, pa), spb = tile_span(hb, t, pb);
+          // room in both rings (releases only add room, so A's stays valid)
+          const uint32_t p0a = pra.reserve(k, spa.plane_words(), k_rel, release_one);
+          const uint32_t p0b = prb.reserve(k, spb.plane_words(), k_rel, release_one);
+          const uint32_t ata = pra.commit(k, p0a, spa.plane_words());
+          const uint32_t atb = prb.commit(k, p0b, spb.plane_words());
           if ((tid & 31) == 0) {
-            issue_in_tile(&ina[sk], &full[sk], a, ha, t, pa);
-            issue_in_tile(&inb[sk], &full[sk], b, hb, t, pb);
+            issue_in_tile(&ina[sk], &full[sk], a, ha, t, spa, ringa, ata);
+            issue_in_tile(&inb[sk], &full[sk], b, hb, t, spb, ringb, atb);
           }
         },
         [&](int sk, unsigned long long t) {
@@ -441,49 +489,116 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_add(
           prepare_tile(inb[sk], t, hb);
         });
   } else {
-    RingPos rp{0, 0u};
+    const int grp = tid / (ADD_GW * 32), lt = tid % (ADD_GW * 32);
+    const int g = lt >> 1, hf = lt & 1;  // block of the tile, half (positions 32hf..32hf+31)
+    uint32_t* zb = zbuf + (grp * TILE + g) * ADD_ZW + hf;  // plane p at zb[2p]
     for (uint64_t k = 0;; k++) {
-      const int st = rp.s;
-      mbar_wait(&ready[st], rp.par, ws.status);
+      const uint64_t u = k * ADD_GROUPS + grp;  // stage use taken by this group
+      const int st = (int)(u % ADD_STAGES);
+      mbar_wait(&ready[st], (uint32_t)((u / ADD_STAGES) & 1), ws.status);
       const unsigned long long tile = stage_tile[st];
       if (tile >= ntiles) break;
-      const BlockRef ra = block_ref_s(ina[st], g, j);
-      const BlockRef rb = block_ref_s(inb[st], g, j);
-      const int ka = ina[st].kmx[w], kb = inb[st].kmx[w];
-      int da[8], db[8], nd[8];
-      octet_deltas(ra, ka, j, S, da);
-      octet_deltas(rb, kb, j, S, db);
+      const InStage& sa = ina[st];
+      const InStage& sb = inb[st];
+      const int ra = sa.rate[g], rb = sb.rate[g];
+      const uint32_t offa = sa.off[g], offb = sb.off[g];
+      const uint32_t* pa =
+          reinterpret_cast<const uint32_t*>(ringa + sa.pring + sa.pbase + (offa & 0xffffu)) + hf;
+      const uint32_t* pb =
+          reinterpret_cast<const uint32_t*>(ringb + sb.pring + sb.pbase + (offb & 0xffffu)) + hf;
+      const uint32_t siga =
+          ra ? reinterpret_cast<const uint32_t*>(sa.sign + sa.sbase + (offa >> 16))[hf] : 0u;
+      uint32_t sigb =
+          rb ? reinterpret_cast<const uint32_t*>(sb.sign + sb.sbase + (offb >> 16))[hf] : 0u;
+      if (SUB) sigb = ~sigb;
+      const int oa = sa.outlier[g], ob = sb.outlier[g];
+      const int m = max(ra, rb);
+      // pass 1: z = (mA ^ sA) + sA + (mB ^ sB) + sB, planes 0 .. m+1
+      uint32_t ca = siga, cb = sigb, cz = 0u, z = 0u;
+      if (m > 0) {
+#pragma unroll 4
+        for (int p = 0; p <= m + 1; p++) {
+          const uint32_t xa = (p < ra ? pa[2 * p] : 0u) ^ siga;
+          const uint32_t xb = (p < rb ? pb[2 * p] : 0u) ^ sigb;
+          const uint32_t x = xa ^ ca, y = xb ^ cb;
+          ca &= xa;
+          cb &= xb;
+          z = x ^ y ^ cz;
+          cz = (x & y) | (cz & (x ^ y));
+          if (p <= m) zb[2 * p] = z;  // plane m+1 (the sign) stays in z
+        }
+      }
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[st]);
-      rp.next<ADD_STAGES>();
-#pragma unroll
-      for (int t = 0; t < 8; t++) nd[t] = da[t] + db[t];
-      uint32_t mag[8], sb;
-      octet_mag_sign(nd, mag, sb);
-      const int rate = octet_rate(mag);
-      produce_tile(srate, k, tile, ha.nb, mag, sb, rate, ra.outlier + rb.outlier,
-                   tile * TILE + g < ha.nb, g, j, out, ws.staging,
-                   slot_offset(SLOT_ADD, tile, pre_a, pre_b, 0), ws.staging_words, ws.agg, S,
-                   bad);
+      // pass 2: sign = top plane; magnitude = (z ^ s) + s, planes 0 .. m
+      const uint32_t sgn = z;  // plane m+1 (0 when both blocks are constant)
+      uint32_t cu = sgn, nzp = 0u;
+      if (m > 0) {
+#pragma unroll 4
+        for (int p = 0; p <= m; p++) {
+          const uint32_t t = zb[2 * p] ^ sgn;
+          const uint32_t mg = t ^ cu;
+          cu &= t;
+          zb[2 * p] = mg;
+          nzp |= (mg != 0u ? 1u : 0u) << p;
+        }
+      }
+      nzp |= __shfl_xor_sync(0xffffffffu, nzp, 1);
+      int rate = 32 - __clz(nzp);
+      if (rate > MAX_RATE) {  // only a header whose qbound understates its values gets here
+        bad = HOSZP_ERR_OVERFLOW;
+        rate = MAX_RATE;
+      }
+      const uint64_t bi = tile * TILE + g;
+      const bool valid = bi < ha.nb;
+      uint8_t* rr = srate[grp][k & 1];
+      if (hf == 0) {
+        rr[g] = valid ? (uint8_t)rate : 0;
+        if (valid) {
+          out[HOSZP_HEADER_BYTES + bi] = (uint8_t)rate;
+          reinterpret_cast<int*>(out + off_outlier(ha.nb))[bi] = SUB ? oa - ob : oa + ob;
+        }
+      }
+      add_bar(grp);
+      const TileOff off = warp_tile_offsets(rr, 0, TILE, g, bad);
+      const uint64_t so = slot_offset(SLOT_ADD, tile, pre_a, pre_b, 0);
+      if (so + off.agg_nc + off.agg_r > ws.staging_words) {
+        bad = HOSZP_ERR_CAPACITY;
+        continue;
+      }
+      uint32_t* slot = reinterpret_cast<uint32_t*>(ws.staging + so);
+      if (valid && rate > 0) {
+        slot[2 * off.nc_excl + hf] = sgn;
+        uint32_t* dst = slot + 2 * (off.agg_nc + off.r_excl) + hf;
+#pragma unroll 4
+        for (int p = 0; p < rate; p++) dst[2 * p] = zb[2 * p];
+      }
+      if (lt == 0) ws.agg[tile] = ((unsigned long long)off.agg_nc << 32) | off.agg_r;
     }
   }
   if (bad) set_status(ws.status, bad);
 }
 
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
-                       uint64_t b_bytes, uint8_t* out, uint64_t cap, Ws ws) {
+                       uint64_t b_bytes, uint8_t* out, uint64_t cap, bool subtract, Ws ws) {
   cudaError_t e = launch_scan(lc, a, a_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
   e = launch_scan(lc, b, b_bytes, ws.pre[1], ws);
   if (e != cudaSuccess) return e;
-  const size_t smem = 2 * ADD_STAGES * sizeof(InStage);
+  const size_t smem = 2 * ADD_STAGES * sizeof(InStage) + 2 * ADD_RING * sizeof(uint64_t) +
+                      ADD_GROUPS * TILE * ADD_ZW * sizeof(uint32_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_add<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_add<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_add<<<persistent_grid(k_add, PRODUCER_THREADS, lc.grid, smem), PRODUCER_THREADS, smem,
-          lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
+  if (subtract)
+    k_add<true><<<persistent_grid(k_add<true>, ADD_THREADS, lc.grid, smem), ADD_THREADS, smem,
+                  lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
+  else
+    k_add<false><<<persistent_grid(k_add<false>, ADD_THREADS, lc.grid, smem), ADD_THREADS, smem,
+                   lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
   return cudaGetLastError();
 }
 

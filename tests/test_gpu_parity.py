@@ -60,6 +60,10 @@ def test_codec_and_ops_small(hz, name, eb, mode):
     ocy = O.compress(y, dims=(y.size,), eb=e)
     assert np.array_equal(host(cy), ocy)
     assert np.array_equal(host(hz.add(c, cy)), O.add(oc, ocy))
+    assert np.array_equal(host(hz.sub(c, cy)), O.sub(oc, ocy))
+    # negated input: sign bits set at zero magnitudes (position 0, tail, zeros)
+    assert np.array_equal(host(hz.add(hz.negate(c), cy)), O.add(O.negate(oc), ocy))
+    assert np.array_equal(host(hz.sub(cy, hz.negate(c))), O.sub(ocy, O.negate(oc)))
     if x.size > 0:
         assert close(hz.mean(c), O.mean(oc))
         assert close(hz.var(c), O.var(oc))
@@ -93,6 +97,23 @@ def test_inplace_negate_and_add_scalar(hz, config1):
     assert np.array_equal(host(w), O.add_scalar(O.negate(oc), -1.25))
 
 
+def test_add_sub_widest_rates(hz):
+    # deltas near 2^31: alternating +-2^22 bins scaled by 120 (q' ~ 5e8), then
+    # summed with itself (qbound 1.007e9 <= HOSZP_QLIM): rates up to 31
+    n = 64 * 37 + 11
+    x = np.where(np.arange(n) % 2 == 0, 4194304.0, -4194304.0).astype(np.float32)
+    x[200:400] = 7.0  # a few constant blocks in between
+    c, oc = hz.compress(dev(x), eb=0.5), O.compress(x, eb=0.5)
+    assert np.array_equal(host(c), oc)
+    m, om = hz.mul_scalar(c, 120.0), O.mul_scalar(oc, 120.0)
+    assert np.array_equal(host(m), om)
+    z, oz = hz.add(m, m), O.add(om, om)
+    assert np.array_equal(host(z), oz)
+    assert int(O.header(oz)["qbound"]) > (1 << 29)
+    assert np.array_equal(host(hz.sub(m, hz.negate(m))), oz)
+    assert np.array_equal(host(hz.sub(m, m)), O.sub(om, om))
+
+
 def test_theorem1_add_negate_is_zero(hz, config1):
     _, c, _ = config1
     z = hz.add(c, hz.negate(c))
@@ -113,6 +134,7 @@ def test_grf_3d(hz, shape, rel):
     cy, ocy = hz.compress(dev(y), eb=e), O.compress(y, eb=e)
     assert np.array_equal(host(cy), ocy)
     assert np.array_equal(host(hz.add(c, cy)), O.add(oc, ocy))
+    assert np.array_equal(host(hz.sub(c, cy)), O.sub(oc, ocy))
     assert np.array_equal(host(hz.decompress(c)), O.decompress(oc))
     assert np.array_equal(host(hz.mul_scalar(c, -1.5)), O.mul_scalar(oc, -1.5))
     assert close(hz.mean(c), O.mean(oc)) and close(hz.var(c), O.var(oc))

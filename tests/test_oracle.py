@@ -309,6 +309,20 @@ def test_add_fields(pair):
     assert np.array_equal(qa, O.decode_q(ca)[:200])
 
 
+def test_sub_fields(pair):
+    ca, cb = pair
+    z = O.sub(ca, cb)
+    qa, qb = values(parse(ca)), values(parse(cb))  # independent parser
+    assert np.array_equal(values(parse(z)), qa - qb)
+    assert parse(z)["qbound"] == parse(ca)["qbound"] + parse(cb)["qbound"]
+    # A - B is A + (-B) byte for byte (both re-encode q_A - q_B canonically)
+    assert np.array_equal(z, O.add(ca, O.negate(cb)))
+    # anti-commutative at the bin level, and A - A is the all-constant zero stream
+    assert np.array_equal(values(parse(O.sub(cb, ca))), qb - qa)
+    zero = parse(O.sub(ca, ca))
+    assert zero["nnc"] == 0 and zero["R"] == 0 and not zero["outlier"].any()
+
+
 def test_negate_metadata_equals_reencode_up_to_zero_signs(pair):
     ca, _ = pair
     ng = parse(O.negate(ca))
