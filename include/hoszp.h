@@ -188,6 +188,54 @@ int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
 int hoszp_mean_noalloc(const void* d_c, size_t c_bytes, double* d_result, int* d_status,
                        hoszp_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched execution over many resident streams (one snapshot's fields).
+ *
+ * A plan fixes a set of resident compressed streams (the paper's operators
+ * applied field by field, Sec. V) and lays their 64-block tiles end to end in
+ * one global tile space. Each batched operator is one persistent launch over
+ * that space, with every CTA walking the per-field table as its contiguous tile
+ * range crosses field boundaries. The paper has no batched form; the results
+ * are exactly those of the single-stream operators applied to each field.
+ *
+ * hoszp_batch_create: d_streams[f] (host array of device pointers, 16-byte
+ * aligned) and stream_bytes[f] describe nfields >= 1 streams, each with n >= 1.
+ * Synchronous: parses every header (FORMAT on a bad one, ARG on n == 0) and
+ * runs each stream's rate pre-scan once. The plan owns a small device table
+ * and the prefixes; it does not own the streams, which must stay resident and
+ * keep their rates (only the batched negate / add_scalar below may modify them
+ * in place). The plan keeps a pointer to ctx, which must outlive it.
+ * Batched operators allocate nothing and never synchronize, so a sequence of
+ * them can be captured in a CUDA graph. Device errors go to the plan's own
+ * status word (hoszp_batch_get_status). Calls on one plan must not overlap. */
+typedef struct hoszp_batch hoszp_batch;
+int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_streams,
+                       const size_t* stream_bytes, hoszp_batch** out);
+void hoszp_batch_destroy(hoszp_batch* b);
+int hoszp_batch_info(const hoszp_batch* b, uint32_t* nfields, uint64_t* total_tiles);
+/* Synchronizes the plan's device, returns its status word and clears it. */
+int hoszp_batch_get_status(hoszp_batch* b, int* status);
+
+/* Per-field mean / population variance (Sec. V-B) into d_results[f] (device
+ * doubles, nfields of them); each equals hoszp_mean / hoszp_var of field f. */
+int hoszp_batch_mean(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
+int hoszp_batch_var(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
+
+/* In place on every field: negation (Sec. V-A), and scalar addition with the
+ * same s for all fields, each field quantizing s with its own eps (Eq. 3).
+ * A field whose rho_s or bound would leave the integer range is left
+ * unchanged and the plan's status gets RANGE or OVERFLOW. */
+int hoszp_batch_negate(hoszp_batch* b, hoszp_stream_t stream);
+int hoszp_batch_add_scalar(hoszp_batch* b, double s, hoszp_stream_t stream);
+
+/* Autotuner: times the batched mean and variance under each candidate launch
+ * shape (pipeline depth 8 or 4 stages x 1 or 2 CTAs per SM) on the plan's own
+ * data, writing into d_results, and keeps the fastest for later calls.
+ * Synchronizes the stream. hoszp_batch_config reports the pick (op 0: mean,
+ * op 1: variance). */
+int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
+int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@ the compiled library and a CUDA device, and raises otherwise.
 from ._binding import (  # noqa: F401
     HoszpError,
     Context,
+    Batch,
     STATUS,
     lib_path,
     load_library,
@@ -37,7 +38,7 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
-    "HoszpError", "Context", "STATUS", "lib_path", "load_library", "default_context",
+    "HoszpError", "Context", "Batch", "STATUS", "lib_path", "load_library", "default_context",
     "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add", "sub",
     "mean", "var", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

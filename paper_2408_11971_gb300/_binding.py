@@ -59,6 +59,16 @@ def load_library():
             "hoszp_sub": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
+            "hoszp_batch_create": (I, [P, ctypes.c_uint32, P, P, ctypes.POINTER(P)]),
+            "hoszp_batch_destroy": (None, [P]),
+            "hoszp_batch_info": (I, [P, P, P]),
+            "hoszp_batch_get_status": (I, [P, ctypes.POINTER(I)]),
+            "hoszp_batch_mean": (I, [P, P, P]),
+            "hoszp_batch_var": (I, [P, P, P]),
+            "hoszp_batch_negate": (I, [P, P]),
+            "hoszp_batch_add_scalar": (I, [P, D, P]),
+            "hoszp_batch_tune": (I, [P, P, P]),
+            "hoszp_batch_config": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -355,3 +365,94 @@ def fop_moments(x, variance: bool, out=None, stream=None, ctx=None):
     _check(_fop_lib().hoszp_fop_moments(ctx.handle, _dev_ptr(x), x.numel(), 1 if variance else 0,
                                         _dev_ptr(out), _stream_ptr(stream)), "fop_moments")
     return out
+
+
+class Batch:
+    """A batch plan over resident streams (one snapshot's fields): one launch
+    per operator over all of them. Keeps references to the stream tensors,
+    which the plan reads (and, for negate / add_scalar, modifies) in place."""
+
+    def __init__(self, streams, ctx=None):
+        torch = _torch()
+        self._streams = [_stream_tensor(c) for c in streams]
+        if not self._streams:
+            raise ValueError("empty batch")
+        self.ctx = _ctx(ctx, self._streams[0])
+        self._lib = load_library()
+        nf = len(self._streams)
+        ptrs = (ctypes.c_void_p * nf)(*[c.data_ptr() for c in self._streams])
+        sizes = (ctypes.c_size_t * nf)(*[c.numel() for c in self._streams])
+        h = ctypes.c_void_p()
+        torch.cuda.synchronize(self._streams[0].device)
+        _check(self._lib.hoszp_batch_create(self.ctx.handle, nf, ptrs, sizes, ctypes.byref(h)),
+               "batch_create")
+        self.handle = h
+        self.nfields = nf
+        self.device = self._streams[0].device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.hoszp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self) -> int:
+        st = ctypes.c_int(0)
+        _check(self._lib.hoszp_batch_get_status(self.handle, ctypes.byref(st)),
+               "batch_get_status")
+        return st.value
+
+    def check(self, what: str = "batch"):
+        st = self.status()
+        if st != 0:
+            raise HoszpError(st, what)
+
+    def _moment(self, fn, what, out, stream, sync, check):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.nfields, dtype=torch.float64, device=self.device)
+        _check(fn(self.handle, _dev_ptr(out), _stream_ptr(stream)), what)
+        if sync:
+            torch.cuda.synchronize(self.device)
+            if check:
+                self.check(what)
+        return out
+
+    def mean(self, out=None, stream=None, sync: bool = True, check: bool = True):
+        """Per-field means (Sec. V-B), one launch."""
+        return self._moment(self._lib.hoszp_batch_mean, "batch_mean", out, stream, sync, check)
+
+    def var(self, out=None, stream=None, sync: bool = True, check: bool = True):
+        """Per-field population variances (Sec. V-B), one launch."""
+        return self._moment(self._lib.hoszp_batch_var, "batch_var", out, stream, sync, check)
+
+    def negate(self, stream=None):
+        """Every field negated in place (Sec. V-A), one launch."""
+        _check(self._lib.hoszp_batch_negate(self.handle, _stream_ptr(stream)), "batch_negate")
+
+    def add_scalar(self, s: float, stream=None):
+        """s added to every field in place (Sec. V-A), one launch (+ a per-field
+        quantization of s)."""
+        _check(self._lib.hoszp_batch_add_scalar(self.handle, float(s), _stream_ptr(stream)),
+               "batch_add_scalar")
+
+    def tune(self, stream=None):
+        """Pick each reduction's launch shape from timed runs; returns the picks."""
+        torch = _torch()
+        out = torch.empty(self.nfields, dtype=torch.float64, device=self.device)
+        _check(self._lib.hoszp_batch_tune(self.handle, _dev_ptr(out), _stream_ptr(stream)),
+               "batch_tune")
+        self.check("batch_tune")
+        return {"mean": self.config(0), "var": self.config(1)}
+
+    def config(self, op: int):
+        st, cps = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self._lib.hoszp_batch_config(self.handle, int(op), ctypes.byref(st),
+                                            ctypes.byref(cps)), "batch_config")
+        return {"stages": st.value, "ctas_per_sm": cps.value}
+

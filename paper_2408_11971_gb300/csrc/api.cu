@@ -378,6 +378,19 @@ int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
 }  // extern "C"
 
 namespace hz {
+// Context access for batch plans (batch.cu): grows the workspace to `tiles`
+// tiles and returns it with the context's device and SM count.
+int ctx_prepare(hoszp_ctx* ctx, uint64_t tiles, Ws* ws, int* device, int* num_sms) {
+  if (!ctx) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  const int rc = ensure_ws(ctx, tiles, 16);
+  if (rc) return rc;
+  *ws = ctx->ws;
+  *device = ctx->device;
+  *num_sms = ctx->num_sms;
+  return HOSZP_OK;
+}
+
 // Workspace access for the traditional-workflow helpers (baseline.cu); the
 // grid they use (SMs x 4) stays within the partials the workspace holds.
 Ws ctx_workspace(hoszp_ctx* ctx) {

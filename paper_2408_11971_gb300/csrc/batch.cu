@@ -1,0 +1,617 @@
+// batch.cu — batched persistent execution over many resident streams.
+//
+// A snapshot holds thousands of fields of very different sizes; one launch per
+// field per operator would spend more time launching than working on the small
+// ones. A batch plan fixes a set of resident streams and lays their tiles end
+// to end in one global tile space (field f owns tiles [tile0_f, tile0_f +
+// ntiles_f)); each operator is then one persistent launch in which CTA b takes
+// the contiguous tile range [T b / G, T (b+1) / G) and walks the field table
+// as its range crosses field boundaries. Per-field results are finished inside
+// the same launch by whichever warp contributes a field's last tiles.
+//
+// Plan creation parses every header and runs each stream's rate pre-scan once
+// (the prefixes stay valid for negation and scalar addition, which change no
+// rate). The operators launch no allocation and no synchronization, so a
+// sequence of them can be captured in a CUDA graph. A small autotuner picks,
+// per reduction, the pipeline depth and the CTAs per SM from timed runs on the
+// plan's own data.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "hz_moments.cuh"
+#include "hz_scalar.cuh"
+#include "hz_kernels.cuh"
+
+namespace hz {
+int ctx_prepare(hoszp_ctx* ctx, uint64_t tiles, Ws* ws, int* device, int* num_sms);  // api.cu
+}  // namespace hz
+
+namespace hz {
+namespace {
+
+// One field of a plan (device table).
+struct BField {
+  const uint8_t* c;
+  uint8_t* cw;       // same stream, writable (in-place operators)
+  Info h;
+  uint64_t tile0;    // first tile in the global tile space
+  uint64_t ntiles;
+  uint64_t pre0;     // first word of the field's (nc, r) prefixes in pre[]
+  uint64_t ch0[2];   // first 16-byte chunk of the field's metadata region: [0] negate, [1] add
+  uint64_t nch[2];
+  long long rho;     // scalar addition: this field's quantized scalar (0: field skipped)
+};
+
+// ---------------------------------------------------------------- plan parsing
+__global__ void k_bparse(const uint8_t* const* ptrs, const uint64_t* bytes, uint32_t nf,
+                         BField* F, int* status) {
+  const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  BField b{};
+  b.c = ptrs[f];
+  b.cw = const_cast<uint8_t*>(ptrs[f]);
+  b.h = parse_header(ptrs[f], bytes[f]);
+  if (!b.h.ok) set_status(status, HOSZP_ERR_FORMAT);
+  else if (b.h.n == 0) set_status(status, HOSZP_ERR_ARG);
+  b.ntiles = b.h.ok ? ntiles_of(b.h.nb) : 0;
+  if (b.h.ok) {
+    b.nch[0] = (align16(b.h.o_plane) - b.h.o_out) / 16;
+    b.nch[1] = (b.h.o_sign - b.h.o_out) / 16;
+  }
+  F[f] = b;
+}
+
+// ---------------------------------------------------------------- field walk
+// Index of the field holding global tile t (fields have >= 1 tile; tile0 grows).
+__device__ __forceinline__ uint32_t field_of_tile(const BField* F, uint32_t nf, uint64_t t) {
+  uint32_t lo = 0, hi = nf;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (F[mid].tile0 <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ uint32_t field_of_chunk(const BField* F, uint32_t nf, int op,
+                                                   uint64_t ch) {
+  uint32_t lo = 0, hi = nf;
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (F[mid].ch0[op] <= ch) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The current field of a walker (one per loader warp), advanced as tiles grow.
+struct Walk {
+  uint32_t f;
+  uint64_t tile0, ntiles, pre0;
+  const uint8_t* c;
+  Info h;
+  __device__ __forceinline__ void load(const BField* F, uint32_t fi) {
+    f = fi;
+    const BField& b = F[fi];
+    tile0 = b.tile0;
+    ntiles = b.ntiles;
+    pre0 = b.pre0;
+    c = b.c;
+    h = b.h;
+  }
+  __device__ __forceinline__ void to_tile(const BField* F, uint32_t nf, uint64_t t) {
+    if (f == ~0u || t < tile0) load(F, field_of_tile(F, nf, t));
+    while (t >= tile0 + ntiles && f + 1 < nf) load(F, f + 1);
+  }
+};
+
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* p, unsigned long long lo,
+                                                unsigned long long hi) {
+  const unsigned long long old = atomicAdd(p, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(p + 1, hi + carry);
+}
+
+// ---------------------------------------------------------------- batched mean / variance
+// Per field: acc[4f .. 4f+3] = S1 (128-bit two's complement), S2 (128-bit);
+// done[f] counts warp-tiles (16 per tile); both are zero between launches.
+template <bool VAR, int STAGES>
+__global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_bmoments(
+    const BField* __restrict__ F, uint32_t nf, uint64_t total_tiles,
+    const unsigned long long* __restrict__ pre, unsigned long long* acc, unsigned int* done,
+    double* results, int* status) {
+  constexpr uint32_t RING = 8192;
+  extern __shared__ __align__(16) uint8_t dyn[];
+  InStage* stages = reinterpret_cast<InStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + STAGES);
+  __shared__ uint64_t full[STAGES], ready[STAGES], empty[STAGES];
+  __shared__ unsigned long long stage_tile[STAGES];
+  __shared__ uint32_t stage_field[STAGES];
+  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7, lane = tid & 31;
+  const uint64_t G = gridDim.x;
+  const uint64_t t_begin = total_tiles * blockIdx.x / G;
+  const uint64_t t_end = total_tiles * (blockIdx.x + 1) / G;
+  ring_init3<STAGES>(full, ready, empty);
+  if (w >= LOADER_WARP) {
+    __shared__ uint32_t s_beg[STAGES];
+    __shared__ unsigned long long s_win[32][4];
+    PlaneRing<STAGES, RING> pr;
+    pr.init(ring, s_beg);
+    Walk wk;
+    wk.f = ~0u;
+    uint64_t win_f = ~0ull, win0 = 0;  // prefixes of local tiles win0 .. win0+31 of field win_f
+    loader_warps<STAGES>(
+        w - LOADER_WARP, stage_tile, full, ready, empty, total_tiles, status,
+        [&](uint32_t k) {
+          const uint64_t t = t_begin + k;
+          return (unsigned long long)(t < t_end ? t : total_tiles);
+        },
+        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
+            auto&& release_one) {
+          wk.to_tile(F, nf, t);
+          const uint64_t lt = t - wk.tile0;
+          if (win_f != wk.f || lt >= win0 + 32) {  // refill the prefix window
+            win_f = wk.f;
+            win0 = lt;
+            __syncwarp();
+            if (lt + lane < wk.ntiles) {
+              const ulonglong2* p =
+                  reinterpret_cast<const ulonglong2*>(pre + wk.pre0 + 2 * (lt + lane));
+              const ulonglong2 a = __ldg(p), b = __ldg(p + 1);
+              s_win[lane][0] = a.x;
+              s_win[lane][1] = a.y;
+              s_win[lane][2] = b.x;
+              s_win[lane][3] = b.y;
+            }
+            __syncwarp();
+          }
+          unsigned long long pv[4];
+#pragma unroll
+          for (int i = 0; i < 4; i++) pv[i] = s_win[lt - win0][i];
+          const TileSpan sp = tile_span(wk.h, lt, pv);
+          const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
+          const uint32_t at = pr.commit(k, p0, sp.plane_words());
+          if (lane == 0) {
+            stage_field[sk] = wk.f;
+            issue_in_tile(&stages[sk], &full[sk], wk.c, wk.h, lt, sp, ring, at);
+          }
+        },
+        [&](int sk, unsigned long long t) {
+          wk.to_tile(F, nf, t);
+          prepare_tile(stages[sk], t - wk.tile0, wk.h);
+        });
+  } else {
+    const OctetSel S = octet_sel(j);
+    uint32_t wlo, whi;
+    mean_weights(j, wlo, whi);
+    long long s1 = 0;
+    U128 s2 = {0, 0};
+    uint32_t cur = ~0u, cnt = 0;  // field being accumulated, warp-tiles of it
+    auto flush = [&]() {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        if (VAR) {
+          U128 t;
+          t.lo = __shfl_xor_sync(0xffffffffu, s2.lo, o);
+          t.hi = __shfl_xor_sync(0xffffffffu, s2.hi, o);
+          add_u128(s2, t);
+        }
+      }
+      if (lane == 0) {
+        unsigned long long* a = acc + 4 * (uint64_t)cur;
+        atomic_add_u128(a, (unsigned long long)s1, s1 < 0 ? ~0ull : 0ull);
+        if (VAR) atomic_add_u128(a + 2, s2.lo, s2.hi);
+        __threadfence();
+        const unsigned int need = (unsigned int)(F[cur].ntiles * NCW);
+        const unsigned int prev = atomicAdd(&done[cur], cnt);
+        if (prev + cnt == need) {  // this warp completes the field
+          __threadfence();
+          const volatile unsigned long long* va = a;
+          const __int128 S1 = (__int128)(((unsigned __int128)va[1] << 64) | va[0]);
+          U128 S2 = {va[2], va[3]};
+          const Info& h = F[cur].h;
+          results[cur] = moment_finish(S1, S2, h.n, h.eps_q, VAR);
+          a[0] = a[1] = a[2] = a[3] = 0;
+          done[cur] = 0;
+        }
+      }
+      s1 = 0;
+      s2 = {0, 0};
+      cnt = 0;
+    };
+    RingPos rp{0, 0u};
+    for (;;) {
+      const int st = rp.s;
+      mbar_wait(&ready[st], rp.par, status);
+      const unsigned long long t = stage_tile[st];
+      if (t >= total_tiles) break;
+      const uint32_t f = stage_field[st];
+      if (f != cur) {
+        if (cur != ~0u) flush();
+        cur = f;
+      }
+      moments_octet<VAR>(stages[st], ring, g, j, w, S, wlo, whi, s1, s2, [&]() {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+      });
+      cnt++;
+      rp.next<STAGES>();
+    }
+    if (cur != ~0u) flush();
+  }
+}
+
+template <bool VAR, int STAGES>
+cudaError_t launch_bmoments(int grid, cudaStream_t s, const BField* F, uint32_t nf,
+                            uint64_t total_tiles, const unsigned long long* pre,
+                            unsigned long long* acc, unsigned int* done, double* results,
+                            int* status) {
+  const size_t smem = STAGES * sizeof(InStage) + 8192 * sizeof(uint64_t);
+  static std::once_flag once;
+  std::call_once(once, [&]() {
+    cudaFuncSetAttribute(k_bmoments<VAR, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  });
+  k_bmoments<VAR, STAGES><<<grid, CONSUMER_THREADS, smem, s>>>(F, nf, total_tiles, pre, acc,
+                                                               done, results, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched negate / add_scalar
+// In place over the fields' metadata regions laid end to end as 16-byte
+// chunks (negation: outliers and sign words; scalar addition: outliers).
+__global__ void k_brho(BField* F, uint32_t nf, double s, int* status) {
+  const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  BField& b = F[f];
+  long long rho = 0;
+  if (!quantize_scalar(s, b.h.eps_q, rho)) {
+    set_status(status, HOSZP_ERR_RANGE);
+    b.rho = 0;
+    return;
+  }
+  const long long arho = rho < 0 ? -rho : rho;
+  if ((long long)b.h.qbound + arho > HOSZP_QLIM) {
+    set_status(status, HOSZP_ERR_OVERFLOW);
+    b.rho = 0;
+    return;
+  }
+  b.rho = rho;
+  if (rho != 0) {  // the header's bound grows by |rho| (Sec. V-A)
+    b.h.qbound = (uint32_t)((long long)b.h.qbound + arho);
+    reinterpret_cast<hoszp_header*>(b.cw)->qbound = b.h.qbound;
+  }
+}
+
+template <bool NEG>
+__global__ void __launch_bounds__(512) k_bmeta(const BField* __restrict__ F, uint32_t nf,
+                                               uint64_t total_ch) {
+  constexpr int OP = NEG ? 0 : 1;
+  const uint64_t G = gridDim.x;
+  const uint64_t c_begin = total_ch * blockIdx.x / G, c_end = total_ch * (blockIdx.x + 1) / G;
+  if (c_begin >= c_end) return;
+  __shared__ uint32_t s_f;
+  if (threadIdx.x == 0) s_f = field_of_chunk(F, nf, OP, c_begin);
+  __syncthreads();
+  for (uint32_t f = s_f; f < nf; f++) {
+    const BField& b = F[f];
+    const uint64_t f0 = b.ch0[OP], f1 = f0 + b.nch[OP];
+    if (f0 >= c_end) break;
+    const uint64_t lo = max(f0, c_begin), hi = min(f1, c_end);
+    if (lo >= hi) continue;
+    const int r32 = (int)b.rho;
+    if (!NEG && r32 == 0) continue;
+    const Info& h = b.h;
+    uint4* base = reinterpret_cast<uint4*>(b.cw + h.o_out);  // chunk i of the region
+    constexpr int U = 4;
+    const uint64_t n = hi - lo, off = lo - f0;
+    for (uint64_t i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
+      uint4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (i0 + u * blockDim.x < n) v[u] = base[off + i0 + u * blockDim.x];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint64_t i = i0 + u * blockDim.x;
+        if (i >= n) break;
+        const uint64_t bpos = h.o_out + 16 * (off + i);
+        if (bpos < h.o_sign) {  // 4 outliers (padding past nb unchanged)
+          const uint64_t k0 = (bpos - h.o_out) >> 2;
+          uint32_t* wv = reinterpret_cast<uint32_t*>(&v[u]);
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (k0 + k < h.nb)
+              wv[k] = NEG ? (uint32_t)(-(int)wv[k]) : (uint32_t)((int)wv[k] + r32);
+        } else if (NEG) {  // sign words (the second may be a plane word)
+          v[u].x = ~v[u].x;
+          v[u].y = ~v[u].y;
+          if (bpos + 8 < h.o_plane) {
+            v[u].z = ~v[u].z;
+            v[u].w = ~v[u].w;
+          }
+        }
+        base[off + i] = v[u];
+      }
+    }
+  }
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline int rc_of(cudaError_t e) {
+  if (e == cudaSuccess) return HOSZP_OK;
+  cudaGetLastError();
+  return HOSZP_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace hz
+
+using namespace hz;
+
+// Autotuned launch shape of one reduction: pipeline depth (variant) and CTAs per SM.
+struct BatchCfg {
+  int variant;  // 0: 8 stages, 1: 4 stages
+  int cps;      // CTAs per SM (1 or 2)
+};
+
+struct hoszp_batch {
+  hoszp_ctx* ctx;
+  int device, num_sms;
+  uint32_t nf;
+  uint64_t total_tiles, total_ch[2];
+  void* mem;
+  BField* d_fields;
+  unsigned long long* d_pre;
+  unsigned long long* d_acc;
+  unsigned int* d_done;
+  int* status;  // the plan's own status word (first device error of its operators)
+  BatchCfg cfg[2];  // mean, variance
+};
+
+namespace {
+
+int run_moments(hoszp_batch* b, bool var, const BatchCfg& c, double* d_results,
+                cudaStream_t s) {
+  const int grid = b->num_sms * c.cps;
+  cudaError_t e;
+  if (var)
+    e = c.variant == 0 ? launch_bmoments<true, 8>(grid, s, b->d_fields, b->nf, b->total_tiles,
+                                                   b->d_pre, b->d_acc, b->d_done, d_results,
+                                                   b->status)
+                       : launch_bmoments<true, 4>(grid, s, b->d_fields, b->nf, b->total_tiles,
+                                                   b->d_pre, b->d_acc, b->d_done, d_results,
+                                                   b->status);
+  else
+    e = c.variant == 0 ? launch_bmoments<false, 8>(grid, s, b->d_fields, b->nf, b->total_tiles,
+                                                    b->d_pre, b->d_acc, b->d_done, d_results,
+                                                    b->status)
+                       : launch_bmoments<false, 4>(grid, s, b->d_fields, b->nf, b->total_tiles,
+                                                    b->d_pre, b->d_acc, b->d_done, d_results,
+                                                    b->status);
+  return rc_of(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_streams,
+                       const size_t* stream_bytes, hoszp_batch** out) {
+  if (!ctx || !out || nfields == 0 || !d_streams || !stream_bytes) return HOSZP_ERR_ARG;
+  *out = nullptr;
+  for (uint32_t f = 0; f < nfields; f++) {
+    if (!d_streams[f] || ((uintptr_t)d_streams[f] & 15u) || stream_bytes[f] < HOSZP_HEADER_BYTES)
+      return HOSZP_ERR_ARG;
+  }
+  Ws ws;
+  int device = 0, sms = 0;
+  int rc = ctx_prepare(ctx, 1, &ws, &device, &sms);
+  if (rc) return rc;
+  DeviceGuard guard(device);
+  // parse every header on the device
+  std::vector<BField> F(nfields);
+  void* tmp = nullptr;
+  const size_t tbytes = nfields * (sizeof(void*) + sizeof(uint64_t)) + nfields * sizeof(BField);
+  if (cudaMalloc(&tmp, tbytes) != cudaSuccess) return rc_of(cudaErrorMemoryAllocation);
+  const uint8_t** d_ptrs = (const uint8_t**)tmp;
+  uint64_t* d_bytes = (uint64_t*)(d_ptrs + nfields);
+  BField* d_tmpF = (BField*)(d_bytes + nfields);
+  std::vector<uint64_t> hb(stream_bytes, stream_bytes + nfields);
+  cudaMemcpy(d_ptrs, d_streams, nfields * sizeof(void*), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_bytes, hb.data(), nfields * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  k_bparse<<<(nfields + 127) / 128, 128>>>(d_ptrs, d_bytes, nfields, d_tmpF, ws.status);
+  int st = 0;
+  if (cudaMemcpy(F.data(), d_tmpF, nfields * sizeof(BField), cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      cudaMemcpy(&st, ws.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaFree(tmp);
+    return rc_of(cudaErrorUnknown);
+  }
+  cudaFree(tmp);
+  if (st) {
+    cudaMemset(ws.status, 0, sizeof(int));
+    return st;
+  }
+  // global tile space, prefix offsets, metadata chunk spaces
+  uint64_t tiles = 0, pre_words = 0, ch[2] = {0, 0}, max_tiles = 0;
+  for (uint32_t f = 0; f < nfields; f++) {
+    F[f].tile0 = tiles;
+    F[f].pre0 = pre_words;
+    for (int o = 0; o < 2; o++) {
+      F[f].ch0[o] = ch[o];
+      ch[o] += F[f].nch[o];
+    }
+    tiles += F[f].ntiles;
+    pre_words += 2 * (F[f].ntiles + 1);
+    max_tiles = std::max<uint64_t>(max_tiles, F[f].ntiles);
+  }
+  hoszp_batch* b = new hoszp_batch();
+  b->ctx = ctx;
+  b->device = device;
+  b->num_sms = sms;
+  b->nf = nfields;
+  b->total_tiles = tiles;
+  b->total_ch[0] = ch[0];
+  b->total_ch[1] = ch[1];
+  b->cfg[0] = b->cfg[1] = BatchCfg{0, 2};
+  const size_t fbytes = (nfields * sizeof(BField) + 255) / 256 * 256;
+  const size_t pbytes = (pre_words * 8 + 255) / 256 * 256;
+  const size_t abytes = (nfields * 32 + 255) / 256 * 256;
+  const size_t dbytes = (nfields * 4 + 255) / 256 * 256;
+  if (cudaMalloc(&b->mem, fbytes + pbytes + abytes + dbytes + 256) != cudaSuccess) {
+    delete b;
+    return rc_of(cudaErrorMemoryAllocation);
+  }
+  uint8_t* m = (uint8_t*)b->mem;
+  b->d_fields = (BField*)m;
+  b->d_pre = (unsigned long long*)(m + fbytes);
+  b->d_acc = (unsigned long long*)(m + fbytes + pbytes);
+  b->d_done = (unsigned int*)(m + fbytes + pbytes + abytes);
+  b->status = (int*)(m + fbytes + pbytes + abytes + dbytes);
+  cudaMemcpy(b->d_fields, F.data(), nfields * sizeof(BField), cudaMemcpyHostToDevice);
+  cudaMemset(b->d_acc, 0, abytes + dbytes + 256);
+  // each stream's rate pre-scan, once
+  rc = ctx_prepare(ctx, max_tiles + 1, &ws, &device, &sms);
+  if (rc) {
+    hoszp_batch_destroy(b);
+    return rc;
+  }
+  Launch lc;
+  lc.grid = sms;
+  lc.stream = 0;
+  for (uint32_t f = 0; f < nfields; f++) {
+    const cudaError_t e = launch_scan(lc, F[f].c, F[f].h.size, b->d_pre + F[f].pre0, ws);
+    if (e != cudaSuccess) {
+      hoszp_batch_destroy(b);
+      return rc_of(e);
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&st, ws.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    hoszp_batch_destroy(b);
+    return rc_of(cudaErrorUnknown);
+  }
+  if (st) {
+    cudaMemset(ws.status, 0, sizeof(int));
+    hoszp_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return HOSZP_OK;
+}
+
+void hoszp_batch_destroy(hoszp_batch* b) {
+  if (!b) return;
+  DeviceGuard guard(b->device);
+  if (b->mem) cudaFree(b->mem);
+  delete b;
+}
+
+int hoszp_batch_get_status(hoszp_batch* b, int* status) {
+  if (!b || !status) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  int v = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&v, b->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(b->status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    *status = HOSZP_ERR_CUDA;
+    return HOSZP_ERR_CUDA;
+  }
+  *status = v;
+  return HOSZP_OK;
+}
+
+int hoszp_batch_info(const hoszp_batch* b, uint32_t* nfields, uint64_t* total_tiles) {
+  if (!b) return HOSZP_ERR_ARG;
+  if (nfields) *nfields = b->nf;
+  if (total_tiles) *total_tiles = b->total_tiles;
+  return HOSZP_OK;
+}
+
+int hoszp_batch_mean(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
+  if (!b || !d_results || ((uintptr_t)d_results & 7u)) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  return run_moments(b, false, b->cfg[0], d_results, (cudaStream_t)stream);
+}
+
+int hoszp_batch_var(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
+  if (!b || !d_results || ((uintptr_t)d_results & 7u)) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  return run_moments(b, true, b->cfg[1], d_results, (cudaStream_t)stream);
+}
+
+int hoszp_batch_negate(hoszp_batch* b, hoszp_stream_t stream) {
+  if (!b) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  if (b->total_ch[0] == 0) return HOSZP_OK;
+  k_bmeta<true><<<b->num_sms * 4, 512, 0, (cudaStream_t)stream>>>(b->d_fields, b->nf,
+                                                                  b->total_ch[0]);
+  return rc_of(cudaGetLastError());
+}
+
+int hoszp_batch_add_scalar(hoszp_batch* b, double s, hoszp_stream_t stream) {
+  if (!b || !(s == s) || s - s != 0.0) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  const cudaStream_t cs = (cudaStream_t)stream;
+  k_brho<<<(b->nf + 127) / 128, 128, 0, cs>>>(b->d_fields, b->nf, s, b->status);
+  if (b->total_ch[1] == 0) return rc_of(cudaGetLastError());
+  k_bmeta<false><<<b->num_sms * 4, 512, 0, cs>>>(b->d_fields, b->nf, b->total_ch[1]);
+  return rc_of(cudaGetLastError());
+}
+
+int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
+  if (!b || !d_results) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const BatchCfg cands[4] = {{0, 2}, {0, 1}, {1, 2}, {1, 1}};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return rc_of(cudaErrorUnknown);
+  int rc = HOSZP_OK;
+  for (int op = 0; op < 2 && !rc; op++) {
+    float best = 1e30f;
+    BatchCfg pick = b->cfg[op];
+    for (const BatchCfg& c : cands) {
+      if ((rc = run_moments(b, op == 1, c, d_results, s))) break;  // warm-up
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3 && !rc; r++) rc = run_moments(b, op == 1, c, d_results, s);
+      cudaEventRecord(e1, s);
+      if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = rc ? rc : HOSZP_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    b->cfg[op] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm) {
+  if (!b || op < 0 || op > 1) return HOSZP_ERR_ARG;
+  if (stages) *stages = b->cfg[op].variant == 0 ? 8 : 4;
+  if (ctas_per_sm) *ctas_per_sm = b->cfg[op].cps;
+  return HOSZP_OK;
+}
+
+}  // extern "C"

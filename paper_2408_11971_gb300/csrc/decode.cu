@@ -3,7 +3,7 @@
 // sum the quantized integers exactly and finish in FP64.
 #include <cfloat>
 
-#include "hz_ws.cuh"
+#include "hz_moments.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -101,57 +101,6 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
 }
 
 // ---------------------------------------------------------------- mean / variance
-// 128-bit helpers for the exact sums.
-struct U128 {
-  unsigned long long lo, hi;
-};
-__device__ __forceinline__ void add_u64(U128& a, unsigned long long v) {
-  a.lo += v;
-  a.hi += (a.lo < v) ? 1ull : 0ull;
-}
-__device__ __forceinline__ void add_u128(U128& a, const U128& b) {
-  a.lo += b.lo;
-  a.hi += b.hi + ((a.lo < b.lo) ? 1ull : 0ull);
-}
-
-// exact unsigned 256-bit product helpers for the variance numerator
-struct U256 {
-  unsigned long long w[4];
-};
-__device__ __forceinline__ U256 mul_u128_u128(unsigned __int128 a, unsigned __int128 b) {
-  unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
-  unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
-  unsigned __int128 p00 = (unsigned __int128)a0 * b0, p01 = (unsigned __int128)a0 * b1;
-  unsigned __int128 p10 = (unsigned __int128)a1 * b0, p11 = (unsigned __int128)a1 * b1;
-  U256 r;
-  r.w[0] = (unsigned long long)p00;
-  unsigned __int128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
-  r.w[1] = (unsigned long long)mid;
-  unsigned __int128 hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (unsigned long long)p11;
-  r.w[2] = (unsigned long long)hi;
-  r.w[3] = (unsigned long long)(hi >> 64) + (unsigned long long)(p11 >> 64);
-  return r;
-}
-__device__ __forceinline__ U256 sub_u256(const U256& a, const U256& b) {  // a >= b
-  U256 r;
-  unsigned long long borrow = 0;
-  for (int i = 0; i < 4; i++) {
-    unsigned long long bi = b.w[i] + borrow;
-    unsigned long long nb = (bi < borrow) || (a.w[i] < bi) ? 1ull : 0ull;
-    r.w[i] = a.w[i] - bi;
-    borrow = nb;
-  }
-  return r;
-}
-__device__ __forceinline__ double u256_to_double(const U256& a) {
-  const double two64 = 18446744073709551616.0;
-  double d = (double)a.w[3];
-  d = d * two64 + (double)a.w[2];
-  d = d * two64 + (double)a.w[1];
-  d = d * two64 + (double)a.w[0];
-  return d;
-}
-
 constexpr int MOM_STAGES = 8;
 constexpr uint32_t MOM_RING = 8192;  // plane-ring words (64 KB)
 
@@ -175,14 +124,8 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
   long long s1 = 0;  // per thread: |q| <= 2^30, far fewer than 2^32 values per thread
   U128 s2 = {0, 0};
   const OctetSel S = octet_sel(j);
-  // weight bytes 64 - (8j + t) of the block sum (0 at position 0)
-  uint32_t wlo = 0, whi = 0;
-#pragma unroll
-  for (int t = 0; t < 4; t++) {
-    wlo |= (uint32_t)(64 - 8 * j - t) << (8 * t);
-    whi |= (uint32_t)(64 - 8 * j - 4 - t) << (8 * t);
-  }
-  if (j == 0) wlo &= 0xffffff00u;
+  uint32_t wlo, whi;
+  mean_weights(j, wlo, whi);
   ring_init3<MOM_STAGES>(full, ready, empty);
   if (w >= LOADER_WARP) {
     const uint64_t G = gridDim.x;
@@ -211,40 +154,12 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
       mbar_wait(&ready[rp.s], rp.par, ws.status);
       const unsigned long long tile = stage_tile[rp.s];
       if (tile >= ntiles) break;
-      const InStage& sg = stages[rp.s];
-      const BlockRef br = block_ref_s(sg, ring, g, j);
-      const int kmax = sg.kmx[w];
-      const bool full_tile = sg.nvalid == TILE && sg.lastlen == L;
-      if (!VAR && kmax <= 2 && full_tile) {
-        const int v = octet_sum_fast(br, kmax, j, S, wlo, whi);
+      const int st = rp.s;
+      moments_octet<VAR>(stages[st], ring, g, j, w, S, wlo, whi, s1, s2, [&]() {
         __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[rp.s]);
-        rp.next<MOM_STAGES>();
-        s1 += v;
-        if (j == 0) s1 += (long long)L * br.outlier;
-        continue;
-      }
-      int d[8];
-      octet_deltas(br, kmax, j, S, d);
-      __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(&empty[rp.s]);
+        if ((tid & 31) == 0) mbar_arrive(&empty[st]);
+      });
       rp.next<MOM_STAGES>();
-      if (!VAR) {
-        s1 += octet_sum_q(br, d, j, kmax);
-      } else {
-        int q[8];
-        octet_values(br, d, j, q);
-        long long a = 0;
-        unsigned long long b = 0;  // 8 squares of |q| <= 2^30 stay below 2^63
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-          const int qq = (8 * j + t < br.len) ? q[t] : 0;
-          a += qq;
-          b += (unsigned long long)((long long)qq * qq);
-        }
-        s1 += a;
-        add_u64(s2, b);
-      }
     }
   }
   // CTA reduction -> per-CTA partial
@@ -291,24 +206,7 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
     if (h.ok && h.n == 0) {
       set_status(ws.status, HOSZP_ERR_ARG);
     } else if (h.ok) {
-      const double e2 = 2.0 * (double)h.eps_q;
-      if (!VAR) {
-        // sign and magnitude: hi * 2^64 + lo without cancellation
-        const unsigned __int128 m = (unsigned __int128)(S1 < 0 ? -S1 : S1);
-        const double md = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 +
-                          (double)(unsigned long long)m;
-        const double s1d = S1 < 0 ? -md : md;
-        res = (s1d / (double)h.n) * e2;
-      } else {
-        // n S2 - S1^2 >= 0 exactly (Cauchy-Schwarz), in 256-bit integers
-        unsigned __int128 s2u = ((unsigned __int128)S2.hi << 64) | S2.lo;
-        unsigned __int128 a1 = (unsigned __int128)(S1 < 0 ? -S1 : S1);
-        U256 nS2 = mul_u128_u128(s2u, (unsigned __int128)h.n);
-        U256 S1sq = mul_u128_u128(a1, a1);
-        U256 D = sub_u256(nS2, S1sq);
-        const double dn = (double)h.n;
-        res = (u256_to_double(D) / (dn * dn)) * (e2 * e2);
-      }
+      res = moment_finish(S1, S2, h.n, h.eps_q, VAR);
     }
     *result = res;
     launch_reset(ws);

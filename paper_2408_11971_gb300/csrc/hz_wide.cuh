@@ -1,0 +1,80 @@
+// hz_wide.cuh — exact wide-integer helpers for the reductions (Sec. V-B):
+// 128-bit sums, the 256-bit variance numerator, and the FP64 finish.
+#pragma once
+#include <cstdint>
+
+namespace hz {
+
+struct U128 {
+  unsigned long long lo, hi;
+};
+__device__ __forceinline__ void add_u64(U128& a, unsigned long long v) {
+  a.lo += v;
+  a.hi += (a.lo < v) ? 1ull : 0ull;
+}
+__device__ __forceinline__ void add_u128(U128& a, const U128& b) {
+  a.lo += b.lo;
+  a.hi += b.hi + ((a.lo < b.lo) ? 1ull : 0ull);
+}
+
+// exact unsigned 256-bit product helpers for the variance numerator
+struct U256 {
+  unsigned long long w[4];
+};
+__device__ __forceinline__ U256 mul_u128_u128(unsigned __int128 a, unsigned __int128 b) {
+  unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
+  unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
+  unsigned __int128 p00 = (unsigned __int128)a0 * b0, p01 = (unsigned __int128)a0 * b1;
+  unsigned __int128 p10 = (unsigned __int128)a1 * b0, p11 = (unsigned __int128)a1 * b1;
+  U256 r;
+  r.w[0] = (unsigned long long)p00;
+  unsigned __int128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
+  r.w[1] = (unsigned long long)mid;
+  unsigned __int128 hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (unsigned long long)p11;
+  r.w[2] = (unsigned long long)hi;
+  r.w[3] = (unsigned long long)(hi >> 64) + (unsigned long long)(p11 >> 64);
+  return r;
+}
+__device__ __forceinline__ U256 sub_u256(const U256& a, const U256& b) {  // a >= b
+  U256 r;
+  unsigned long long borrow = 0;
+  for (int i = 0; i < 4; i++) {
+    unsigned long long bi = b.w[i] + borrow;
+    unsigned long long nb = (bi < borrow) || (a.w[i] < bi) ? 1ull : 0ull;
+    r.w[i] = a.w[i] - bi;
+    borrow = nb;
+  }
+  return r;
+}
+__device__ __forceinline__ double u256_to_double(const U256& a) {
+  const double two64 = 18446744073709551616.0;
+  double d = (double)a.w[3];
+  d = d * two64 + (double)a.w[2];
+  d = d * two64 + (double)a.w[1];
+  d = d * two64 + (double)a.w[0];
+  return d;
+}
+
+// mean = (S1 / n) * 2 eps_q ; variance = (2 eps_q)^2 (n S2 - S1^2) / n^2, the
+// numerator exact in 256-bit integers (n S2 >= S1^2 by Cauchy-Schwarz).
+__device__ __forceinline__ double moment_finish(__int128 S1, const U128& S2, uint64_t n,
+                                                float eps_q, bool var) {
+  const double e2 = 2.0 * (double)eps_q;
+  if (!var) {
+    // sign and magnitude: hi * 2^64 + lo without cancellation
+    const unsigned __int128 m = (unsigned __int128)(S1 < 0 ? -S1 : S1);
+    const double md =
+        (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 + (double)(unsigned long long)m;
+    const double s1d = S1 < 0 ? -md : md;
+    return (s1d / (double)n) * e2;
+  }
+  const unsigned __int128 s2u = ((unsigned __int128)S2.hi << 64) | S2.lo;
+  const unsigned __int128 a1 = (unsigned __int128)(S1 < 0 ? -S1 : S1);
+  const U256 nS2 = mul_u128_u128(s2u, (unsigned __int128)n);
+  const U256 S1sq = mul_u128_u128(a1, a1);
+  const U256 D = sub_u256(nS2, S1sq);
+  const double dn = (double)n;
+  return (u256_to_double(D) / (dn * dn)) * (e2 * e2);
+}
+
+}  // namespace hz

@@ -1,0 +1,167 @@
+"""Batched execution over many resident streams, against the single-stream
+operators and the oracle (through the C ABI).
+
+Each batched result must equal the single-stream operator on that field:
+bit-identical doubles for mean / variance (same exact integer sums, same FP64
+finish), identical bytes for in-place negation / scalar addition, and within
+1e-12 of the oracle.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def hz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2408_11971_gb300 as hz
+    from paper_2408_11971_gb300 import build
+
+    build.build()
+    O.build()
+    return hz
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def close(a, b, tol=REL_TOL):
+    return abs(a - b) <= tol * max(abs(b), 1e-300)
+
+
+def uneven_fields(seed=11):
+    """Fields of uneven sizes (1 value .. 2e5, ragged tails, constant fields),
+    each with its own relative bound."""
+    rng = np.random.default_rng(seed)
+    sizes = [1, 63, 64, 65, 4096, 4097, 50_000, 200_003, 7, 130_000]
+    sizes += [int(v) for v in np.exp(rng.uniform(np.log(10), np.log(80_000), 22))]
+    xs, ebs = [], []
+    for i, n in enumerate(sizes):
+        kind = i % 4
+        if kind == 0:
+            x = datagen.sines_1d(n, seed=100 + i) if n >= 64 else rng.normal(size=n).astype(np.float32)
+        elif kind == 1:
+            x = datagen.grf((n,), seed=200 + i) if n >= 2 else np.float32([0.5] * n)
+        elif kind == 2:
+            x = np.full(n, np.float32(rng.normal()), np.float32)  # constant field
+        else:
+            x = (rng.normal(size=n) * 10 ** rng.uniform(-2, 3)).astype(np.float32)
+        xs.append(np.ascontiguousarray(x, np.float32))
+        ebs.append(float(10 ** rng.uniform(-5, -2)))
+    return xs, ebs
+
+
+@pytest.fixture(scope="module")
+def fields(hz):
+    xs, ebs = uneven_fields()
+    cs = [hz.compress(dev(x), eb=e, mode="rel") for x, e in zip(xs, ebs)]
+    ocs = [O.compress(x, eb=e, mode="rel") for x, e in zip(xs, ebs)]
+    for c, oc in zip(cs, ocs):
+        assert np.array_equal(host(c), oc)
+    return xs, ebs, cs, ocs
+
+
+def test_batch_reductions(hz, fields):
+    _, _, cs, ocs = fields
+    work = [c.clone() for c in cs]
+    b = hz.Batch(work)
+    m, v = host(b.mean()), host(b.var())
+    for f, (c, oc) in enumerate(zip(work, ocs)):
+        assert m[f] == hz.mean(c) and v[f] == hz.var(c), f
+        assert close(m[f], O.mean(oc)) and close(v[f], O.var(oc)), f
+    # repeated launches reuse the per-field accumulators (reset in-kernel)
+    assert np.array_equal(host(b.mean()), m) and np.array_equal(host(b.var()), v)
+
+
+def test_batch_in_place_operators(hz, fields):
+    _, _, cs, ocs = fields
+    work = [c.clone() for c in cs]
+    b = hz.Batch(work)
+    b.negate()
+    torch.cuda.synchronize()
+    b.check()
+    neg = [O.negate(oc) for oc in ocs]
+    for f in range(len(work)):
+        assert np.array_equal(host(work[f]), neg[f]), f
+    b.add_scalar(0.37)
+    torch.cuda.synchronize()
+    b.check()
+    for f in range(len(work)):
+        assert np.array_equal(host(work[f]), O.add_scalar(neg[f], 0.37)), f
+    m = host(b.mean())
+    for f in range(len(work)):
+        assert close(m[f], O.mean(O.add_scalar(neg[f], 0.37))), f
+
+
+def test_batch_graph_capture(hz, fields):
+    _, _, cs, ocs = fields
+    work = [c.clone() for c in cs]
+    b = hz.Batch(work)
+    out = torch.zeros(len(work), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):  # warm-up outside capture
+        b.negate(stream=s)
+        b.negate(stream=s)
+        b.mean(out=out, stream=s, sync=False)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.negate(stream=s)
+        b.mean(out=out, stream=s, sync=False)
+    torch.cuda.synchronize()
+    ref = np.array([O.mean(oc) for oc in ocs])
+    for rep in range(4):
+        g.replay()
+        torch.cuda.synchronize()
+        sign = -1.0 if rep % 2 == 0 else 1.0
+        got = host(out)
+        for f in range(len(work)):
+            assert close(got[f], sign * ref[f]) or (ref[f] == 0 and got[f] == 0), (rep, f)
+    b.check()
+    for f in range(len(work)):  # an even number of negations
+        assert np.array_equal(host(work[f]), ocs[f]), f
+
+
+def test_batch_autotune(hz, fields):
+    _, _, cs, ocs = fields
+    b = hz.Batch([c.clone() for c in cs])
+    picks = b.tune()
+    for op in ("mean", "var"):
+        assert picks[op]["stages"] in (4, 8) and picks[op]["ctas_per_sm"] in (1, 2)
+    m = host(b.mean())
+    for f, oc in enumerate(ocs):
+        assert close(m[f], O.mean(oc)), f
+
+
+def test_batch_errors(hz, fields):
+    _, _, cs, _ = fields
+    bad = cs[4].clone()
+    bad[0] ^= 0xFF  # magic
+    with pytest.raises(hz.HoszpError) as e:
+        hz.Batch([cs[0], bad])
+    assert e.value.name == "FORMAT"
+    empty = hz.compress(dev(np.zeros(0, np.float32)), eb=0.1)
+    with pytest.raises(hz.HoszpError) as e:
+        hz.Batch([cs[0], empty])
+    assert e.value.name == "ARG"
+    # a scalar that leaves the integer range: no field changes, status RANGE
+    work = [c.clone() for c in cs[:3]]
+    b = hz.Batch(work)
+    b.add_scalar(1e30)
+    torch.cuda.synchronize()
+    assert b.status() == -5  # RANGE
+    for f in range(3):
+        assert torch.equal(work[f], cs[f])
