@@ -66,15 +66,15 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel sources have not changed since the counters were taken."""
+def ncu_traffic(op: str):
+    """DRAM bytes per call of operator `op` (all its kernels, scaled to the 512^3
+    workload) from the committed ncu summary, if the kernel sources have not
+    changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
-        e = d.get(kernel)
-        if e and e.get("csrc_sha") == csrc_hash():
-            return e
+        if d.get("csrc_sha") == csrc_hash():
+            return d["ops"].get(op)
     except Exception:
         pass
     return None
@@ -83,7 +83,7 @@ def ncu_traffic(kernel: str):
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -98,11 +98,13 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader",
-                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Median SM clock, max clock and throttle reasons over the samples taken
+        between host times t0 and t1 (datetime; all samples if not given)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -111,18 +113,23 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
+        import datetime
+
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1].split()[0]))
-                smax = max(smax, float(parts[2].split()[0]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                if t0 is not None and not (t0 <= ts <= t1):
+                    continue
+                sm.append(float(parts[2].split()[0]))
+                smax = max(smax, float(parts[3].split()[0]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
@@ -220,7 +227,7 @@ def profile_op(op: str, shape):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hoszp", choices=["hoszp", "reference"])
     ap.add_argument("--oracle-sample", type=int, default=1 << 24,
@@ -359,14 +366,18 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t_start, t_end = ev(), ev()
+    import datetime
+
+    h0 = datetime.datetime.now()
     t_start.record(stream)
     for k in range(K):
         step(marks[k])
     t_end.record(stream)
     torch.cuda.synchronize()
+    h1 = datetime.datetime.now()
     if dist is not None:
         dist.barrier()
-    clocks = clk.stop()
+    clocks = clk.stop(h0, h1)
     ctx.check("timed steps")
     total_ms = t_start.elapsed_time(t_end)
     if dist is not None:
@@ -437,11 +448,12 @@ def main():
                "add_scalar": "k_meta", "mul_scalar": "k_mul_scalar", "add": "k_add",
                "mean": "k_moments", "var": "k_moments", "decompress": "k_decompress"}
     achieved = alg[dom] / per_op_ms[dom] / 1e6
-    tr = ncu_traffic(kern_of[dom])
+    tr = ncu_traffic(dom)
     roofline = {"bound": "hbm", "op": dom, "kernel": kern_of[dom], "achieved": achieved,
                 "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                 "frac": achieved / peak, "alg_bytes_per_launch": alg[dom],
-                "traffic": (tr["dram_bytes_per_launch"] if tr else None)}
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "traffic_kernels": (tr["kernels"] if tr else None)}
 
     # end to end through host memory: pinned inputs in, results out, every step
     e2e = None
