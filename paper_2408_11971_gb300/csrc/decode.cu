@@ -4,6 +4,7 @@
 #include <cfloat>
 
 #include "hz_moments.cuh"
+#include "hz_super.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -213,6 +214,118 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
   }
 }
 
+// Mean alone: the bit-sliced column sums of hz_moments.cuh over the
+// super-tile pipeline of hz_super.cuh. MEAN_GROUPS groups of STILES compute
+// warps take the stages in turn; warp i of a group takes tile i of the stage,
+// and lane l blocks 2l and 2l+1 of that tile.
+constexpr int MEAN_GW = STILES;  // warps per group: one per tile of a stage
+constexpr int MEAN_GROUPS = 2;   // groups per CTA
+constexpr int MEAN_NCW = MEAN_GW * MEAN_GROUPS;
+constexpr int MEAN_THREADS = (MEAN_NCW + 1) * 32;  // + loader warp
+constexpr int MEAN_STAGES = 6;
+constexpr uint32_t MEAN_RING = 16384;  // plane-ring words (128 KB)
+constexpr int MEAN_MIN_CTAS = 1;       // resident CTAs per SM (shared memory)
+
+__device__ __forceinline__ void cta_sum_i128_partial(__int128 v, Partial* out, __int128* s_w) {
+  const int tid = threadIdx.x;
+  v = warp_sum_i128(v);
+  if ((tid & 31) == 0) s_w[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    __int128 t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+    Partial p;
+    p.s1_lo = (long long)(unsigned long long)t;
+    p.s1_hi = (long long)(t >> 64);
+    p.s2_lo = 0;
+    p.s2_hi = 0;
+    *out = p;
+  }
+}
+
+__global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result,
+    const unsigned long long* __restrict__ pre, Ws ws) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  SStage* stages = reinterpret_cast<SStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MEAN_STAGES);
+  __shared__ uint64_t full[MEAN_STAGES], empty[MEAN_STAGES];
+  __shared__ unsigned long long stage_st[MEAN_STAGES];
+  __shared__ __int128 s_w[MEAN_THREADS / 32];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const Info h = parse_header(c, c_bytes);
+  int bad = 0;
+  uint64_t ntiles = 0;
+  if (!h.ok) bad = HOSZP_ERR_FORMAT;
+  else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
+  const uint64_t nst = nsuper_of(ntiles);
+  const uint64_t G = gridDim.x;
+  // full: the loader's arrival; empty: the MEAN_GW warps of the group that took the stage
+  if (tid == 0) {
+    for (int k = 0; k < MEAN_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], MEAN_GW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  MeanAcc A;
+  A.init();
+  if (w == MEAN_NCW) {
+    __shared__ uint32_t s_beg[MEAN_STAGES];
+    __shared__ ulonglong2 s_win[32][STILES + 1];
+    super_loader<MEAN_STAGES, MEAN_RING, MEAN_GROUPS>(
+        stages, ring, s_beg, s_win, full, empty, stage_st, c, h, pre, ntiles, nst, ws.status,
+        [&](uint64_t k) { return blockIdx.x + k * G; });
+  } else if (w < MEAN_NCW) {
+    const int grp = w / MEAN_GW, ti = w % MEAN_GW;
+    const int lastlen = (int)(h.n - (h.nb - 1) * L);
+    for (uint64_t k = 0;; k++) {
+      const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
+      const int sk = (int)(u % MEAN_STAGES);
+      mbar_wait(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status);
+      const unsigned long long s = stage_st[sk];
+      if (s == ~0ull) break;
+      const SStage& sg = stages[sk];
+      const uint64_t tile = (uint64_t)STILES * s + ti;
+      const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+      const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
+      const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
+#pragma unroll 1
+      for (int j = 0; j < 2; j++) {  // blocks 2 lane and 2 lane + 1
+        const int b = 2 * lane + j;
+        const uint32_t r = j ? tr.r1 : tr.r0, ex = j ? tr.e1 : tr.e0;
+        const int len = (b < tr.nvt - 1) ? L
+                        : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+        const int O = sg.outlier[TILE * ti + b];
+        const uint64_t sw = r ? sgn[ex >> 16] : 0ull;
+        mean_block((int)r, len, O, sw, reinterpret_cast<const uint2*>(pls + (ex & 0xffffu)), A);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+    A.flush();
+  }
+  cta_sum_i128_partial(A.s1, &ws.partials[blockIdx.x], s_w);
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && tid == 0) {
+    __int128 S1 = 0;
+    for (unsigned int b = 0; b < gridDim.x; b++) {
+      const Partial p = ws.partials[b];
+      S1 += ((__int128)p.s1_hi << 64) | (unsigned long long)p.s1_lo;
+    }
+    const U128 S2 = {0, 0};
+    double res = 0.0;
+    if (h.ok && h.n == 0) {
+      set_status(ws.status, HOSZP_ERR_ARG);
+    } else if (h.ok) {
+      res = moment_finish(S1, S2, h.n, h.eps_q, false);
+    }
+    *result = res;
+    launch_reset(ws);
+  }
+}
+
 template <bool VAR>
 static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                                     double* result, Ws ws) {
@@ -232,8 +345,16 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                            bool variance, Ws ws) {
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
-  return variance ? launch_moments_t<true>(lc, c, c_bytes, result, ws)
-                  : launch_moments_t<false>(lc, c, c_bytes, result, ws);
+  if (variance) return launch_moments_t<true>(lc, c, c_bytes, result, ws);
+  const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_mean<<<persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem), MEAN_THREADS, smem,
+           lc.stream>>>(c, c_bytes, result, ws.pre[0], ws);
+  return cudaGetLastError();
 }
 
 }  // namespace hz

@@ -59,3 +59,140 @@ __device__ __forceinline__ void moments_octet(const InStage& sg, const uint64_t*
 }
 
 }  // namespace hz
+
+namespace hz {
+
+// ---------------------------------------------------------------- bit-sliced mean
+// The mean needs only S1 = sum_b [L_b O_b + sum_i (L_b - i) delta_{b,i}]
+// (Sec. V-B). For a full block (L_b = 64) write each delta through the r-bit
+// word u_i = |delta_i| at a non-negative position and 2^r - 1 - |delta_i| at a
+// negative one (the plane bits xor the sign bit), so that
+//     delta_i = u_i - s_i (2^r - 1)   and
+//     sum_i (64 - i) delta_i = sum_i (64 - i) u_i - (2^r - 1) W(s),
+// with W(m) = sum_i (64 - i) m_i, a weighted popcount. A lane owns two blocks
+// of a tile per visit and adds their u into per-position column sums kept
+// bit-sliced, one set per 32-position half: acc[k] holds bit k of every
+// position's running sum, and adding a block is a ripple-carry add over its
+// plane words, about two logic operations per column per 32 values, with no
+// transpose and no per-value arithmetic. The ripple stops at the warp's
+// largest rate: the carry word leaving the top column goes straight into the
+// exact sum as a weighted popcount, so the columns never overflow and are
+// converted once per thread. Planes at or above RF, and the stream's last
+// block when it is short, go through popcounts directly (both rare).
+__device__ __forceinline__ int wsum32(uint32_t m, int base) {
+  // sum over set bits l of m of (base - l)
+  const int t = __popc(m & 0xAAAAAAAAu) + 2 * __popc(m & 0xCCCCCCCCu) +
+                4 * __popc(m & 0xF0F0F0F0u) + 8 * __popc(m & 0xFF00FF00u) +
+                16 * __popc(m & 0xFFFF0000u);
+  return base * __popc(m) - t;
+}
+// both halves of a 64-bit word: sum over set bits i of (64 - i)
+__device__ __forceinline__ long long wsum64(uint32_t lo, uint32_t hi) {
+  return (long long)wsum32(lo, 64) + wsum32(hi, 32);
+}
+
+struct MeanAcc {
+  static constexpr int RF = 16;  // planes added through the columns
+  uint32_t a0[RF], a1[RF];       // columns of positions 0..31 and 32..63
+  __int128 s1;
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int k = 0; k < RF; k++) a0[k] = a1[k] = 0u;
+    s1 = 0;
+  }
+  // Moves the column sums into s1: sum_k 2^k W(acc[k]).
+  __device__ __forceinline__ void flush() {
+    long long t = 0;
+#pragma unroll
+    for (int k = 0; k < RF; k++) {
+      t += wsum64(a0[k], a1[k]) << k;
+      a0[k] = a1[k] = 0u;
+    }
+    s1 += t;
+  }
+};
+
+// Ripple-carry add of the first rl (<= R) planes of a block into columns
+// 0..R-1; returns the carry words leaving column R-1.
+template <int R>
+__device__ __forceinline__ void mean_cols(MeanAcc& A, const uint2* pl, int rl, uint32_t s0,
+                                          uint32_t s1, uint32_t& c0, uint32_t& c1) {
+#pragma unroll
+  for (int k = 0; k < R; k++) {
+    uint32_t u0 = 0u, u1 = 0u;
+    if (k < rl) {
+      const uint2 x = pl[k];
+      u0 = (x.x & 0xfffffffeu) ^ s0;  // position 0 holds delta_0 := 0
+      u1 = x.y ^ s1;
+    }
+    const uint32_t a = A.a0[k], b = A.a1[k];
+    A.a0[k] = a ^ u0 ^ c0;
+    c0 = (a & u0) | (c0 & (a ^ u0));
+    A.a1[k] = b ^ u1 ^ c1;
+    c1 = (b & u1) | (c1 & (b ^ u1));
+  }
+}
+
+// Adds one block to A: rate r (<= 31, 0 for a constant block or none), block
+// length len (64, fewer for the stream's last block, 0 for no block), outlier
+// O, sign word sg and plane words pl[0 .. r-1]. All 32 lanes of the warp call
+// this together, each with its own block.
+__device__ __forceinline__ void mean_block(int r, int len, int O, uint64_t sg, const uint2* pl,
+                                           MeanAcc& A) {
+  const bool full = (len == L);
+  const int rl = full ? min(r, MeanAcc::RF) : 0;
+  const int rw = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
+  const uint32_t sl = (uint32_t)sg, sh = (uint32_t)(sg >> 32);
+  long long e = (long long)len * O;
+  if (rw > 0) {
+    uint32_t c0 = 0u, c1 = 0u;
+    switch (rw) {
+#define HZ_MEAN_CASE(R) \
+  case R:               \
+    mean_cols<R>(A, pl, rl, sl, sh, c0, c1); \
+    break;
+      HZ_MEAN_CASE(1) HZ_MEAN_CASE(2) HZ_MEAN_CASE(3) HZ_MEAN_CASE(4)
+      HZ_MEAN_CASE(5) HZ_MEAN_CASE(6) HZ_MEAN_CASE(7) HZ_MEAN_CASE(8)
+      HZ_MEAN_CASE(9) HZ_MEAN_CASE(10) HZ_MEAN_CASE(11) HZ_MEAN_CASE(12)
+      HZ_MEAN_CASE(13) HZ_MEAN_CASE(14) HZ_MEAN_CASE(15) HZ_MEAN_CASE(16)
+#undef HZ_MEAN_CASE
+      default:
+        break;
+    }
+    if (c0 | c1) e += wsum64(c0, c1) << rw;  // carry out of the top column: weight 2^rw
+  }
+  if (r > 0 && full) {
+    e -= (long long)((1ull << r) - 1ull) * wsum64(sl, sh);
+    for (int p = MeanAcc::RF; p < r; p++) {
+      const uint2 x = pl[p];
+      e += wsum64((x.x & 0xfffffffeu) ^ sl, x.y ^ sh) << p;
+    }
+  } else if (r > 0 && len > 0) {  // the stream's short last block: weights len - i
+    const uint32_t m0 = (len >= 32 ? 0xffffffffu : ((1u << len) - 1u)) & 0xfffffffeu;
+    const uint32_t m1 = len >= 64 ? 0xffffffffu : (len <= 32 ? 0u : ((1u << (len - 32)) - 1u));
+    for (int p = 0; p < r; p++) {
+      const uint2 x = pl[p];
+      const uint32_t x0 = x.x & m0, x1 = x.y & m1;
+      const long long t = (long long)wsum32(x0, len) + wsum32(x1, len - 32) -
+                          2ll * ((long long)wsum32(x0 & sl, len) + wsum32(x1 & sh, len - 32));
+      e += t << p;
+    }
+  }
+  A.s1 += e;
+}
+
+// Sum of a 128-bit value over the 32 lanes of a warp (lane 0 holds the result).
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const unsigned long long nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+}  // namespace hz
