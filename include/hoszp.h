@@ -176,7 +176,7 @@ int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
  * latency-critical loop that cannot afford the device synchronization a
  * cudaMalloc implies -- and that therefore cannot create a hoszp_ctx. The
  * paper has no counterpart; the result is the same as hoszp_mean's.
- * Scratch: one file-scope device array of about 1.2 MB per device, kept for as
+ * Scratch: one file-scope device array of about 1.4 MB per device, kept for as
  * long as the library is loaded; it bounds the stream to at most 2^28 values
  * (larger streams: status HOSZP_ERR_CAPACITY). The first call on a device looks
  * up the array's device address with that device current; make that first

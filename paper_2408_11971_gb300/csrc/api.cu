@@ -56,7 +56,8 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
   tiles = tiles > c->ws_tiles ? tiles : c->ws_tiles;
   staging_words = staging_words > c->ws_staging_words ? staging_words : c->ws_staging_words;
   staging_words = staging_words < 16 ? 16 : staging_words;
-  // layout: sync | status | totals | eps_q, eps | hdr | desc x3 | partials | range | staging
+  // layout: sync | status | totals | eps_q, eps | hdr | desc x3 | pre x3 | agg | cta_agg |
+  // partials | range | staging
   uint64_t off = 0;
   const uint64_t o_sync = off;
   off += 256;
@@ -80,6 +81,8 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
   }
   const uint64_t o_agg = off;
   off = round_up(off + (tiles + 1) * 8, 256);
+  const uint64_t o_cagg = off;
+  off = round_up(off + grid * sizeof(CtaAgg), 256);
   const uint64_t o_part = off;
   off = round_up(off + grid * sizeof(Partial), 256);
   const uint64_t o_range = off;
@@ -124,6 +127,7 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
   w.opre = (unsigned long long*)(base + o_pre[2]);
   w.agg = (unsigned long long*)(base + o_agg);
   w.partials = (Partial*)(base + o_part);
+  w.cta_agg = (CtaAgg*)(base + o_cagg);
   w.range_part = (float*)(base + o_range);
   w.max_grid = grid;
   w.staging = (uint64_t*)(base + o_stage);

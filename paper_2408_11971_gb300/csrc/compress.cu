@@ -59,14 +59,21 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, uint
     ws.range_part[3 * blockIdx.x + 1] = mx;
     ws.range_part[3 * blockIdx.x + 2] = (float)nonfinite;
   }
-  if (launch_end_is_last(ws) && threadIdx.x == 0) {
+  if (launch_end_is_last(ws) && threadIdx.x < 32) {  // one warp reads all partials at once
     float gmn = FLT_MAX, gmx = -FLT_MAX;
     int nf = 0;
-    for (unsigned int b = 0; b < gridDim.x; b++) {
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32) {
       gmn = fminf(gmn, ws.range_part[3 * b + 0]);
       gmx = fmaxf(gmx, ws.range_part[3 * b + 1]);
       nf |= ws.range_part[3 * b + 2] != 0.0f;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gmn = fminf(gmn, __shfl_xor_sync(0xffffffffu, gmn, o));
+      gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, o));
+      nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+    }
+    if (threadIdx.x != 0) return;
     float eq = 0.0f;
     double eps = 0.0;
     if (nf) {

@@ -194,23 +194,20 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
     ws.partials[blockIdx.x] = p;
   }
   if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && tid == 0) {
-    __int128 S1 = 0;
-    U128 S2 = {0, 0};
-    for (unsigned int b = 0; b < gridDim.x; b++) {
-      const Partial p = ws.partials[b];
-      S1 += ((__int128)p.s1_hi << 64) | (unsigned long long)p.s1_lo;
-      U128 v = {p.s2_lo, p.s2_hi};
-      add_u128(S2, v);
+  if (launch_end_is_last(ws) && w == 0) {
+    __int128 S1;
+    U128 S2;
+    sum_partials_warp(ws.partials, gridDim.x, S1, S2);
+    if (tid == 0) {
+      double res = 0.0;
+      if (h.ok && h.n == 0) {
+        set_status(ws.status, HOSZP_ERR_ARG);
+      } else if (h.ok) {
+        res = moment_finish(S1, S2, h.n, h.eps_q, VAR);
+      }
+      *result = res;
+      launch_reset(ws);
     }
-    double res = 0.0;
-    if (h.ok && h.n == 0) {
-      set_status(ws.status, HOSZP_ERR_ARG);
-    } else if (h.ok) {
-      res = moment_finish(S1, S2, h.n, h.eps_q, VAR);
-    }
-    *result = res;
-    launch_reset(ws);
   }
 }
 
@@ -222,8 +219,8 @@ constexpr int MEAN_GW = STILES;  // warps per group: one per tile of a stage
 constexpr int MEAN_GROUPS = 2;   // groups per CTA
 constexpr int MEAN_NCW = MEAN_GW * MEAN_GROUPS;
 constexpr int MEAN_THREADS = (MEAN_NCW + 1) * 32;  // + loader warp
-constexpr int MEAN_STAGES = 6;
-constexpr uint32_t MEAN_RING = 16384;  // plane-ring words (128 KB)
+constexpr int MEAN_STAGES = 4;
+constexpr uint32_t MEAN_RING = 22528;  // plane-ring words (176 KB)
 constexpr int MEAN_MIN_CTAS = 1;       // resident CTAs per SM (shared memory)
 
 __device__ __forceinline__ void cta_sum_i128_partial(__int128 v, Partial* out, __int128* s_w) {
@@ -244,22 +241,20 @@ __device__ __forceinline__ void cta_sum_i128_partial(__int128 v, Partial* out, _
 }
 
 __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
-    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result,
-    const unsigned long long* __restrict__ pre, Ws ws) {
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   SStage* stages = reinterpret_cast<SStage*>(dyn);
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MEAN_STAGES);
   __shared__ uint64_t full[MEAN_STAGES], empty[MEAN_STAGES];
   __shared__ unsigned long long stage_st[MEAN_STAGES];
+  __shared__ uint32_t s_ts[TS_MAX];
   __shared__ __int128 s_w[MEAN_THREADS / 32];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const Info h = parse_header(c, c_bytes);
-  int bad = 0;
-  uint64_t ntiles = 0;
-  if (!h.ok) bad = HOSZP_ERR_FORMAT;
-  else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
+  const unsigned long long epoch = launch_epoch(ws);
+  int bad = h.ok ? 0 : HOSZP_ERR_FORMAT;
+  const uint64_t ntiles = h.ok ? ntiles_of(h.nb) : 0;
   const uint64_t nst = nsuper_of(ntiles);
-  const uint64_t G = gridDim.x;
   // full: the loader's arrival; empty: the MEAN_GW warps of the group that took the stage
   if (tid == 0) {
     for (int k = 0; k < MEAN_STAGES; k++) {
@@ -268,15 +263,14 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const SRange rg = range_sums(c, h, ntiles, nst, s_ts, ws, epoch, bad);
   __syncthreads();
   MeanAcc A;
   A.init();
   if (w == MEAN_NCW) {
     __shared__ uint32_t s_beg[MEAN_STAGES];
-    __shared__ ulonglong2 s_win[32][STILES + 1];
-    super_loader<MEAN_STAGES, MEAN_RING, MEAN_GROUPS>(
-        stages, ring, s_beg, s_win, full, empty, stage_st, c, h, pre, ntiles, nst, ws.status,
-        [&](uint64_t k) { return blockIdx.x + k * G; });
+    super_loader<MEAN_STAGES, MEAN_RING, MEAN_GROUPS>(stages, ring, s_beg, full, empty, stage_st,
+                                                       c, h, rg, s_ts, ws, epoch);
   } else if (w < MEAN_NCW) {
     const int grp = w / MEAN_GW, ti = w % MEAN_GW;
     const int lastlen = (int)(h.n - (h.nb - 1) * L);
@@ -308,21 +302,23 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
   }
   cta_sum_i128_partial(A.s1, &ws.partials[blockIdx.x], s_w);
   if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && tid == 0) {
-    __int128 S1 = 0;
-    for (unsigned int b = 0; b < gridDim.x; b++) {
-      const Partial p = ws.partials[b];
-      S1 += ((__int128)p.s1_hi << 64) | (unsigned long long)p.s1_lo;
+  if (launch_end_is_last(ws) && w == 0) {
+    __int128 S1;
+    U128 S2;
+    sum_partials_warp(ws.partials, gridDim.x, S1, S2);
+    const bool tot_ok = range_totals_ok(ws, h);
+    if (tid == 0) {
+      double res = 0.0;
+      if (h.ok && !tot_ok) {
+        set_status(ws.status, HOSZP_ERR_FORMAT);
+      } else if (h.ok && h.n == 0) {
+        set_status(ws.status, HOSZP_ERR_ARG);
+      } else if (h.ok) {
+        res = moment_finish(S1, S2, h.n, h.eps_q, false);
+      }
+      *result = res;
+      launch_reset(ws);
     }
-    const U128 S2 = {0, 0};
-    double res = 0.0;
-    if (h.ok && h.n == 0) {
-      set_status(ws.status, HOSZP_ERR_ARG);
-    } else if (h.ok) {
-      res = moment_finish(S1, S2, h.n, h.eps_q, false);
-    }
-    *result = res;
-    launch_reset(ws);
   }
 }
 
@@ -343,17 +339,22 @@ static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t
 
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
                            bool variance, Ws ws) {
-  cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
-  if (e != cudaSuccess) return e;
-  if (variance) return launch_moments_t<true>(lc, c, c_bytes, result, ws);
+  if (variance) {
+    cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
+    if (e != cudaSuccess) return e;
+    return launch_moments_t<true>(lc, c, c_bytes, result, ws);
+  }
+  // the mean kernel finds the rate prefix itself (range_sums): no pre-scan
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_mean<<<persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem), MEAN_THREADS, smem,
-           lc.stream>>>(c, c_bytes, result, ws.pre[0], ws);
+  const uint64_t nb_bound = c_bytes > HOSZP_HEADER_BYTES ? (c_bytes - HOSZP_HEADER_BYTES) / 5 + 1 : 1;
+  int grid = range_grid(persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem), ntiles_of(nb_bound));
+  if ((uint64_t)grid > ws.max_grid) grid = (int)ws.max_grid;  // then the kernel reports CAPACITY
+  k_mean<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
   return cudaGetLastError();
 }
 

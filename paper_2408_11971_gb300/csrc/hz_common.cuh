@@ -112,6 +112,13 @@ struct Sync {
   unsigned long long epoch;
 };
 
+// Per-CTA record of the in-kernel rate prefix: the CTA's (non-constant
+// blocks, rate sum) over its range of the stream, published under `flag` =
+// (epoch << 1) | 1 of the launch.
+struct CtaAgg {
+  unsigned long long flag, nc, r, pad;
+};
+
 struct Partial {  // per-CTA exact sums for the reductions
   long long s1_lo, s1_hi;
   unsigned long long s2_lo, s2_hi;
@@ -127,6 +134,7 @@ struct Ws {
   Desc* desc[NCHAIN];
   uint64_t max_tiles;
   Partial* partials;
+  CtaAgg* cta_agg;     // max_grid records (in-kernel rate prefix)
   float* range_part;  // per-CTA min, max (2 floats) + nonfinite flag as float
   uint64_t max_grid;
   uint64_t* staging;  // plane words of a produced stream before placement

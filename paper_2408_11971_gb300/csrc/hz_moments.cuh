@@ -181,18 +181,21 @@ __device__ __forceinline__ void mean_block(int r, int len, int O, uint64_t sg, c
   A.s1 += e;
 }
 
-// Sum of a 128-bit value over the 32 lanes of a warp (lane 0 holds the result).
-__device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
-  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
-    const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
-    const unsigned long long nl = lo + l2;
-    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
-    lo = nl;
+// Last CTA of a reduction launch, one whole warp: the exact sums of the
+// per-CTA partials (lane 0 holds them), read by all lanes at once.
+__device__ __forceinline__ void sum_partials_warp(const Partial* P, unsigned int G, __int128& S1,
+                                                  U128& S2) {
+  const int lane = threadIdx.x & 31;
+  __int128 a = 0;
+  U128 b = {0, 0};
+  for (unsigned int u = lane; u < G; u += 32) {
+    const Partial p = P[u];
+    a += ((__int128)p.s1_hi << 64) | (unsigned long long)p.s1_lo;
+    const U128 v = {p.s2_lo, p.s2_hi};
+    add_u128(b, v);
   }
-  return (__int128)(((unsigned __int128)hi << 64) | lo);
+  S1 = warp_sum_i128(a);
+  S2 = warp_sum_u128(b);
 }
 
 }  // namespace hz

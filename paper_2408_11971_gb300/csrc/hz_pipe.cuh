@@ -150,7 +150,12 @@ __device__ __forceinline__ void issue_in_tile(InStage* s, uint64_t* bar, const u
 // state (identical in every lane).
 template <int S, uint32_t RW>
 struct PlaneRing {
-  static_assert((RW & (RW - 1)) == 0 && RW >= TILE_PLANE_WORDS_MAX + 2, "ring size");
+  static_assert(RW % 2 == 0 && RW >= TILE_PLANE_WORDS_MAX + 2, "ring size");
+  // word index of a position (positions only grow and stay below 2^32 per launch)
+  static __device__ __forceinline__ uint32_t wrap(uint32_t p) {
+    if constexpr ((RW & (RW - 1)) == 0) return p & (RW - 1);
+    else return p % RW;
+  }
   uint64_t* ring;  // shared, RW words, 16-byte aligned
   uint32_t* beg;   // shared, S entries
   uint32_t head;   // next free position (even)
@@ -167,7 +172,7 @@ struct PlaneRing {
   __device__ __forceinline__ uint32_t reserve(uint32_t k, uint32_t words, const uint32_t& k_rel,
                                               ReleaseOne&& release_one) const {
     uint32_t p0 = head;
-    if ((p0 & (RW - 1)) + words > RW) p0 += RW - (p0 & (RW - 1));
+    if (wrap(p0) + words > RW) p0 += RW - wrap(p0);
     for (;;) {
       const uint32_t tail = (k_rel < k) ? beg[k_rel % S] : p0;
       if (p0 + words - tail <= RW) return p0;
@@ -179,7 +184,7 @@ struct PlaneRing {
     if ((threadIdx.x & 31) == 0) beg[k % S] = p0;
     __syncwarp();
     head = p0 + words;
-    return p0 & (RW - 1);
+    return wrap(p0);
   }
 };
 

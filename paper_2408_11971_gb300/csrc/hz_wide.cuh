@@ -55,6 +55,30 @@ __device__ __forceinline__ double u256_to_double(const U256& a) {
   return d;
 }
 
+// Sum of a signed 128-bit value over the 32 lanes of a warp (lane 0 holds it).
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const unsigned long long nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U128 t;
+    t.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    t.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    add_u128(v, t);
+  }
+  return v;
+}
+
 // mean = (S1 / n) * 2 eps_q ; variance = (2 eps_q)^2 (n S2 - S1^2) / n^2, the
 // numerator exact in 256-bit integers (n S2 >= S1^2 by Cauchy-Schwarz).
 __device__ __forceinline__ double moment_finish(__int128 S1, const U128& S2, uint64_t n,

@@ -6,8 +6,8 @@
 // while it runs, and latency-critical loops that cannot afford the implicit
 // device synchronization of a cudaMalloc. Such callers cannot create a
 // hoszp_ctx (its workspace is a device allocation), so this entry point keeps
-// its scratch -- launch counters, status word, the rate pre-scan's per-tile
-// prefixes, its look-back descriptors and the per-CTA partial sums -- in one
+// its scratch -- launch counters, status word, the per-CTA rate aggregates,
+// the per-CTA partial sums and room for a rate pre-scan -- in one
 // file-scope array that exists for as long as the library is loaded on a
 // device. It runs the same rate pre-scan and reduction kernels as hoszp_mean.
 #include <mutex>
@@ -27,7 +27,8 @@ constexpr uint64_t NA_OFF_STATUS = 64;
 constexpr uint64_t NA_OFF_TOTALS = 128;
 constexpr uint64_t NA_OFF_DESC = 256;
 constexpr uint64_t NA_OFF_PRE = NA_OFF_DESC + NA_MAX_SUPER * sizeof(Desc);
-constexpr uint64_t NA_OFF_PART = NA_OFF_PRE + 2 * (NA_MAX_TILES + 1) * 8;
+constexpr uint64_t NA_OFF_CAGG = NA_OFF_PRE + 2 * (NA_MAX_TILES + 1) * 8;
+constexpr uint64_t NA_OFF_PART = NA_OFF_CAGG + NA_MAX_GRID * sizeof(CtaAgg);
 constexpr uint64_t NA_BYTES = NA_OFF_PART + NA_MAX_GRID * sizeof(Partial);
 
 // The scratch: zero at load (look-back flags 0 never match a published state;
@@ -97,6 +98,7 @@ extern "C" int hoszp_mean_noalloc(const void* d_c, size_t c_bytes, double* d_res
   for (int k = 0; k < NCHAIN; k++) w.desc[k] = reinterpret_cast<Desc*>(base + NA_OFF_DESC);
   w.max_tiles = NA_MAX_TILES;
   w.partials = reinterpret_cast<Partial*>(base + NA_OFF_PART);
+  w.cta_agg = reinterpret_cast<CtaAgg*>(base + NA_OFF_CAGG);
   w.max_grid = NA_MAX_GRID;
   w.pre[0] = w.pre[1] = reinterpret_cast<unsigned long long*>(base + NA_OFF_PRE);
   const cudaStream_t s = (cudaStream_t)stream;
