@@ -236,6 +236,98 @@ int hoszp_batch_add_scalar(hoszp_batch* b, double s, hoszp_stream_t stream);
 int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
 int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of operator requests over resident streams.
+ *
+ * Analysis queries arrive as a stream of mixed operators over compressed fields
+ * that stay resident on the device. A server owns `slots` execution slots (each
+ * a context and a CUDA stream of its own, so the work of different requests
+ * overlaps on the device) and an arena of device memory for the requests'
+ * outputs. A scheduling thread of the library admits requests in arrival order
+ * as soon as a slot is free and the arena can hold the request's output
+ * (reductions need none and may pass a request that waits for memory), launches
+ * them, and reports each completion with its latency. Every result is exactly
+ * the one the same call gives alone (the operators are deterministic). The
+ * paper has no serving form; the operators are those of Sec. V.
+ *
+ * Memory: hbm_budget_bytes bounds everything the server allocates -- the slot
+ * workspaces (sized for streams of up to max_n values) and the output arena,
+ * which gets the rest; creation fails with HOSZP_ERR_CAPACITY if nothing is
+ * left for outputs. Output bounds used for admission: negate / add_scalar: the
+ * input's size; mul_scalar: the input's size plus 8 bytes per block and bit of
+ * rate growth; add / sub: the two inputs' sizes; decompress: 4 n. After a
+ * request completes, the unused tail of its block returns to the arena.
+ * Outputs are server memory: the caller reads them, then hands them back with
+ * hoszp_server_release(). Requests on one server must name registered streams;
+ * registered streams must stay resident and unmodified while requests use them.
+ * Times are microseconds on the server's clock (hoszp_server_now_us).
+ * --------------------------------------------------------------------------- */
+typedef enum {
+  HOSZP_OP_MEAN = 0,
+  HOSZP_OP_VAR = 1,
+  HOSZP_OP_NEGATE = 2,
+  HOSZP_OP_ADD_SCALAR = 3,
+  HOSZP_OP_MUL_SCALAR = 4,
+  HOSZP_OP_ADD = 5,
+  HOSZP_OP_SUB = 6,
+  HOSZP_OP_DECOMPRESS = 7
+} hoszp_op;
+
+typedef struct hoszp_request {
+  uint64_t tag;        /* the caller's id, returned with the completion */
+  int32_t op;          /* hoszp_op */
+  uint32_t a, b;       /* registered stream ids (b: ADD and SUB only) */
+  double scalar;       /* ADD_SCALAR, MUL_SCALAR */
+  uint64_t arrival_us; /* when the request arrives (0: at submission) */
+} hoszp_request;
+
+typedef struct hoszp_completion {
+  uint64_t tag;
+  int32_t op;
+  int32_t status;      /* HOSZP_OK, or the request's host or device error */
+  double value;        /* MEAN, VAR */
+  void* d_out;         /* output stream or floats (NULL for reductions and errors) */
+  uint64_t out_bytes;  /* bytes of d_out */
+  uint64_t arrival_us, start_us, done_us; /* arrival, launch, completion seen by the server */
+} hoszp_completion;
+
+typedef struct hoszp_server_stats {
+  uint64_t submitted, completed, pending, in_flight;
+  uint64_t arena_bytes, arena_in_use, arena_peak;  /* output arena (bytes) */
+  uint64_t workspace_bytes;                        /* slot workspaces and scratch */
+  uint64_t max_in_flight;                          /* most requests on the device at once */
+} hoszp_server_stats;
+
+typedef struct hoszp_server hoszp_server;
+
+/* Create a server on `device` with `slots` (1..64) execution slots, an HBM
+ * budget in bytes and the largest stream (in values) any request will name.
+ * sms_per_request limits the SMs one request's kernels spread over (0: all),
+ * so that requests in different slots can run side by side. Starts the
+ * scheduling thread. Errors: ARG, CAPACITY (budget too small), CUDA. */
+int hoszp_server_create(int device, uint32_t slots, uint64_t hbm_budget_bytes, uint64_t max_n,
+                        uint32_t sms_per_request, hoszp_server** out);
+/* Stop admitting, wait for requests on the device, free everything (outputs
+ * not yet released included). NULL is a no-op. */
+void hoszp_server_destroy(hoszp_server* s);
+/* Register a resident stream (device pointer, 16-byte aligned, and its size);
+ * reads its header once (synchronous). *id names it in requests. Errors: ARG,
+ * FORMAT (bad header), CAPACITY (more values than max_n). */
+int hoszp_server_register(hoszp_server* s, const void* d_stream, size_t bytes, uint32_t* id);
+/* Queue a request; thread-safe, never waits for the device. Requests are
+ * considered in submission order, so arrival_us must not decrease. ARG on an
+ * unknown op or stream id (nothing queued). */
+int hoszp_server_submit(hoszp_server* s, const hoszp_request* r);
+/* Move up to `max` completions (in completion order) into out[]; *count gets
+ * how many. Waits up to wait_us microseconds for the first one. */
+int hoszp_server_poll(hoszp_server* s, hoszp_completion* out, uint32_t max, uint32_t* count,
+                      uint64_t wait_us);
+/* Hand an output (a completion's d_out) back to the arena. ARG if unknown. */
+int hoszp_server_release(hoszp_server* s, void* d_out);
+/* Current time on the server's clock, microseconds since creation. */
+uint64_t hoszp_server_now_us(const hoszp_server* s);
+int hoszp_server_get_stats(hoszp_server* s, hoszp_server_stats* st);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     HoszpError,
     Context,
     Batch,
+    Server,
     STATUS,
     lib_path,
     load_library,
@@ -38,7 +39,7 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
-    "HoszpError", "Context", "Batch", "STATUS", "lib_path", "load_library", "default_context",
+    "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library", "default_context",
     "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add", "sub",
     "mean", "var", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

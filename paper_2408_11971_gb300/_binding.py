@@ -27,6 +27,25 @@ _lib = None
 _lock = threading.Lock()
 
 
+class _Request(ctypes.Structure):  # hoszp_request
+    _fields_ = [("tag", ctypes.c_uint64), ("op", ctypes.c_int32), ("a", ctypes.c_uint32),
+                ("b", ctypes.c_uint32), ("scalar", ctypes.c_double),
+                ("arrival_us", ctypes.c_uint64)]
+
+
+class _Completion(ctypes.Structure):  # hoszp_completion
+    _fields_ = [("tag", ctypes.c_uint64), ("op", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("value", ctypes.c_double), ("d_out", ctypes.c_void_p),
+                ("out_bytes", ctypes.c_uint64), ("arrival_us", ctypes.c_uint64),
+                ("start_us", ctypes.c_uint64), ("done_us", ctypes.c_uint64)]
+
+
+class _ServerStats(ctypes.Structure):  # hoszp_server_stats
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "completed", "pending", "in_flight", "arena_bytes", "arena_in_use",
+        "arena_peak", "workspace_bytes", "max_in_flight")]
+
+
 def lib_path() -> str:
     return _LIB_PATH
 
@@ -69,6 +88,16 @@ def load_library():
             "hoszp_batch_add_scalar": (I, [P, D, P]),
             "hoszp_batch_tune": (I, [P, P, P]),
             "hoszp_batch_config": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "hoszp_server_create": (I, [I, ctypes.c_uint32, U64, U64, ctypes.c_uint32,
+                                        ctypes.POINTER(P)]),
+            "hoszp_server_destroy": (None, [P]),
+            "hoszp_server_register": (I, [P, P, SZ, ctypes.POINTER(ctypes.c_uint32)]),
+            "hoszp_server_submit": (I, [P, ctypes.POINTER(_Request)]),
+            "hoszp_server_poll": (I, [P, ctypes.POINTER(_Completion), ctypes.c_uint32,
+                                      ctypes.POINTER(ctypes.c_uint32), U64]),
+            "hoszp_server_release": (I, [P, P]),
+            "hoszp_server_now_us": (U64, [P]),
+            "hoszp_server_get_stats": (I, [P, ctypes.POINTER(_ServerStats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -456,3 +485,93 @@ class Batch:
                                             ctypes.byref(cps)), "batch_config")
         return {"stages": st.value, "ctas_per_sm": cps.value}
 
+
+
+class _DevBuf:
+    """A device buffer exposed through the CUDA array interface (no copy)."""
+
+    def __init__(self, ptr: int, nbytes: int, typestr: str, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+class Server:
+    """Continuous-batching server over resident streams (hoszp_server_*).
+
+    register() the resident streams, submit() requests (optionally with an
+    arrival time on the server's clock), poll() completions. An output stays
+    in the server's arena until release(); output() views it as a tensor."""
+
+    OPS = {"mean": 0, "var": 1, "negate": 2, "add_scalar": 3, "mul_scalar": 4, "add": 5,
+           "sub": 6, "decompress": 7}
+    OP_NAMES = {v: k for k, v in OPS.items()}
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 8 << 30,
+                 max_n: int = 1 << 27, sms_per_request: int = 0):
+        self._lib = load_library()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _check(self._lib.hoszp_server_create(self.device, int(slots), int(hbm_budget), int(max_n),
+                                             int(sms_per_request), ctypes.byref(h)),
+               "server_create")
+        self.handle = h
+        self._streams = []
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.hoszp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, c) -> int:
+        c = _stream_tensor(c)
+        _torch().cuda.synchronize(c.device)
+        sid = ctypes.c_uint32(0)
+        _check(self._lib.hoszp_server_register(self.handle, _dev_ptr(c), c.numel(),
+                                               ctypes.byref(sid)), "server_register")
+        self._streams.append(c)  # keeps the stream alive while the server may read it
+        return sid.value
+
+    def submit(self, op, a: int, b: int = 0, scalar: float = 0.0, tag: int = 0,
+               arrival_us: int = 0):
+        r = _Request(int(tag), self.OPS[op] if isinstance(op, str) else int(op), int(a), int(b),
+                     float(scalar), int(arrival_us))
+        _check(self._lib.hoszp_server_submit(self.handle, ctypes.byref(r)), "server_submit")
+
+    def poll(self, max_n: int = 256, wait_us: int = 0):
+        buf = (_Completion * max_n)()
+        n = ctypes.c_uint32(0)
+        _check(self._lib.hoszp_server_poll(self.handle, buf, max_n, ctypes.byref(n), int(wait_us)),
+               "server_poll")
+        return [{k: getattr(buf[i], k) for k, _ in _Completion._fields_} for i in range(n.value)]
+
+    def output(self, comp):
+        """The completion's output as a CUDA tensor view (uint8 stream or float32 values)."""
+        torch = _torch()
+        if not comp["d_out"]:
+            return None
+        if comp["op"] == self.OPS["decompress"]:
+            v = _DevBuf(comp["d_out"], comp["out_bytes"], "<f4", comp["out_bytes"] // 4)
+        else:
+            v = _DevBuf(comp["d_out"], comp["out_bytes"], "|u1", comp["out_bytes"])
+        return torch.as_tensor(v, device=torch.device("cuda", self.device))
+
+    def release(self, comp_or_ptr):
+        ptr = comp_or_ptr["d_out"] if isinstance(comp_or_ptr, dict) else comp_or_ptr
+        if ptr:
+            _check(self._lib.hoszp_server_release(self.handle, ctypes.c_void_p(ptr)),
+                   "server_release")
+
+    def now_us(self) -> int:
+        return int(self._lib.hoszp_server_now_us(self.handle))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(self._lib.hoszp_server_get_stats(self.handle, ctypes.byref(st)), "server_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}

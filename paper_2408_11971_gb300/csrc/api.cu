@@ -395,6 +395,20 @@ int ctx_prepare(hoszp_ctx* ctx, uint64_t tiles, Ws* ws, int* device, int* num_sm
   return HOSZP_OK;
 }
 
+// Serving (serve.cu): the context's device status word, its workspace size,
+// and a cap on the SMs its persistent grids spread over (0 restores all).
+int* ctx_status_word(hoszp_ctx* ctx) { return ctx ? ctx->ws.status : nullptr; }
+size_t ctx_workspace_bytes(const hoszp_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+void ctx_limit_sms(hoszp_ctx* ctx, int sms) {
+  if (!ctx) return;
+  int all = 0;
+  if (cudaDeviceGetAttribute(&all, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  ctx->num_sms = (sms > 0 && sms < all) ? sms : all;
+}
+
 // Workspace access for the traditional-workflow helpers (baseline.cu); the
 // grid they use (SMs x 4) stays within the partials the workspace holds.
 Ws ctx_workspace(hoszp_ctx* ctx) {
