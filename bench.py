@@ -223,6 +223,79 @@ def profile_op(op: str, shape):
     print(f"profile-op {op} done: stream {ca.numel()} bytes")
 
 
+# ---------------------------------------------------------------- serving
+SERVE_MIX = (("mean", 0.20), ("var", 0.20), ("add_scalar", 0.15), ("mul_scalar", 0.15),
+             ("add", 0.20), ("decompress", 0.10))
+
+
+def serving_bench(hz, xa, xb, eps_q, nfields: int, budget: int, rates, per_rate: int,
+                  slots: int, seed: int = 7):
+    """Poisson streams of mixed requests over `nfields` resident compressed
+    fields of the workload's size (seeded rolls, scales and offsets of fields A
+    and B, all at A's absolute bound so any two can be added), served by
+    hoszp_server under an HBM budget that covers the resident streams too.
+    Returns p50 / p99 latency (arrival to completion) and throughput per rate."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    n = xa.numel()
+    cap = hz.compress_bound(n)
+    buf = torch.empty(cap, dtype=torch.uint8, device=xa.device)
+    size = torch.zeros(1, dtype=torch.int64, device=xa.device)
+    tmp = torch.empty_like(xa)
+    streams = []
+    for k in range(nfields):
+        base = xa if k % 2 == 0 else xb
+        r = int(rng.integers(1, n))
+        tmp[: n - r].copy_(base[r:])
+        tmp[n - r:].copy_(base[:r])
+        tmp.mul_(float(rng.uniform(0.5, 2.0))).add_(float(rng.uniform(-1.0, 1.0)))
+        hz.compress(tmp, eb=eps_q, out=buf, out_bytes=size, sync=False)
+        streams.append(buf[: int(size.item())].clone())
+    del buf, tmp
+    torch.cuda.synchronize()
+    resident = sum(c.numel() for c in streams)
+    srv = hz.Server(xa.device.index, slots=slots, hbm_budget=budget - resident, max_n=n)
+    ids = [srv.register(c) for c in streams]
+    names = [m for m, _ in SERVE_MIX]
+    probs = np.array([p for _, p in SERVE_MIX])
+    out = {"fields": nfields, "resident_gib": resident / 2**30, "budget_gib": budget / 2**30,
+           "slots": slots, "mix": dict(SERVE_MIX), "requests_per_rate": per_rate, "rates": []}
+    for rate in rates:
+        ops = rng.choice(len(names), size=per_rate, p=probs)
+        gaps = rng.exponential(1e6 / rate, per_rate)
+        t0 = srv.now_us() + 5000
+        arr = t0 + np.cumsum(gaps).astype(np.int64)
+        orig = 0
+        for i in range(per_rate):
+            op = names[ops[i]]
+            a, b = int(rng.integers(nfields)), int(rng.integers(nfields))
+            orig += (2 if op == "add" else 1) * 4 * n
+            srv.submit(op, ids[a], ids[b], 0.5 if op == "add_scalar" else 3.14, tag=i,
+                       arrival_us=int(arr[i]))
+        lat, done_t, errs = [], [], 0
+        deadline = time.time() + 120
+        while len(lat) < per_rate and time.time() < deadline:
+            for c in srv.poll(256, wait_us=20000):
+                if c["status"] != 0:
+                    errs += 1
+                srv.release(c)
+                lat.append((c["done_us"] - c["arrival_us"]) / 1e3)
+                done_t.append(c["done_us"])
+        span_s = (max(done_t) - t0) / 1e6 if done_t else float("nan")
+        out["rates"].append({"offered_req_s": rate, "completed": len(lat), "errors": errs,
+                             "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+                             "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+                             "served_req_s": len(lat) / span_s, "orig_gbs": orig / span_s / 1e9})
+    st = srv.stats()
+    out["max_in_flight"] = st["max_in_flight"]
+    out["arena_peak_gib"] = st["arena_peak"] / 2**30
+    srv.close()
+    del streams
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -233,6 +306,9 @@ def main():
     ap.add_argument("--oracle-sample", type=int, default=1 << 24,
                     help="values per field in the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-fields", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered rate")
     ap.add_argument("--shape", type=int, nargs=3, default=list(DEFAULT_SHAPE),
                     help="field shape (smaller cases are for profiling, not bench lines)")
     ap.add_argument("--profile-op", default=None,
@@ -494,6 +570,13 @@ def main():
             dist.destroy_process_group()
         return
 
+    serving = None
+    if world == 1 and not args.no_serving:
+        del tmp1, tmp2, tmp3, outb
+        torch.cuda.empty_cache()
+        serving = serving_bench(hz, xa, xb, eps_q, args.serve_fields, 120 << 30,
+                                (200, 2000, 5000, 10000, 20000), args.serve_requests, slots=8)
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         a, b = sample_fields(A, B, args.oracle_sample)
@@ -508,7 +591,8 @@ def main():
             "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": config,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
-            "compressed_bytes": C, "per_op": per_op, "decompress_op_recompress": base}
+            "compressed_bytes": C, "per_op": per_op, "decompress_op_recompress": base,
+            "serving": serving}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
