@@ -522,7 +522,7 @@ def main():
     dom = max(ops, key=lambda o: per_op_ms[o])
     kern_of = {"compress A": "k_compress", "compress B": "k_compress", "negate": "k_meta",
                "add_scalar": "k_meta", "mul_scalar": "k_mul_scalar", "add": "k_add",
-               "mean": "k_mean", "var": "k_moments", "decompress": "k_decompress"}
+               "mean": "k_mean", "var": "k_var", "decompress": "k_decompress"}
     achieved = alg[dom] / per_op_ms[dom] / 1e6
     tr = ncu_traffic(dom)
     roofline = {"bound": "hbm", "op": dom, "kernel": kern_of[dom], "achieved": achieved,

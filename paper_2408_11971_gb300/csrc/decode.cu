@@ -322,6 +322,154 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
   }
 }
 
+// Variance over the same super-tile pipeline: warp i of a group takes tile i
+// of the stage and decodes it 4 blocks at a time (8 lanes per block, octet
+// layout of hz_decode.cuh) to the quantized integers, summing q and q^2.
+__global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result, Ws ws) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  SStage* stages = reinterpret_cast<SStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MEAN_STAGES);
+  __shared__ uint64_t full[MEAN_STAGES], empty[MEAN_STAGES];
+  __shared__ unsigned long long stage_st[MEAN_STAGES];
+  __shared__ uint32_t s_ts[TS_MAX];
+  __shared__ long long s_s1[MEAN_THREADS / 32];
+  __shared__ U128 s_s2[MEAN_THREADS / 32];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const Info h = parse_header(c, c_bytes);
+  const unsigned long long epoch = launch_epoch(ws);
+  int bad = h.ok ? 0 : HOSZP_ERR_FORMAT;
+  const uint64_t ntiles = h.ok ? ntiles_of(h.nb) : 0;
+  const uint64_t nst = nsuper_of(ntiles);
+  if (tid == 0) {
+    for (int k = 0; k < MEAN_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], MEAN_GW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const SRange rg = range_sums(c, h, ntiles, nst, s_ts, ws, epoch, bad);
+  __syncthreads();
+  long long s1 = 0;  // per thread: |q| <= 2^30, far fewer than 2^32 values per thread
+  U128 s2 = {0, 0};
+  if (w == MEAN_NCW) {
+    __shared__ uint32_t s_beg[MEAN_STAGES];
+    super_loader<MEAN_STAGES, MEAN_RING, MEAN_GROUPS>(stages, ring, s_beg, full, empty, stage_st,
+                                                       c, h, rg, s_ts, ws, epoch);
+  } else if (w < MEAN_NCW) {
+    const int grp = w / MEAN_GW, ti = w % MEAN_GW;
+    const int j = lane & 7, gq = lane >> 3;
+    const OctetSel S = octet_sel(j);
+    const int lastlen = (int)(h.n - (h.nb - 1) * L);
+    const bool small = h.qbound < (1u << 13);  // the header bounds every |q|
+    for (uint64_t k = 0;; k++) {
+      const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
+      const int sk = (int)(u % MEAN_STAGES);
+      mbar_wait(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status);
+      const unsigned long long s = stage_st[sk];
+      if (s == ~0ull) break;
+      const SStage& sg = stages[sk];
+      const uint64_t tile = (uint64_t)STILES * s + ti;
+      const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+      const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
+      const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
+      const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
+      for (int it = 0; it < steps; it++) {
+        const int b = 4 * it + gq;
+        uint32_t r, ex;
+        tile_block(tr, b, r, ex);
+        BlockRef br;
+        br.rate = (int)r;
+        br.outlier = sg.outlier[TILE * ti + b];
+        br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+        br.planes = pls + (ex & 0xffffu);
+        br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
+        const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+        int d[8], q[8];
+        octet_deltas(br, kmax, j, S, d);
+        octet_values(br, d, j, q);
+        long long a = 0;
+        unsigned long long b2 = 0;  // 8 squares of |q| <= 2^30 stay below 2^63
+        if (small && br.len == L) {  // |q| < 2^13: 8 squares fit 32 bits
+          int a32 = 0;
+          uint32_t b32 = 0;
+#pragma unroll
+          for (int t = 0; t < 8; t++) {
+            a32 += q[t];
+            b32 += (uint32_t)(q[t] * q[t]);
+          }
+          a = a32;
+          b2 = b32;
+        } else if (br.len == L) {
+#pragma unroll
+          for (int t = 0; t < 8; t++) {
+            a += q[t];
+            b2 += (unsigned long long)((long long)q[t] * q[t]);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; t++) {
+            const int qq = (8 * j + t < br.len) ? q[t] : 0;
+            a += qq;
+            b2 += (unsigned long long)((long long)qq * qq);
+          }
+        }
+        s1 += a;
+        add_u64(s2, b2);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+  }
+  // CTA reduction -> per-CTA partial
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    U128 t;
+    t.lo = __shfl_xor_sync(0xffffffffu, s2.lo, o);
+    t.hi = __shfl_xor_sync(0xffffffffu, s2.hi, o);
+    add_u128(s2, t);
+  }
+  if (lane == 0) {
+    s_s1[w] = s1;
+    s_s2[w] = s2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __int128 t1 = 0;
+    U128 t2 = {0, 0};
+    for (int k = 0; k < MEAN_THREADS / 32; k++) {
+      t1 += s_s1[k];
+      add_u128(t2, s_s2[k]);
+    }
+    Partial p;
+    p.s1_lo = (long long)(unsigned long long)t1;
+    p.s1_hi = (long long)(t1 >> 64);
+    p.s2_lo = t2.lo;
+    p.s2_hi = t2.hi;
+    ws.partials[blockIdx.x] = p;
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && w == 0) {
+    __int128 S1;
+    U128 S2;
+    sum_partials_warp(ws.partials, gridDim.x, S1, S2);
+    const bool tot_ok = range_totals_ok(ws, h);
+    if (tid == 0) {
+      double res = 0.0;
+      if (h.ok && !tot_ok) {
+        set_status(ws.status, HOSZP_ERR_FORMAT);
+      } else if (h.ok && h.n == 0) {
+        set_status(ws.status, HOSZP_ERR_ARG);
+      } else if (h.ok) {
+        res = moment_finish(S1, S2, h.n, h.eps_q, true);
+      }
+      *result = res;
+      launch_reset(ws);
+    }
+  }
+}
+
 template <bool VAR>
 static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                                     double* result, Ws ws) {
@@ -339,22 +487,23 @@ static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t
 
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
                            bool variance, Ws ws) {
-  if (variance) {
-    cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
-    if (e != cudaSuccess) return e;
-    return launch_moments_t<true>(lc, c, c_bytes, result, ws);
-  }
-  // the mean kernel finds the rate prefix itself (range_sums): no pre-scan
+  // both kernels find the rate prefix themselves (range_sums): no pre-scan
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_var, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   const uint64_t nb_bound = c_bytes > HOSZP_HEADER_BYTES ? (c_bytes - HOSZP_HEADER_BYTES) / 5 + 1 : 1;
-  int grid = range_grid(persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem), ntiles_of(nb_bound));
+  const int per = variance ? persistent_grid(k_var, MEAN_THREADS, lc.grid, smem)
+                           : persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem);
+  int grid = range_grid(per, ntiles_of(nb_bound));
   if ((uint64_t)grid > ws.max_grid) grid = (int)ws.max_grid;  // then the kernel reports CAPACITY
-  k_mean<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
+  if (variance)
+    k_var<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
+  else
+    k_mean<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
   return cudaGetLastError();
 }
 
