@@ -170,6 +170,16 @@ int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result
 int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
               hoszp_stream_t stream);
 
+/* The exact integer sums behind mean and variance (Sec. V-B), for combining
+ * shards of one field held by several devices or processes: d_sums (device,
+ * 5 words) gets S1 = sum of q as a 128-bit two's complement integer (words 0
+ * low, 1 high), S2 = sum of q^2 as a 128-bit unsigned integer (words 2, 3) and
+ * n (word 4). Shards of one field (whole blocks each, the same eps_q) combine
+ * by adding the sums; mean = (S1 / n) 2 eps_q and the population variance
+ * (2 eps_q)^2 (n S2 - S1^2) / n^2 then follow exactly as for one stream. */
+int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums,
+               hoszp_stream_t stream);
+
 /* Mean of a stream without allocating: for callers that may not allocate
  * device memory when they call -- e.g. code whose device memory is owned by a
  * host framework's pool that forbids driver allocations while it runs, or a

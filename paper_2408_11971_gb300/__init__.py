@@ -32,6 +32,7 @@ from ._binding import (  # noqa: F401
     sub,
     mean,
     var,
+    sums,
     header,
     fop_axpb,
     fop_add,
@@ -41,5 +42,5 @@ from ._binding import (  # noqa: F401
 __all__ = [
     "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library", "default_context",
     "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add", "sub",
-    "mean", "var", "header", "fop_axpb", "fop_add", "fop_moments",
+    "mean", "var", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

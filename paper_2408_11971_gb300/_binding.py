@@ -77,6 +77,7 @@ def load_library():
             "hoszp_add": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_sub": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
+            "hoszp_sums": (I, [P, P, SZ, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
             "hoszp_batch_create": (I, [P, ctypes.c_uint32, P, P, ctypes.POINTER(P)]),
             "hoszp_batch_destroy": (None, [P]),
@@ -343,6 +344,19 @@ def _moment(fn, what, c, out, stream, ctx, sync, check):
     if check:
         ctx.check(what)
     return float(out.item())
+
+
+def sums(c, stream=None, ctx=None):
+    """The stream's exact sums as the five words of hoszp_sums (S1 low/high,
+    S2 low/high, n), read back to the host."""
+    torch = _torch()
+    c = _stream_tensor(c)
+    ctx = _ctx(ctx, c)
+    w = torch.zeros(5, dtype=torch.int64, device=c.device)
+    _check(load_library().hoszp_sums(ctx.handle, _dev_ptr(c), c.numel(), _dev_ptr(w),
+                                     _stream_ptr(stream)), "sums")
+    ctx.check("sums")
+    return [int(v) & ((1 << 64) - 1) for v in w.cpu().tolist()]
 
 
 def mean(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):

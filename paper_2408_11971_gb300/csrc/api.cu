@@ -369,6 +369,17 @@ static int moments(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_re
       launch_moments(lc_of(ctx, stream), (const uint8_t*)d_c, c_bytes, d_result, var, ctx->ws));
 }
 
+int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums,
+               hoszp_stream_t stream) {
+  if (!ctx || !d_c || !d_sums || c_bytes < HOSZP_HEADER_BYTES) return HOSZP_ERR_ARG;
+  if (!aligned16(d_c) || !aligned8(d_sums)) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = ensure_ws(ctx, tiles_from_bytes(c_bytes), 16);
+  if (rc) return rc;
+  return cuda_rc(launch_moments(lc_of(ctx, stream), (const uint8_t*)d_c, c_bytes, nullptr, false,
+                                ctx->ws, reinterpret_cast<unsigned long long*>(d_sums)));
+}
+
 int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
                hoszp_stream_t stream) {
   return moments(ctx, d_c, c_bytes, d_result, stream, false);

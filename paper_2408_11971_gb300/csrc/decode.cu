@@ -326,7 +326,8 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
 // of the stage and decodes it 4 blocks at a time (8 lanes per block, octet
 // layout of hz_decode.cuh) to the quantized integers, summing q and q^2.
 __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
-    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result, Ws ws) {
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result, unsigned long long* sums,
+    Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   SStage* stages = reinterpret_cast<SStage*>(dyn);
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MEAN_STAGES);
@@ -464,7 +465,14 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
       } else if (h.ok) {
         res = moment_finish(S1, S2, h.n, h.eps_q, true);
       }
-      *result = res;
+      if (result) *result = res;
+      if (sums) {  // the exact sums themselves (for combining shards)
+        sums[0] = (unsigned long long)S1;
+        sums[1] = (unsigned long long)((unsigned __int128)S1 >> 64);
+        sums[2] = S2.lo;
+        sums[3] = S2.hi;
+        sums[4] = h.ok ? h.n : 0ull;
+      }
       launch_reset(ws);
     }
   }
@@ -486,7 +494,7 @@ static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t
 }
 
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
-                           bool variance, Ws ws) {
+                           bool variance, Ws ws, unsigned long long* sums) {
   // both kernels find the rate prefix themselves (range_sums): no pre-scan
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
@@ -500,8 +508,9 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                            : persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem);
   int grid = range_grid(per, ntiles_of(nb_bound));
   if ((uint64_t)grid > ws.max_grid) grid = (int)ws.max_grid;  // then the kernel reports CAPACITY
-  if (variance)
-    k_var<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
+  if (variance || sums)
+    k_var<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, variance ? result : nullptr, sums,
+                                                   ws);
   else
     k_mean<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
   return cudaGetLastError();

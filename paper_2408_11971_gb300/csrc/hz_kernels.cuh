@@ -32,8 +32,9 @@ cudaError_t launch_scan_agg(const Launch& lc, Ws ws);
 // decode.cu
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
                               uint64_t n, Ws ws);
+// sums (optional, 5 words): S1 (two's complement, lo, hi), S2 (lo, hi), n
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
-                           bool variance, Ws ws);
+                           bool variance, Ws ws, unsigned long long* sums = nullptr);
 // ops.cu
 cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, uint8_t* out,
                           uint64_t cap, uint64_t* out_bytes, Ws ws);

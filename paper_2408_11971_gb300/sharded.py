@@ -1,0 +1,98 @@
+"""Mean and variance of one field whose compressed shards live on several
+devices or processes (one per rank).
+
+Each rank holds a stream of whole blocks of the field, compressed with the same
+absolute bound (the same eps_q bits). The library returns each shard's exact
+integer sums (hoszp_sums: S1 = sum q, S2 = sum q^2, n; Sec. V-B); the ranks add
+them with one all-reduce of 32-bit limbs held in int64 -- exact and independent
+of the order of addition -- and every rank finishes mean and variance with the
+same FP64 steps as the single-stream kernels, so a sharded field gives the same
+double as the whole field on one device.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+MASK64 = (1 << 64) - 1
+_LIMBS = 8  # S1 and S2 as four 32-bit limbs each
+
+
+@dataclass
+class Sums:
+    s1: int  # sum of q (signed)
+    s2: int  # sum of q^2
+    n: int
+
+    def __add__(self, o: "Sums") -> "Sums":
+        return Sums(self.s1 + o.s1, self.s2 + o.s2, self.n + o.n)
+
+
+def from_words(w) -> Sums:
+    """The five words written by hoszp_sums."""
+    s1 = int(w[0]) | (int(w[1]) << 64)
+    if s1 >> 127:
+        s1 -= 1 << 128
+    return Sums(s1, int(w[2]) | (int(w[3]) << 64), int(w[4]))
+
+
+def _to_limbs(s: Sums):
+    s1 = s.s1 & ((1 << 128) - 1)  # two's complement; the sum is taken modulo 2^128
+    out = [(s1 >> (32 * k)) & 0xFFFFFFFF for k in range(4)]
+    out += [(s.s2 >> (32 * k)) & 0xFFFFFFFF for k in range(4)]
+    return out + [s.n]
+
+
+def _from_limbs(v) -> Sums:
+    s1 = sum(int(v[k]) << (32 * k) for k in range(4)) & ((1 << 128) - 1)
+    if s1 >> 127:
+        s1 -= 1 << 128
+    s2 = sum(int(v[4 + k]) << (32 * k) for k in range(4))
+    return Sums(s1, s2, int(v[_LIMBS]))
+
+
+def allreduce(s: Sums, group=None) -> Sums:
+    """Exact sum of every rank's Sums (torch.distributed, any backend). Each
+    32-bit limb sum stays exact in int64 for up to 2^31 ranks."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(_to_limbs(s), dtype=torch.int64)
+    if dist.get_backend(group) == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return _from_limbs(t.cpu().tolist())
+
+
+def _u64_double(v: int) -> float:
+    return float(v & MASK64)
+
+
+def finish(s: Sums, eps_q: float):
+    """(mean, population variance) with the kernels' FP64 steps: the mean from
+    |S1| as hi * 2^64 + lo, the variance from the exact 256-bit numerator
+    n S2 - S1^2 converted word by word from the top."""
+    if s.n == 0:
+        raise ValueError("empty field")
+    import struct
+
+    e = struct.unpack("<f", struct.pack("<f", eps_q))[0]
+    e2 = 2.0 * e
+    a = -s.s1 if s.s1 < 0 else s.s1
+    md = _u64_double(a >> 64) * 18446744073709551616.0 + _u64_double(a)
+    mean = ((-md if s.s1 < 0 else md) / float(s.n)) * e2
+    D = s.n * s.s2 - s.s1 * s.s1
+    d = _u64_double(D >> 192)
+    for k in (2, 1, 0):
+        d = d * 18446744073709551616.0 + _u64_double(D >> (64 * k))
+    dn = float(s.n)
+    var = (d / (dn * dn)) * (e2 * e2)
+    return mean, var
+
+
+def mean_var(c_local, eps_q: float, group=None, ctx=None):
+    """Mean and variance of the field whose shard on this rank is the stream
+    c_local (a CUDA uint8 tensor); collective over `group`."""
+    from . import _binding as B
+
+    s = from_words(B.sums(c_local, ctx=ctx))
+    return finish(allreduce(s, group), eps_q)

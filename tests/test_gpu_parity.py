@@ -231,3 +231,22 @@ def test_repeated_calls_are_deterministic(hz, config1):
     for _ in range(3):
         assert np.array_equal(host(hz.compress(dev(x), eb=1e-3, mode="rel")), oc)
         assert close(hz.var(c), O.var(oc))
+
+
+def test_sums_words_and_sharded_finish(hz, config1):
+    """hoszp_sums gives the oracle's exact sums; finishing them on the host
+    (the multi-rank path) gives the kernels' mean and variance bit for bit, and
+    two shards of whole blocks add up to the whole field."""
+    from paper_2408_11971_gb300 import sharded
+
+    x, c, oc = config1
+    s = sharded.from_words(hz.sums(c))
+    s1, s2, n, e = O.sums(oc)
+    assert (s.s1, s.s2, s.n) == (s1, s2, n)
+    eq = float(hz.header(c)["eps_q"])
+    m, v = sharded.finish(s, eq)
+    assert m == hz.mean(c) and v == hz.var(c)
+    cut = 64 * 5000
+    p = [hz.compress(dev(x[:cut]), eb=eq), hz.compress(dev(x[cut:]), eb=eq)]
+    t = sharded.from_words(hz.sums(p[0])) + sharded.from_words(hz.sums(p[1]))
+    assert (t.s1, t.s2, t.n) == (s1, s2, n)

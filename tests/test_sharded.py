@@ -1,0 +1,89 @@
+"""A field split into shards of whole blocks across ranks (gloo, world size 2,
+on the CPU): the exact sums of the shards, added by one all-reduce, equal the
+sums of the whole field, and the finished mean and variance match the oracle's
+for the whole field. The shards' sums come from the oracle (no GPU here); on a
+GPU the same words come from hoszp_sums."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _field():
+    import datagen
+
+    return datagen.sines_1d(200_003, seed=31)  # ragged tail: 3125 blocks + 3 values
+
+
+def _rank(rank, world, port, q):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import oracle as O
+    from paper_2408_11971_gb300 import sharded
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x = _field()
+    eps = 1e-3 * float(x.max() - x.min())
+    nb = (x.size + 63) // 64
+    cut = [0, 1000 * 64, x.size][rank:rank + 2]  # shard 0: 1000 blocks, shard 1: the rest
+    shard = np.ascontiguousarray(x[cut[0]:cut[1]])
+    s1, s2, n, e = O.sums(O.compress(shard, eb=eps))
+    tot = sharded.allreduce(sharded.Sums(s1, s2, n))
+    m, v = sharded.finish(tot, float(e))
+    q.put((rank, tot.s1, tot.s2, tot.n, m, v, nb))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_combine_exact_sums():
+    import multiprocessing as mp
+
+    import oracle as O
+
+    O.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got = [q.get(timeout=120) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    x = _field()
+    eps = 1e-3 * float(x.max() - x.min())
+    whole = O.compress(x, eb=eps)
+    s1, s2, n, e = O.sums(whole)
+    om, ov = O.mean(whole), O.var(whole)
+    for rank, t1, t2, tn, m, v, nb in got:
+        assert (t1, t2, tn) == (s1, s2, n)  # exact, whatever the split
+        assert abs(m - om) <= 1e-12 * abs(om) and abs(v - ov) <= 1e-12 * abs(ov)
+    assert got[0][4:6] == got[1][4:6]  # every rank finishes to the same doubles
+
+
+def test_sums_words_roundtrip():
+    from paper_2408_11971_gb300 import sharded
+
+    for s1, s2, n in [(0, 0, 1), (-5, 25, 3), (-(1 << 100) - 7, (1 << 120) + 3, 1 << 40),
+                      ((1 << 126) - 1, (1 << 128) - 1, 5)]:
+        w = [s1 & (2**64 - 1), (s1 >> 64) & (2**64 - 1), s2 & (2**64 - 1), s2 >> 64, n]
+        s = sharded.from_words(w)
+        assert (s.s1, s.s2, s.n) == (s1, s2, n)
+        assert sharded._from_limbs(sharded._to_limbs(s)) == s
