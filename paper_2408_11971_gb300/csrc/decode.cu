@@ -9,98 +9,6 @@
 
 namespace hz {
 
-// ---------------------------------------------------------------- decompression
-constexpr int DEC_STAGES = 8;
-constexpr uint32_t DEC_RING = 8192;  // plane-ring words (64 KB)
-
-__global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_decompress(
-    const uint8_t* __restrict__ c, uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect,
-    const unsigned long long* __restrict__ pre, Ws ws) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  InStage* stages = reinterpret_cast<InStage*>(dyn);
-  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + DEC_STAGES);
-  __shared__ uint64_t full[DEC_STAGES], ready[DEC_STAGES], empty[DEC_STAGES];
-  __shared__ unsigned long long stage_tile[DEC_STAGES];
-  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
-  const Info h = parse_header(c, c_bytes);
-  int bad = 0;
-  uint64_t ntiles = 0;
-  if (!h.ok) bad = HOSZP_ERR_FORMAT;
-  else if (h.n != n_expect) bad = HOSZP_ERR_MISMATCH;
-  else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
-  const float e2 = 2.0f * h.eps_q;
-  const bool small = h.qbound < (1u << 22);
-  const OctetSel S = octet_sel(j);
-  ring_init3<DEC_STAGES>(full, ready, empty);
-  if (w >= LOADER_WARP) {
-    const uint64_t G = gridDim.x;
-    __shared__ ulonglong2 s_win[32][2];
-    PreWindow pw;
-    pw.init(s_win);
-    __shared__ uint32_t s_beg[DEC_STAGES];
-    PlaneRing<DEC_STAGES, DEC_RING> pr;
-    pr.init(ring, s_beg);
-    loader_warps<DEC_STAGES>(
-        w - LOADER_WARP, stage_tile, full, ready, empty, ntiles, ws.status,
-        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
-            auto&& release_one) {
-          unsigned long long pv[4];
-          pw.get(pre, k, blockIdx.x, G, ntiles, pv);
-          const TileSpan sp = tile_span(h, t, pv);
-          const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
-          const uint32_t at = pr.commit(k, p0, sp.plane_words());
-          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, sp, ring, at);
-        },
-        [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
-  } else {
-    RingPos rp{0, 0u};
-    for (;;) {
-      mbar_wait(&ready[rp.s], rp.par, ws.status);
-      const unsigned long long tile = stage_tile[rp.s];
-      if (tile >= ntiles) break;
-      const InStage& sg = stages[rp.s];
-      const BlockRef br = block_ref_s(sg, ring, g, j);
-      const int kmax = sg.kmx[w];
-      int d[8], q[8];
-      octet_deltas(br, kmax, j, S, d);
-      __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(&empty[rp.s]);
-      rp.next<DEC_STAGES>();
-      octet_values(br, d, j, q);
-      const uint64_t i0 = (tile * TILE + g) * L + 8 * j;
-      float v[8];
-#pragma unroll
-      for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
-      if (br.len == L) {
-        float4* o = reinterpret_cast<float4*>(x + i0);
-        o[0] = make_float4(v[0], v[1], v[2], v[3]);
-        o[1] = make_float4(v[4], v[5], v[6], v[7]);
-      } else {
-#pragma unroll
-        for (int t = 0; t < 8; t++)
-          if (8 * j + t < br.len) x[i0 + t] = v[t];
-      }
-    }
-  }
-  if (bad) set_status(ws.status, bad);
-}
-
-cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
-                              uint64_t n, Ws ws) {
-  cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
-  if (e != cudaSuccess) return e;
-  const size_t smem = DEC_STAGES * sizeof(InStage) + DEC_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
-  k_decompress<<<persistent_grid(k_decompress, CONSUMER_THREADS, lc.grid, smem), CONSUMER_THREADS,
-                 smem, lc.stream>>>(c, c_bytes, x, n, ws.pre[0], ws);
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- mean / variance
 constexpr int MOM_STAGES = 8;
 constexpr uint32_t MOM_RING = 8192;  // plane-ring words (64 KB)
@@ -476,6 +384,123 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
       launch_reset(ws);
     }
   }
+}
+
+// ---------------------------------------------------------------- decompression
+// Full decompression (inverse of every pipeline step, Fig. 2) over the
+// super-tile pipeline: warp i of a group decodes tile i of the stage 4 blocks
+// at a time (octet layout) to q, dequantizes x' = float(q) * 2 eps_q and
+// stores each block's 64 floats (a warp writes 1 KB contiguous per step).
+__global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
+    const uint8_t* __restrict__ c, uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect,
+    Ws ws) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  SStage* stages = reinterpret_cast<SStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MEAN_STAGES);
+  __shared__ uint64_t full[MEAN_STAGES], empty[MEAN_STAGES];
+  __shared__ unsigned long long stage_st[MEAN_STAGES];
+  __shared__ uint32_t s_ts[TS_MAX];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const Info h = parse_header(c, c_bytes);
+  const unsigned long long epoch = launch_epoch(ws);
+  int bad = 0;
+  bool ok = h.ok;
+  if (!h.ok) bad = HOSZP_ERR_FORMAT;
+  else if (h.n != n_expect) {
+    bad = HOSZP_ERR_MISMATCH;
+    ok = false;
+  }
+  const uint64_t ntiles = ok ? ntiles_of(h.nb) : 0;
+  const uint64_t nst = nsuper_of(ntiles);
+  if (tid == 0) {
+    for (int k = 0; k < MEAN_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], MEAN_GW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const SRange rg = range_sums(c, h, ntiles, nst, s_ts, ws, epoch, bad);
+  __syncthreads();
+  if (w == MEAN_NCW) {
+    __shared__ uint32_t s_beg[MEAN_STAGES];
+    super_loader<MEAN_STAGES, MEAN_RING, MEAN_GROUPS>(stages, ring, s_beg, full, empty, stage_st,
+                                                       c, h, rg, s_ts, ws, epoch);
+  } else if (w < MEAN_NCW) {
+    const int grp = w / MEAN_GW, ti = w % MEAN_GW;
+    const int j = lane & 7, gq = lane >> 3;
+    const OctetSel S = octet_sel(j);
+    const int lastlen = (int)(h.n - (h.nb - 1) * L);
+    const float e2 = 2.0f * h.eps_q;
+    const bool small = h.qbound < (1u << 22);
+    for (uint64_t k = 0;; k++) {
+      const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
+      const int sk = (int)(u % MEAN_STAGES);
+      mbar_wait(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status);
+      const unsigned long long s = stage_st[sk];
+      if (s == ~0ull) break;
+      const SStage& sg = stages[sk];
+      const uint64_t tile = (uint64_t)STILES * s + ti;
+      const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+      const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
+      const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
+      const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
+      for (int it = 0; it < steps; it++) {
+        const int b = 4 * it + gq;
+        uint32_t r, ex;
+        tile_block(tr, b, r, ex);
+        BlockRef br;
+        br.rate = (int)r;
+        br.outlier = sg.outlier[TILE * ti + b];
+        br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+        br.planes = pls + (ex & 0xffffu);
+        br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
+        const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+        int d[8], q[8];
+        octet_deltas(br, kmax, j, S, d);
+        octet_values(br, d, j, q);
+        float v[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+        const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
+        if (br.len == L) {
+          float4* o = reinterpret_cast<float4*>(x + i0);
+          __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
+          __stcs(o + 1, make_float4(v[4], v[5], v[6], v[7]));
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; t++)
+            if (8 * j + t < br.len) x[i0 + t] = v[t];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && w == 0) {
+    const bool tot_ok = range_totals_ok(ws, h);
+    if (tid == 0) {
+      if (ok && !tot_ok) set_status(ws.status, HOSZP_ERR_FORMAT);
+      launch_reset(ws);
+    }
+  }
+}
+
+cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
+                              uint64_t n, Ws ws) {
+  // the kernel finds the rate prefix itself (range_sums): no pre-scan
+  const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const uint64_t nb_bound = c_bytes > HOSZP_HEADER_BYTES ? (c_bytes - HOSZP_HEADER_BYTES) / 5 + 1 : 1;
+  int grid = range_grid(persistent_grid(k_decompress, MEAN_THREADS, lc.grid, smem),
+                        ntiles_of(nb_bound));
+  if ((uint64_t)grid > ws.max_grid) grid = (int)ws.max_grid;  // then the kernel reports CAPACITY
+  k_decompress<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
+  return cudaGetLastError();
 }
 
 template <bool VAR>
