@@ -82,7 +82,7 @@ int ensure_ws(hoszp_ctx* c, uint64_t tiles, uint64_t staging_words) {
   const uint64_t o_agg = off;
   off = round_up(off + (tiles + 1) * 8, 256);
   const uint64_t o_cagg = off;
-  off = round_up(off + grid * sizeof(CtaAgg), 256);
+  off = round_up(off + 2 * grid * sizeof(CtaAgg), 256);  // two streams per CTA (addition)
   const uint64_t o_part = off;
   off = round_up(off + grid * sizeof(Partial), 256);
   const uint64_t o_range = off;
@@ -345,7 +345,7 @@ static int add_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* 
   Launch lc = lc_of(ctx, stream);
   rc = cuda_rc(launch_add(lc, a, a_bytes, b, b_bytes, o, cap, subtract, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_ADD, 0, ctx->ws));
+  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_EXPLICIT, 0, ctx->ws));
 }
 
 int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,

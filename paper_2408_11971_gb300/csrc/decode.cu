@@ -495,10 +495,7 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
     cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  const uint64_t nb_bound = c_bytes > HOSZP_HEADER_BYTES ? (c_bytes - HOSZP_HEADER_BYTES) / 5 + 1 : 1;
-  int grid = range_grid(persistent_grid(k_decompress, MEAN_THREADS, lc.grid, smem),
-                        ntiles_of(nb_bound));
-  if ((uint64_t)grid > ws.max_grid) grid = (int)ws.max_grid;  // then the kernel reports CAPACITY
+  const int grid = persistent_grid(k_decompress, MEAN_THREADS, lc.grid, smem);
   k_decompress<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
   return cudaGetLastError();
 }
@@ -528,11 +525,8 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
     cudaFuncSetAttribute(k_var, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  const uint64_t nb_bound = c_bytes > HOSZP_HEADER_BYTES ? (c_bytes - HOSZP_HEADER_BYTES) / 5 + 1 : 1;
-  const int per = variance ? persistent_grid(k_var, MEAN_THREADS, lc.grid, smem)
-                           : persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem);
-  int grid = range_grid(per, ntiles_of(nb_bound));
-  if ((uint64_t)grid > ws.max_grid) grid = (int)ws.max_grid;  // then the kernel reports CAPACITY
+  const int grid = (variance || sums) ? persistent_grid(k_var, MEAN_THREADS, lc.grid, smem)
+                                      : persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem);
   if (variance || sums)
     k_var<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, variance ? result : nullptr, sums,
                                                    ws);

@@ -1,69 +1,80 @@
-// hz_super.cuh — input pipeline over super-tiles: a stage holds STB = 512
-// consecutive blocks (8 tiles) of one stream and is filled by one loader warp
-// with four bulk copies (rates, outliers, sign words, plane words). Compared
-// with one stage per 64-block tile, the loader does an eighth of the work per
-// byte: issuing a stage costs the loader several hundred cycles whatever its
-// size, so stages must be large for one loader warp to keep HBM busy. The
-// consumer warps (one per tile of the stage) find their blocks' sign and plane
-// words themselves, from the tile's rates and the tile bases the loader writes
-// into the stage.
+// hz_super.cuh — input pipeline over super-tiles: a stage holds NT
+// consecutive tiles (64 NT blocks) of one stream -- or of two streams with
+// the same block count, for the bivariate operators -- and is filled by one
+// loader warp with four bulk copies per stream (rates, outliers, sign words,
+// plane words). Compared with one stage per 64-block tile, the loader does
+// 1/NT of the work per byte: issuing a stage costs the loader several hundred
+// cycles whatever its size, so stages must be large for one loader warp to
+// keep HBM busy. The consumer warps find their blocks' sign and plane words
+// themselves, from the tile's rates and the tile bases the loader writes into
+// the stage.
 #pragma once
 #include <cstddef>
 
-#include "hz_pipe.cuh"
+#include "hz_ws.cuh"
 
 namespace hz {
 
-constexpr int STILES = 8;              // tiles per super-tile
-constexpr int STB = STILES * TILE;     // blocks per super-tile
-
-struct __align__(16) SStage {
-  uint64_t sign[STB + 2];  // the super-tile's sign words, from a 16-byte boundary
-  int outlier[STB];
-  uint8_t rate[STB];       // as copied: read through tile_rates(), which sanitizes
-  uint32_t sbase, pbase;   // index of the first sign / plane word in sign[] / its ring span
-  uint32_t pring;          // ring word index where the plane copy starts
-  uint32_t tnc[STILES];    // non-constant blocks of the super-tile before each tile
-  uint32_t tr[STILES];     // plane words of the super-tile before each tile
-  uint32_t pad[1];
+template <int NT>
+struct __align__(16) SStageT {
+  uint64_t sign[NT * TILE + 2];  // the super-tile's sign words, from a 16-byte boundary
+  int outlier[NT * TILE];
+  uint8_t rate[NT * TILE];       // as copied: read through tile_rates(), which sanitizes
+  uint32_t sbase, pbase;         // index of the first sign / plane word in sign[] / its ring span
+  uint32_t pring;                // ring word index where the plane copy starts
+  uint32_t tnc[NT];              // non-constant blocks of the super-tile before each tile
+  uint32_t tr[NT];               // plane words of the super-tile before each tile
+  unsigned long long bnc, br;    // the stream's prefix (non-constant blocks, words) at the stage
 };
-static_assert(sizeof(uint64_t) * (STB + 2) % 16 == 0, "sign[] keeps alignment");
-static_assert(sizeof(SStage) % 16 == 0, "stages stay 16-byte aligned");
-static_assert(offsetof(SStage, sign) % 16 == 0 && offsetof(SStage, outlier) % 16 == 0 &&
-                  offsetof(SStage, rate) % 16 == 0,
-              "bulk-copy destinations are 16-byte aligned");
 
-// Largest plane copy of one super-tile, in words (rate 31 everywhere, plus the
-// rounding of both ends to 16 bytes).
-constexpr uint32_t STILE_PLANE_WORDS_MAX = STB * MAX_RATE + 2;
+constexpr int STILES = 8;            // tiles per super-tile of the univariate kernels
+constexpr int STB = STILES * TILE;   // blocks per super-tile
+using SStage = SStageT<STILES>;
 
+template <int NT>
+struct SuperChecks {
+  static_assert(sizeof(uint64_t) * (NT * TILE + 2) % 16 == 0, "sign[] keeps alignment");
+  static_assert(sizeof(SStageT<NT>) % 16 == 0, "stages stay 16-byte aligned");
+  static_assert(offsetof(SStageT<NT>, sign) % 16 == 0 && offsetof(SStageT<NT>, outlier) % 16 == 0 &&
+                    offsetof(SStageT<NT>, rate) % 16 == 0,
+                "bulk-copy destinations are 16-byte aligned");
+  // Largest plane copy of one super-tile, in words (rate 31 everywhere, plus
+  // the rounding of both ends to 16 bytes).
+  static constexpr uint32_t kPlaneWordsMax = NT * TILE * MAX_RATE + 2;
+};
+constexpr uint32_t STILE_PLANE_WORDS_MAX = SuperChecks<STILES>::kPlaneWordsMax;
+
+template <int NT = STILES>
 __device__ __forceinline__ uint64_t nsuper_of(uint64_t ntiles) {
-  return (ntiles + STILES - 1) / STILES;
+  return (ntiles + NT - 1) / NT;
 }
 
-// Byte ranges of super-tile s (blocks STB*s ..), from the pre-scan's {nc, r}
-// prefixes at its first tile (pv0) and after its last tile (pv1).
+// Byte ranges of super-tile s (blocks 64 NT s ..), from the {nc, r} prefixes
+// of the stream at its first tile (pv0) and after its last tile (pv1).
 struct SSpan {
   uint64_t sa16, pa16;
   unsigned rb, ob, sbytes, pbytes;
   uint32_t sbase, pbase;
   __device__ __forceinline__ uint32_t plane_words() const { return pbytes >> 3; }
 };
+template <int NT>
 __device__ __forceinline__ SSpan sspan(const Info& h, uint64_t s, ulonglong2 pv0, ulonglong2 pv1) {
+  constexpr int NB = NT * TILE;
   SSpan sp;
-  const uint64_t b0 = (uint64_t)STB * s;
+  const uint64_t b0 = (uint64_t)NB * s;
   const uint64_t rate_end = align16(h.nb), out_end = align16(4 * h.nb);
-  sp.rb = (unsigned)umin64(STB, rate_end - b0);
-  sp.ob = (unsigned)umin64(4 * STB, out_end - 4 * b0);
+  sp.rb = (unsigned)umin64(NB, rate_end - b0);
+  sp.ob = (unsigned)umin64(4 * NB, out_end - 4 * b0);
   const uint64_t sa = h.o_sign + 8 * pv0.x, se = h.o_sign + 8 * pv1.x;
   const uint64_t pa = h.o_plane + 8 * pv0.y, pe = h.o_plane + 8 * pv1.y;
   sp.sa16 = sa & ~15ull;
   sp.pa16 = pa & ~15ull;
   sp.sbytes = (pv1.x > pv0.x) ? (unsigned)(align16(se) - sp.sa16) : 0u;
   sp.pbytes = (pv1.y > pv0.y) ? (unsigned)(align16(pe) - sp.pa16) : 0u;
-  // only a corrupt pre-scan (refused before any stage is issued) exceeds these
-  if (sp.pbytes > 8u * STILE_PLANE_WORDS_MAX) sp.pbytes = 8u * STILE_PLANE_WORDS_MAX;
-  if (sp.sbytes > 8u * (STB + 2)) sp.sbytes = 8u * (STB + 2);
+  // only a range that runs past the header's totals exceeds these, and the
+  // loader refuses such a range before any copy
+  if (sp.pbytes > 8u * SuperChecks<NT>::kPlaneWordsMax) sp.pbytes = 8u * SuperChecks<NT>::kPlaneWordsMax;
+  if (sp.sbytes > 8u * (NB + 2)) sp.sbytes = 8u * (NB + 2);
   sp.sbase = (uint32_t)((sa - sp.sa16) >> 3);
   sp.pbase = (uint32_t)((pa - sp.pa16) >> 3);
   return sp;
@@ -78,20 +89,17 @@ __device__ __forceinline__ SSpan sspan(const Info& h, uint64_t s, ulonglong2 pv0
 // few microseconds (its CTA may not be resident yet) is summed by the loader
 // itself from the rate bytes, so no CTA ever depends on another being
 // scheduled. The CTA then walks its range in order with a running prefix. No
-// separate pre-scan launch is made.
-constexpr int TS_MAX = 4096;  // tiles of one CTA's range (their sums live in shared memory)
+// separate pre-scan launch is made. With NS streams (same block count), the
+// totals of stream k of range v live at cta_agg[NS v + k].
+// The sums of a range's first TS_MAX tiles are kept in shared memory; a range
+// longer than that (a stream of billions of values) has the sums of its later
+// tiles recomputed by the loader from the rate bytes, stage by stage.
+constexpr int TS_MAX = 4096;
 
 struct SRange {
   uint64_t s0, s1;   // super-tiles [s0, s1) of this CTA
   uint32_t v;        // range index (= blockIdx.x)
 };
-
-// Grid for a stream of at most `tiles_bound` tiles: at least `persistent`
-// CTAs, and enough that no range exceeds TS_MAX tiles.
-__host__ __forceinline__ int range_grid(int persistent, uint64_t tiles_bound) {
-  const uint64_t need = (tiles_bound + TS_MAX - 1) / TS_MAX;
-  return (int)(need > (uint64_t)persistent ? need : (uint64_t)persistent);
-}
 
 // Rate sums of 16 rate bytes starting at block `b0` (a multiple of 16): the
 // non-constant blocks and the rate sum, rates above 31 counting as 31 (as
@@ -126,52 +134,59 @@ __device__ __forceinline__ SRange range_of(uint32_t v, uint64_t nst) {
 }
 
 // All threads of the CTA: its range, the range's per-tile packed sums
-// (non-constant blocks << 16 | rate sum) into s_ts, and the published range
-// total.
-__device__ __forceinline__ SRange range_sums(const uint8_t* c, const Info& h, uint64_t ntiles,
-                                             uint64_t nst, uint32_t* s_ts, const Ws& ws,
-                                             unsigned long long epoch, int& bad) {
-  __shared__ unsigned long long s_tot[2][32];
+// (non-constant blocks << 16 | rate sum) of each of the NS streams into
+// s_ts[k * ts_max ..], and the published range totals.
+template <int NT, int NS>
+__device__ __forceinline__ SRange range_sums_n(const uint8_t* const* c, const Info* h,
+                                               uint64_t ntiles, uint64_t nst, uint32_t* s_ts,
+                                               int ts_max, const Ws& ws, unsigned long long epoch,
+                                               int& bad) {
+  __shared__ unsigned long long s_tot[2 * NS][32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nw = (int)(blockDim.x >> 5);
   SRange rg = range_of(blockIdx.x, nst);
-  const uint64_t t0 = (uint64_t)STILES * rg.s0, t1 = umin64((uint64_t)STILES * rg.s1, ntiles);
-  unsigned long long tnc = 0, tr = 0;
-  if (t1 > t0 + TS_MAX) {  // the host sizes the grid so that this never happens
-    bad = HOSZP_ERR_CAPACITY;
-    rg.s1 = rg.s0;
-  } else {
-    const int nq = (int)(4 * (t1 - t0));  // 16-byte quarters of the range's tiles
-    for (int i = tid; i < ((nq + 31) & ~31); i += (int)blockDim.x) {
-      uint32_t nc = 0, r = 0;
-      if (i < nq) rate_sums16(c, h, TILE * (t0 + (uint64_t)(i >> 2)) + 16 * (uint64_t)(i & 3), nc, r, bad);
-      uint32_t pk = (nc << 16) | r;  // a tile: nc <= 64, r <= 1984
-      pk += __shfl_xor_sync(0xffffffffu, pk, 1);
-      pk += __shfl_xor_sync(0xffffffffu, pk, 2);
-      if (i < nq && (i & 3) == 0) {
-        s_ts[i >> 2] = pk;
-        tnc += pk >> 16;
-        tr += pk & 0xffffu;
+  const uint64_t t0 = (uint64_t)NT * rg.s0, t1 = umin64((uint64_t)NT * rg.s1, ntiles);
+  unsigned long long tnc[NS], tr[NS];
+#pragma unroll
+  for (int k = 0; k < NS; k++) tnc[k] = tr[k] = 0;
+  {
+    const uint64_t nq = 4 * (t1 - t0);  // 16-byte quarters of the range's tiles
+    for (uint64_t i = tid; i < ((nq + 31) & ~31ull); i += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < NS; k++) {
+        uint32_t nc = 0, r = 0;
+        if (i < nq) rate_sums16(c[k], h[k], TILE * (t0 + (i >> 2)) + 16 * (i & 3), nc, r, bad);
+        uint32_t pk = (nc << 16) | r;  // a tile: nc <= 64, r <= 1984
+        pk += __shfl_xor_sync(0xffffffffu, pk, 1);
+        pk += __shfl_xor_sync(0xffffffffu, pk, 2);
+        if (i < nq && (i & 3) == 0) {
+          if ((i >> 2) < (uint64_t)ts_max) s_ts[k * ts_max + (i >> 2)] = pk;
+          tnc[k] += pk >> 16;
+          tr[k] += pk & 0xffffu;
+        }
       }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    tnc += __shfl_xor_sync(0xffffffffu, tnc, o);
-    tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  }
-  if (lane == 0) {
-    s_tot[0][wid] = tnc;
-    s_tot[1][wid] = tr;
+  for (int k = 0; k < NS; k++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tnc[k] += __shfl_xor_sync(0xffffffffu, tnc[k], o);
+      tr[k] += __shfl_xor_sync(0xffffffffu, tr[k], o);
+    }
+    if (lane == 0) {
+      s_tot[2 * k][wid] = tnc[k];
+      s_tot[2 * k + 1][wid] = tr[k];
+    }
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < NS) {
     unsigned long long a = 0, b = 0;
-    for (int k = 0; k < nw; k++) {
-      a += s_tot[0][k];
-      b += s_tot[1][k];
+    for (int w = 0; w < nw; w++) {
+      a += s_tot[2 * tid][w];
+      b += s_tot[2 * tid + 1][w];
     }
-    CtaAgg* g = ws.cta_agg + rg.v;
+    CtaAgg* g = ws.cta_agg + (uint64_t)NS * rg.v + tid;
     g->nc = a;
     g->r = b;
     __threadfence();
@@ -180,12 +195,21 @@ __device__ __forceinline__ SRange range_sums(const uint8_t* c, const Info& h, ui
   return rg;
 }
 
-// Loader warp: the exclusive prefix (nc, r) of range v, summed from the
-// published totals of ranges 0..v-1. A total still missing after about
-// RANGE_POLL_NS is computed here from the rate bytes instead (whole warp).
+// Single-stream form (mean, variance, decompression).
+__device__ __forceinline__ SRange range_sums(const uint8_t* c, const Info& h, uint64_t ntiles,
+                                             uint64_t nst, uint32_t* s_ts, const Ws& ws,
+                                             unsigned long long epoch, int& bad) {
+  return range_sums_n<STILES, 1>(&c, &h, ntiles, nst, s_ts, TS_MAX, ws, epoch, bad);
+}
+
+// Loader warp: the exclusive prefix (nc, r) of stream k (of NS) at range v,
+// summed from the published totals of ranges 0..v-1. A total still missing
+// after about RANGE_POLL_NS is computed here from the rate bytes instead
+// (whole warp).
 constexpr unsigned long long RANGE_POLL_NS = 4000;
+template <int NT, int NS>
 __device__ __forceinline__ void range_base(const uint8_t* c, const Info& h, uint64_t ntiles,
-                                           uint64_t nst, const Ws& ws, uint32_t v,
+                                           uint64_t nst, const Ws& ws, uint32_t v, int k,
                                            unsigned long long epoch, unsigned long long& bnc,
                                            unsigned long long& br, int& bad) {
   const int lane = threadIdx.x & 31;
@@ -196,7 +220,7 @@ __device__ __forceinline__ void range_base(const uint8_t* c, const Info& h, uint
     const uint32_t u = base + lane;
     bool have = u >= v;
     if (!have) {
-      const CtaAgg* g = ws.cta_agg + u;
+      const CtaAgg* g = ws.cta_agg + (uint64_t)NS * u + k;
       for (;;) {
         if (ld_acquire(&g->flag) == want) {
           a += *reinterpret_cast<const volatile unsigned long long*>(&g->nc);
@@ -214,8 +238,8 @@ __device__ __forceinline__ void range_base(const uint8_t* c, const Info& h, uint
       const int src = __ffs(miss) - 1;
       miss &= miss - 1;
       const SRange ru = range_of(base + src, nst);
-      const uint64_t q0 = 4 * (uint64_t)STILES * ru.s0;
-      const uint64_t q1 = 4 * umin64((uint64_t)STILES * ru.s1, ntiles);
+      const uint64_t q0 = 4 * (uint64_t)NT * ru.s0;
+      const uint64_t q1 = 4 * umin64((uint64_t)NT * ru.s1, ntiles);
       unsigned long long sa = 0, sb = 0;
       for (uint64_t q = q0 + lane; q < q1; q += 32) {
         uint32_t nc, r;
@@ -243,22 +267,25 @@ __device__ __forceinline__ void range_base(const uint8_t* c, const Info& h, uint
   br = b;
 }
 
-// Loader warp of a super-tile pipeline over the CTA's range [rg.s0, rg.s1):
-// for stage use k = 0, 1, ... it waits for the release of use k - S
-// (empty[k % S], released in order), then bulk-copies super-tile rg.s0 + k
-// into stages[k % S] and its plane words into the ring; the copy completes on
+// Loader warp of a super-tile pipeline over the CTA's range [rg.s0, rg.s1) of
+// NS streams with the same block count (c[k], h[k], tile sums at
+// s_ts[k ts_max ..]). For stage use k = 0, 1, ... it waits for the release of
+// use k - S (empty[k % S], released in order), then bulk-copies super-tile
+// rg.s0 + k of stream q into stages[q S + k % S] and the plane words of all
+// streams into one span of the ring (stream order); the copies complete on
 // full[k % S]. stage_st[] gets the super-tile id, ~0 once the walk ends (one
-// such end stage per consumer group, each completing without data). Offsets
-// come from the range base and the tile sums in s_ts; a range whose words
-// would run past the header's totals stops with FORMAT.
-template <int S, uint32_t RW, int GROUPS>
-__device__ __forceinline__ void super_loader(SStage* stages, uint64_t* ring, uint32_t* s_beg,
-                                             uint64_t* full, uint64_t* empty,
-                                             unsigned long long* stage_st, const uint8_t* c,
-                                             const Info& h, const SRange& rg,
-                                             const uint32_t* s_ts, const Ws& ws,
-                                             unsigned long long epoch) {
-  static_assert(RW >= STILE_PLANE_WORDS_MAX + 2, "the ring holds the largest super-tile");
+// such end stage per consumer group, each completing without data). A range
+// whose words would run past a header's totals stops with FORMAT.
+template <int NT, int NS, int S, uint32_t RW, int GROUPS>
+__device__ __forceinline__ void super_loader_n(SStageT<NT>* stages, uint64_t* ring,
+                                               uint32_t* s_beg, uint64_t* full, uint64_t* empty,
+                                               unsigned long long* stage_st,
+                                               const uint8_t* const* c, const Info* h,
+                                               const SRange& rg, const uint32_t* s_ts, int ts_max,
+                                               const Ws& ws, unsigned long long epoch) {
+  static_assert(RW >= NS * SuperChecks<NT>::kPlaneWordsMax + 2,
+                "the ring holds the largest super-tile of every stream");
+  static_assert(NT <= 16 && NS <= 2, "tile sums are spread over the warp's lanes");
   const int lane = threadIdx.x & 31;
   PlaneRing<S, RW> pr;
   pr.init(ring, s_beg);
@@ -267,30 +294,54 @@ __device__ __forceinline__ void super_loader(SStage* stages, uint64_t* ring, uin
     mbar_wait(&empty[k_rel % S], (k_rel / S) & 1, ws.status);
     k_rel++;
   };
-  unsigned long long nc = 0, r = 0;
+  const uint64_t ntiles = ntiles_of(h[0].nb);
+  const uint64_t nst = nsuper_of<NT>(ntiles);
+  unsigned long long nc[NS], r[NS];
   int bad = 0;
-  if (rg.s1 > rg.s0) range_base(c, h, ntiles_of(h.nb), nsuper_of(ntiles_of(h.nb)), ws, rg.v, epoch, nc, r, bad);
+#pragma unroll
+  for (int k = 0; k < NS; k++) {
+    nc[k] = r[k] = 0;
+    if (rg.s1 > rg.s0)
+      range_base<NT, NS>(c[k], h[k], ntiles, nst, ws, rg.v, k, epoch, nc[k], r[k], bad);
+  }
   if (bad && lane == 0) set_status(ws.status, bad);
   bool stop = false;
   int ends = 0;
+  // lanes 16q .. 16q + NT - 1 hold the tile sums of stream q
+  const int ks = lane >> 4, ti = lane & 15;
   for (uint32_t k = 0; ends < GROUPS; k++) {
     const int sk = (int)(k % S);
     while (k_rel + S <= k) release_one();
     const uint64_t s = rg.s0 + k;
-    // this super-tile's tile sums: lanes 0..STILES-1 hold one tile each
     uint32_t pk = 0;
-    if (!stop && s < rg.s1 && lane < STILES && (uint64_t)STILES * s + lane < ntiles_of(h.nb))
-      pk = s_ts[STILES * k + lane];  // tiles past the stream's end have no sums
+    if (!stop && s < rg.s1 && ks < NS && ti < NT && (uint64_t)NT * s + ti < ntiles) {
+      if (NT * k + ti < (uint32_t)ts_max) {
+        pk = s_ts[ks * ts_max + NT * k + ti];  // tiles past the stream's end have no sums
+      } else {  // beyond the sums kept: this tile's 64 rate bytes, read again
+        for (int qq = 0; qq < 4; qq++) {
+          uint32_t a, b;
+          rate_sums16(c[ks], h[ks], TILE * ((uint64_t)NT * s + ti) + 16 * qq, a, b, bad);
+          pk += (a << 16) | b;
+        }
+      }
+    }
     uint32_t inc = pk;
 #pragma unroll
-    for (int o = 1; o < STILES; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
+    for (int o = 1; o < NT; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o, 16);
+      if (ti >= o) inc += y;
     }
     const uint32_t excl = inc - pk;
-    const uint32_t tot = __shfl_sync(0xffffffffu, inc, STILES - 1);
-    const unsigned long long nc1 = nc + (tot >> 16), r1 = r + (tot & 0xffffu);
-    if (!stop && s < rg.s1 && (nc1 > h.nnc || r1 > h.R)) {
+    bool over = false;
+    unsigned long long nc1[NS], r1[NS];
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      const uint32_t tot = __shfl_sync(0xffffffffu, inc, 16 * q + NT - 1);
+      nc1[q] = nc[q] + (tot >> 16);
+      r1[q] = r[q] + (tot & 0xffffu);
+      over = over || nc1[q] > h[q].nnc || r1[q] > h[q].R;
+    }
+    if (!stop && s < rg.s1 && over) {
       if (lane == 0) set_status(ws.status, HOSZP_ERR_FORMAT);
       stop = true;
     }
@@ -303,43 +354,82 @@ __device__ __forceinline__ void super_loader(SStage* stages, uint64_t* ring, uin
       __syncwarp();
       continue;
     }
-    const SSpan sp = sspan(h, s, make_ulonglong2(nc, r), make_ulonglong2(nc1, r1));
-    const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
-    const uint32_t at = pr.commit(k, p0, sp.plane_words());
-    SStage* sg = &stages[sk];
-    if (lane < STILES) {
-      sg->tnc[lane] = excl >> 16;
-      sg->tr[lane] = excl & 0xffffu;
+    SSpan sp[NS];
+    uint32_t words[NS], all = 0;
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      sp[q] = sspan<NT>(h[q], s, make_ulonglong2(nc[q], r[q]), make_ulonglong2(nc1[q], r1[q]));
+      words[q] = sp[q].plane_words();
+      all += words[q];
+    }
+    const uint32_t p0 = pr.reserve(k, all, k_rel, release_one);
+    const uint32_t at = pr.commit(k, p0, all);
+    if (ks < NS && ti < NT) {
+      SStageT<NT>* sg = &stages[ks * S + sk];
+      sg->tnc[ti] = excl >> 16;
+      sg->tr[ti] = excl & 0xffffu;
     }
     __syncwarp();  // the tile bases are ordered before lane 0's arrival on full[]
     if (lane == 0) {
       stage_st[sk] = s;
-      sg->sbase = sp.sbase;
-      sg->pbase = sp.pbase;
-      sg->pring = at;
+      uint32_t tx = 0, a = at;
+#pragma unroll
+      for (int q = 0; q < NS; q++) {
+        SStageT<NT>* sg = &stages[q * S + sk];
+        sg->sbase = sp[q].sbase;
+        sg->pbase = sp[q].pbase;
+        sg->pring = a;
+        sg->bnc = nc[q];
+        sg->br = r[q];
+        a += words[q];
+        tx += sp[q].rb + sp[q].ob + sp[q].sbytes + sp[q].pbytes;
+      }
       fence_proxy_async();
-      mbar_expect_tx(&full[sk], sp.rb + sp.ob + sp.sbytes + sp.pbytes);
-      const uint64_t b0 = (uint64_t)STB * s;
-      bulk_g2s(sg->rate, c + HOSZP_HEADER_BYTES + b0, sp.rb, &full[sk]);
-      bulk_g2s(sg->outlier, c + h.o_out + 4 * b0, sp.ob, &full[sk]);
-      if (sp.sbytes) bulk_g2s(sg->sign, c + sp.sa16, sp.sbytes, &full[sk]);
-      if (sp.pbytes) bulk_g2s(ring + at, c + sp.pa16, sp.pbytes, &full[sk]);
+      mbar_expect_tx(&full[sk], tx);
+      const uint64_t b0 = (uint64_t)NT * TILE * s;
+      a = at;
+#pragma unroll
+      for (int q = 0; q < NS; q++) {
+        SStageT<NT>* sg = &stages[q * S + sk];
+        bulk_g2s(sg->rate, c[q] + HOSZP_HEADER_BYTES + b0, sp[q].rb, &full[sk]);
+        bulk_g2s(sg->outlier, c[q] + h[q].o_out + 4 * b0, sp[q].ob, &full[sk]);
+        if (sp[q].sbytes) bulk_g2s(sg->sign, c[q] + sp[q].sa16, sp[q].sbytes, &full[sk]);
+        if (sp[q].pbytes) bulk_g2s(ring + a, c[q] + sp[q].pa16, sp[q].pbytes, &full[sk]);
+        a += words[q];
+      }
     }
     __syncwarp();
-    nc = nc1;
-    r = r1;
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      nc[q] = nc1[q];
+      r[q] = r1[q];
+    }
   }
+  if (bad) set_status(ws.status, bad);
 }
 
-// Last CTA of a launch, one whole warp: the published range totals must add
-// up to the header's (nnc, R); a stream whose rates disagree with its header
-// is FORMAT. Every lane gets the answer.
-__device__ __forceinline__ bool range_totals_ok(const Ws& ws, const Info& h) {
+// Single-stream form (mean, variance, decompression).
+template <int S, uint32_t RW, int GROUPS>
+__device__ __forceinline__ void super_loader(SStage* stages, uint64_t* ring, uint32_t* s_beg,
+                                             uint64_t* full, uint64_t* empty,
+                                             unsigned long long* stage_st, const uint8_t* c,
+                                             const Info& h, const SRange& rg,
+                                             const uint32_t* s_ts, const Ws& ws,
+                                             unsigned long long epoch) {
+  super_loader_n<STILES, 1, S, RW, GROUPS>(stages, ring, s_beg, full, empty, stage_st, &c, &h, rg,
+                                           s_ts, TS_MAX, ws, epoch);
+}
+
+// Last CTA of a launch, one whole warp: the published range totals of stream
+// k (of ns) must add up to its header's (nnc, R); a stream whose rates
+// disagree with its header is FORMAT. Every lane gets the answer.
+__device__ __forceinline__ bool range_totals_ok(const Ws& ws, const Info& h, int k = 0,
+                                                int ns = 1) {
   const int lane = threadIdx.x & 31;
   unsigned long long a = 0, b = 0;
   for (unsigned int u = lane; u < gridDim.x; u += 32) {
-    a += ws.cta_agg[u].nc;
-    b += ws.cta_agg[u].r;
+    a += ws.cta_agg[(uint64_t)ns * u + k].nc;
+    b += ws.cta_agg[(uint64_t)ns * u + k].r;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -358,8 +448,8 @@ struct TileRates {
   uint32_t e0, e1;    // exclusive prefixes before blocks 2l and 2l+1
   int nvt;            // blocks of the tile inside the stream (0 .. 64)
 };
-__device__ __forceinline__ TileRates tile_rates(const SStage& sg, int ti, uint64_t tile,
-                                                uint64_t nb) {
+template <class St>
+__device__ __forceinline__ TileRates tile_rates(const St& sg, int ti, uint64_t tile, uint64_t nb) {
   const int lane = threadIdx.x & 31;
   TileRates tr;
   const uint64_t first = tile * TILE;

@@ -3,6 +3,7 @@
 //   scalar multiplication through the quantized integers (workflow 3),
 //   element-wise addition through the decoded deltas (workflow 2).
 #include "hz_scalar.cuh"
+#include "hz_super.cuh"
 #include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
@@ -362,42 +363,42 @@ cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_byt
 // subtraction is the same with the second input's signs inverted (negation
 // flips every sign bit; a zero magnitude stays zero whatever its sign).
 //
-// CTA: two groups of 4 compute warps taking the tiles in turn (thread = one
-// 32-position half of one of the tile's 64 blocks) and a loader warp that
-// bulk-copies both inputs' tiles.
-constexpr int ADD_STAGES = 5;
-constexpr uint32_t ADD_RING = 4096;  // plane-ring words per input (32 KB)
-constexpr int ADD_GROUPS = 2;
-constexpr int ADD_GW = 4;  // warps per group
+// Inputs come through the two-stream super-tile pipeline of hz_super.cuh
+// (4 tiles of A and of B per stage, one loader warp, in-kernel rate prefixes of
+// both streams, no pre-scan launch). CTA: four groups of 4 compute warps;
+// group i takes tile i of every stage (thread = one 32-position half of one of
+// the tile's 64 blocks). Each tile's words go to its workspace slot, whose
+// offset (the words of A and B before the tile) is written for placement.
+constexpr int ADD_NT = 4;        // tiles per stage
+constexpr int ADD_STAGES = 3;
+constexpr uint32_t ADD_RING = 16384;  // plane-ring words (128 KB), A's and B's words of a stage
+constexpr int ADD_TS = 4096;     // tile sums kept per stream
+constexpr int ADD_GW = 4;        // warps per group (one tile)
+constexpr int ADD_GROUPS = ADD_NT;
 constexpr int ADD_NCW = ADD_GROUPS * ADD_GW;
-constexpr int ADD_THREADS = (ADD_NCW + 2) * 32;  // + issuer and preparer warps
-constexpr int ADD_ZW = 2 * 32 + 1;  // zbuf words per block: 32 planes x 2 halves, +1 against conflicts
+constexpr int ADD_THREADS = (ADD_NCW + 1) * 32;  // + loader warp
 
 __device__ __forceinline__ void add_bar(int grp) {
-  if (grp == 0) asm volatile("bar.sync 1, %0;" ::"n"(ADD_GW * 32) : "memory");
-  else asm volatile("bar.sync 2, %0;" ::"n"(ADD_GW * 32) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(ADD_GW * 32) : "memory");
 }
-static_assert(ADD_GROUPS == 2, "add_bar names one barrier per group");
 
 template <bool SUB>
-__global__ void __launch_bounds__(ADD_THREADS, 2) k_add(
+__global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
     const uint8_t* __restrict__ a, uint64_t a_bytes, const uint8_t* __restrict__ b,
-    uint64_t b_bytes, uint8_t* __restrict__ out, uint64_t cap,
-    const unsigned long long* __restrict__ pre_a, const unsigned long long* __restrict__ pre_b,
-    Ws ws) {
+    uint64_t b_bytes, uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
+  using St = SStageT<ADD_NT>;
   extern __shared__ __align__(16) uint8_t dyn[];
-  InStage* ina = reinterpret_cast<InStage*>(dyn);
-  InStage* inb = ina + ADD_STAGES;
-  uint64_t* ringa = reinterpret_cast<uint64_t*>(inb + ADD_STAGES);
-  uint64_t* ringb = ringa + ADD_RING;
-  uint32_t* zbuf = reinterpret_cast<uint32_t*>(ringb + ADD_RING);  // [groups][64][ADD_ZW]
-  __shared__ uint64_t full[ADD_STAGES], ready[ADD_STAGES], empty[ADD_STAGES];
-  __shared__ unsigned long long stage_tile[ADD_STAGES];
+  St* stages = reinterpret_cast<St*>(dyn);  // [2][ADD_STAGES]: A's, then B's
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + 2 * ADD_STAGES);
+  __shared__ uint64_t full[ADD_STAGES], empty[ADD_STAGES];
+  __shared__ unsigned long long stage_st[ADD_STAGES];
+  __shared__ uint32_t s_ts[2 * ADD_TS];
   __shared__ uint8_t srate[ADD_GROUPS][2][TILE];
   __shared__ int s_ok;
   const int tid = threadIdx.x, w = tid >> 5;
   const Info ha = parse_header(a, a_bytes);
   const Info hb = parse_header(b, b_bytes);
+  const unsigned long long epoch = launch_epoch(ws);
   int bad = 0;
   if (tid == 0) {
     int ok = 0;
@@ -415,98 +416,92 @@ __global__ void __launch_bounds__(ADD_THREADS, 2) k_add(
       write_template(ha, ok ? ha.qbound + hb.qbound : 0, ws);
       if (ok) atomicMax(&ws.totals[2], (unsigned long long)(ha.qbound + hb.qbound));
     }
+    for (int k = 0; k < ADD_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], ADD_NCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // full: one arrival per stream; empty: the 4 warps of the group that took the stage
-  ring_init3<ADD_STAGES, 2, ADD_GW>(full, ready, empty);
-  const uint64_t ntiles =
-      (s_ok && prescan_ok(ha, pre_a, ws.max_tiles) && prescan_ok(hb, pre_b, ws.max_tiles))
-          ? ntiles_of(ha.nb)
-          : 0;
-  if (w >= ADD_NCW) {
-    const uint64_t G = gridDim.x;
-    __shared__ ulonglong2 s_wina[32][2], s_winb[32][2];
-    PreWindow pwa, pwb;
-    pwa.init(s_wina);
-    pwb.init(s_winb);
-    __shared__ uint32_t s_bega[ADD_STAGES], s_begb[ADD_STAGES];
-    PlaneRing<ADD_STAGES, ADD_RING> pra, prb;
-    pra.init(ringa, s_bega);
-    prb.init(ringb, s_begb);
-    loader_warps<ADD_STAGES, 2, ADD_GROUPS>(
-        w - ADD_NCW, stage_tile, full, ready, empty, ntiles, ws.status,
-        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
-            auto&& release_one) {
-          unsigned long long pa[4], pb[4];
-          pwa.get(pre_a, k, blockIdx.x, G, ntiles, pa);
-          pwb.get(pre_b, k, blockIdx.x, G, ntiles, pb);
-          const TileSpan spa = tile_span(ha, t, pa), spb = tile_span(hb, t, pb);
-          // room in both rings (releases only add room, so A's stays valid)
-          const uint32_t p0a = pra.reserve(k, spa.plane_words(), k_rel, release_one);
-          const uint32_t p0b = prb.reserve(k, spb.plane_words(), k_rel, release_one);
-          const uint32_t ata = pra.commit(k, p0a, spa.plane_words());
-          const uint32_t atb = prb.commit(k, p0b, spb.plane_words());
-          if ((tid & 31) == 0) {
-            issue_in_tile(&ina[sk], &full[sk], a, ha, t, spa, ringa, ata);
-            issue_in_tile(&inb[sk], &full[sk], b, hb, t, spb, ringb, atb);
-          }
-        },
-        [&](int sk, unsigned long long t) {
-          prepare_tile(ina[sk], t, ha);
-          prepare_tile(inb[sk], t, hb);
-        });
-  } else {
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  const uint64_t ntiles = ok ? ntiles_of(ha.nb) : 0;
+  const uint64_t nst = nsuper_of<ADD_NT>(ntiles);
+  const uint8_t* cs[2] = {a, b};
+  const Info hs[2] = {ha, hb};
+  const SRange rg = range_sums_n<ADD_NT, 2>(cs, hs, ntiles, nst, s_ts, ADD_TS, ws, epoch, bad);
+  __syncthreads();
+  if (w == ADD_NCW) {
+    __shared__ uint32_t s_beg[ADD_STAGES];
+    super_loader_n<ADD_NT, 2, ADD_STAGES, ADD_RING, 1>(stages, ring, s_beg, full, empty, stage_st,
+                                                        cs, hs, rg, s_ts, ADD_TS, ws, epoch);
+  } else if (w < ADD_NCW) {
     const int grp = tid / (ADD_GW * 32), lt = tid % (ADD_GW * 32);
     const int g = lt >> 1, hf = lt & 1;  // block of the tile, half (positions 32hf..32hf+31)
-    uint32_t* zb = zbuf + (grp * TILE + g) * ADD_ZW + hf;  // plane p at zb[2p]
     for (uint64_t k = 0;; k++) {
-      const uint64_t u = k * ADD_GROUPS + grp;  // stage use taken by this group
-      const int st = (int)(u % ADD_STAGES);
-      mbar_wait(&ready[st], (uint32_t)((u / ADD_STAGES) & 1), ws.status);
-      const unsigned long long tile = stage_tile[st];
-      if (tile >= ntiles) break;
-      const InStage& sa = ina[st];
-      const InStage& sb = inb[st];
-      const int ra = sa.rate[g], rb = sb.rate[g];
-      const uint32_t offa = sa.off[g], offb = sb.off[g];
-      const uint32_t* pa =
-          reinterpret_cast<const uint32_t*>(ringa + sa.pring + sa.pbase + (offa & 0xffffu)) + hf;
-      const uint32_t* pb =
-          reinterpret_cast<const uint32_t*>(ringb + sb.pring + sb.pbase + (offb & 0xffffu)) + hf;
+      const int st = (int)(k % ADD_STAGES);
+      mbar_wait(&full[st], (uint32_t)((k / ADD_STAGES) & 1), ws.status);
+      const unsigned long long s = stage_st[st];
+      if (s == ~0ull) break;
+      const St& sa = stages[st];
+      const St& sb = stages[ADD_STAGES + st];
+      const uint64_t tile = (uint64_t)ADD_NT * s + grp;
+      const TileRates tra = tile_rates(sa, grp, tile, ha.nb);
+      const TileRates trb = tile_rates(sb, grp, tile, hb.nb);
+      uint32_t ra, exa, rb, exb;
+      tile_block(tra, g, ra, exa);
+      tile_block(trb, g, rb, exb);
+      const uint32_t* pa = reinterpret_cast<const uint32_t*>(ring + sa.pring + sa.pbase +
+                                                             sa.tr[grp] + (exa & 0xffffu)) + hf;
+      const uint32_t* pb = reinterpret_cast<const uint32_t*>(ring + sb.pring + sb.pbase +
+                                                             sb.tr[grp] + (exb & 0xffffu)) + hf;
       const uint32_t siga =
-          ra ? reinterpret_cast<const uint32_t*>(sa.sign + sa.sbase + (offa >> 16))[hf] : 0u;
+          ra ? reinterpret_cast<const uint32_t*>(sa.sign + sa.sbase + sa.tnc[grp] + (exa >> 16))[hf]
+             : 0u;
       uint32_t sigb =
-          rb ? reinterpret_cast<const uint32_t*>(sb.sign + sb.sbase + (offb >> 16))[hf] : 0u;
+          rb ? reinterpret_cast<const uint32_t*>(sb.sign + sb.sbase + sb.tnc[grp] + (exb >> 16))[hf]
+             : 0u;
       if (SUB) sigb = ~sigb;
-      const int oa = sa.outlier[g], ob = sb.outlier[g];
-      const int m = max(ra, rb);
-      // pass 1: z = (mA ^ sA) + sA + (mB ^ sB) + sB, planes 0 .. m+1
-      uint32_t ca = siga, cb = sigb, cz = 0u, z = 0u;
-      if (m > 0) {
-#pragma unroll 4
-        for (int p = 0; p <= m + 1; p++) {
-          const uint32_t xa = (p < ra ? pa[2 * p] : 0u) ^ siga;
-          const uint32_t xb = (p < rb ? pb[2 * p] : 0u) ^ sigb;
+      const int oa = sa.outlier[TILE * grp + g], ob = sb.outlier[TILE * grp + g];
+      // slot of this tile: the words of A and B before it
+      const uint64_t so = sa.bnc + sa.tnc[grp] + sa.br + sa.tr[grp] + sb.bnc + sb.tnc[grp] + sb.br +
+                          sb.tr[grp];
+      const int nvt = tra.nvt;
+      const int m = max((int)ra, (int)rb);
+      // planes 0 .. P of the two's-complement sum, P = the warp's largest m + 1
+      // (|delta_A + delta_B| < 2^(m+1), so plane m+1 and above are the sign;
+      // a thread whose own m is smaller just sign-extends further). Fully
+      // unrolled over P so the planes live in registers and every load of the
+      // block is issued at once.
+      const int P = (int)__reduce_max_sync(0xffffffffu, (unsigned)(m > 0 ? m + 1 : 0));
+      uint32_t z[MAX_RATE + 2];
+      uint32_t sgn = 0u, nzp = 0u;
+      if (P > 0) {
+        uint32_t ca = siga, cb = sigb, cz = 0u;
+#pragma unroll
+        for (int p = 0; p <= MAX_RATE + 1; p++) {
+          if (p > P) break;
+          const uint32_t xa = (p < (int)ra ? pa[2 * p] : 0u) ^ siga;
+          const uint32_t xb = (p < (int)rb ? pb[2 * p] : 0u) ^ sigb;
           const uint32_t x = xa ^ ca, y = xb ^ cb;
           ca &= xa;
           cb &= xb;
-          z = x ^ y ^ cz;
+          z[p] = x ^ y ^ cz;
           cz = (x & y) | (cz & (x ^ y));
-          if (p <= m) zb[2 * p] = z;  // plane m+1 (the sign) stays in z
+          sgn = z[p];  // the last plane computed, P, is the sign
         }
       }
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[st]);
-      // pass 2: sign = top plane; magnitude = (z ^ s) + s, planes 0 .. m
-      const uint32_t sgn = z;  // plane m+1 (0 when both blocks are constant)
-      uint32_t cu = sgn, nzp = 0u;
-      if (m > 0) {
-#pragma unroll 4
-        for (int p = 0; p <= m; p++) {
-          const uint32_t t = zb[2 * p] ^ sgn;
+      // back to sign and magnitude: magnitude = (z ^ s) + s, planes 0 .. P-1
+      if (P > 0) {
+        uint32_t cu = sgn;
+#pragma unroll
+        for (int p = 0; p <= MAX_RATE; p++) {
+          if (p >= P) break;
+          const uint32_t t = z[p] ^ sgn;
           const uint32_t mg = t ^ cu;
           cu &= t;
-          zb[2 * p] = mg;
+          z[p] = mg;
           nzp |= (mg != 0u ? 1u : 0u) << p;
         }
       }
@@ -517,7 +512,7 @@ __global__ void __launch_bounds__(ADD_THREADS, 2) k_add(
         rate = MAX_RATE;
       }
       const uint64_t bi = tile * TILE + g;
-      const bool valid = bi < ha.nb;
+      const bool valid = g < nvt;
       uint8_t* rr = srate[grp][k & 1];
       if (hf == 0) {
         rr[g] = valid ? (uint8_t)rate : 0;
@@ -527,8 +522,8 @@ __global__ void __launch_bounds__(ADD_THREADS, 2) k_add(
         }
       }
       add_bar(grp);
+      if (nvt == 0) continue;  // a tile past the stream's end (group-uniform)
       const TileOff off = warp_tile_offsets(rr, 0, TILE, g, bad);
-      const uint64_t so = slot_offset(SLOT_ADD, tile, pre_a, pre_b, 0);
       if (so + off.agg_nc + off.agg_r > ws.staging_words) {
         bad = HOSZP_ERR_CAPACITY;
         continue;
@@ -537,35 +532,43 @@ __global__ void __launch_bounds__(ADD_THREADS, 2) k_add(
       if (valid && rate > 0) {
         slot[2 * off.nc_excl + hf] = sgn;
         uint32_t* dst = slot + 2 * (off.agg_nc + off.r_excl) + hf;
-#pragma unroll 4
-        for (int p = 0; p < rate; p++) dst[2 * p] = zb[2 * p];
+#pragma unroll
+        for (int p = 0; p <= MAX_RATE; p++) {
+          if (p >= P) break;
+          if (p < rate) dst[2 * p] = z[p];
+        }
       }
-      if (lt == 0) ws.agg[tile] = ((unsigned long long)off.agg_nc << 32) | off.agg_r;
+      if (lt == 0) {
+        ws.agg[tile] = ((unsigned long long)off.agg_nc << 32) | off.agg_r;
+        ws.pre[0][2 * tile] = so;
+      }
     }
   }
   if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && w == 0) {
+    const bool ok_a = range_totals_ok(ws, ha, 0, 2), ok_b = range_totals_ok(ws, hb, 1, 2);
+    if (tid == 0) {
+      if (ok && !(ok_a && ok_b)) set_status(ws.status, HOSZP_ERR_FORMAT);
+      launch_reset(ws);
+    }
+  }
 }
 
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, bool subtract, Ws ws) {
-  cudaError_t e = launch_scan(lc, a, a_bytes, ws.pre[0], ws);
-  if (e != cudaSuccess) return e;
-  e = launch_scan(lc, b, b_bytes, ws.pre[1], ws);
-  if (e != cudaSuccess) return e;
-  const size_t smem = 2 * ADD_STAGES * sizeof(InStage) + 2 * ADD_RING * sizeof(uint64_t) +
-                      ADD_GROUPS * TILE * ADD_ZW * sizeof(uint32_t);
+  const size_t smem = 2 * ADD_STAGES * sizeof(SStageT<ADD_NT>) + ADD_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_add<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_add<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
+  const int grid = subtract ? persistent_grid(k_add<true>, ADD_THREADS, lc.grid, smem)
+                            : persistent_grid(k_add<false>, ADD_THREADS, lc.grid, smem);
   if (subtract)
-    k_add<true><<<persistent_grid(k_add<true>, ADD_THREADS, lc.grid, smem), ADD_THREADS, smem,
-                  lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
+    k_add<true><<<grid, ADD_THREADS, smem, lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws);
   else
-    k_add<false><<<persistent_grid(k_add<false>, ADD_THREADS, lc.grid, smem), ADD_THREADS, smem,
-                   lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws.pre[0], ws.pre[1], ws);
+    k_add<false><<<grid, ADD_THREADS, smem, lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws);
   return cudaGetLastError();
 }
 
