@@ -296,6 +296,70 @@ def serving_bench(hz, xa, xb, eps_q, nfields: int, budget: int, rates, per_rate:
     return out
 
 
+# ---------------------------------------------------------------- batched
+def batched_bench(hz, xa, xb, nfields: int, seed: int = 3, reps: int = 5):
+    """One snapshot of `nfields` uneven fields (sizes log-uniform in 1e4..1e7
+    values, relative bounds log-uniform in 1e-5..1e-2; each a slice of field A
+    or B at a seeded offset), compressed and kept resident. Times the batched
+    mean and variance (one launch each over every field) against the same
+    reductions called field by field, and checks that both give the same
+    doubles."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    n_all = xa.numel()
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e7), nfields)).astype(np.int64)
+    rels = np.exp(rng.uniform(np.log(1e-5), np.log(1e-2), nfields))
+    cap = hz.compress_bound(int(sizes.max()))
+    buf = torch.empty(cap, dtype=torch.uint8, device=xa.device)
+    size = torch.zeros(1, dtype=torch.int64, device=xa.device)
+    streams = []
+    for i in range(nfields):
+        base = xa if i % 2 == 0 else xb
+        n = int(sizes[i])
+        off = int(rng.integers(0, (n_all - n) // 4)) * 4
+        hz.compress(base[off:off + n], eb=float(rels[i]), mode="rel", out=buf, out_bytes=size,
+                    sync=False)
+        streams.append(buf[: int(size.item())].clone())
+    del buf
+    b = hz.Batch(streams)
+    cbytes = sum(c.numel() for c in streams)
+    orig = 4 * int(sizes.sum())
+    out = {"fields": nfields, "values": int(sizes.sum()), "compressed_gb": cbytes / 1e9}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    res = torch.empty(nfields, dtype=torch.float64, device=xa.device)
+    per = torch.empty(nfields, dtype=torch.float64, device=xa.device)
+    for name, bfn, sfn in (("mean", b.mean, hz.mean), ("var", b.var, hz.var)):
+        bfn(out=res, sync=False)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            bfn(out=res, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / reps
+        for i, c in enumerate(streams):  # warm the per-field path
+            sfn(c, out=per[i:i + 1], sync=False)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for i, c in enumerate(streams):
+            sfn(c, out=per[i:i + 1], sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1)
+        b.check(name)
+        out[name] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
+                     "batched_orig_gbs": orig / bms / 1e6,
+                     "batched_frac_of_measured_hbm": cbytes / bms / 1e6 / measured_peak()[0],
+                     "identical_to_per_field": bool(torch.equal(res, per))}
+    b.close()
+    del streams
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -307,6 +371,8 @@ def main():
                     help="values per field in the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched measurement")
+    ap.add_argument("--batch-fields", type=int, default=4096)
     ap.add_argument("--serve-fields", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered rate")
     ap.add_argument("--shape", type=int, nargs=3, default=list(DEFAULT_SHAPE),
@@ -570,6 +636,10 @@ def main():
             dist.destroy_process_group()
         return
 
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = batched_bench(hz, xa, xb, args.batch_fields)
+
     serving = None
     if world == 1 and not args.no_serving:
         del tmp1, tmp2, tmp3, outb
@@ -592,7 +662,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
             "compressed_bytes": C, "per_op": per_op, "decompress_op_recompress": base,
-            "serving": serving}
+            "batched": batched, "serving": serving}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
