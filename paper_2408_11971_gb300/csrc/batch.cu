@@ -21,6 +21,7 @@
 
 #include "hz_moments.cuh"
 #include "hz_scalar.cuh"
+#include "hz_super.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -242,6 +243,266 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_bmoments(
   }
 }
 
+// ---------------------------------------------------------------- batched reductions on super-tiles
+// The same per-field accumulators as k_bmoments, fed by the super-tile
+// pipeline of the single-stream reductions: a stage holds up to STILES
+// consecutive tiles of one field (a stage never spans two fields), copied
+// with four bulk copies and located by the plan's per-field prefixes; the
+// consumer warps run the single-stream mean (bit-sliced column sums) or
+// variance (octet decode) on their tile and flush a field's sums when their
+// next stage belongs to another field.
+constexpr int BS_STAGES = 4;
+constexpr uint32_t BS_RING = 22528;  // plane-ring words (176 KB)
+constexpr int BS_GW = STILES;        // warps per group: one per tile of a stage
+constexpr int BS_GROUPS = 2;
+constexpr int BS_NCW = BS_GW * BS_GROUPS;
+constexpr int BS_THREADS = (BS_NCW + 1) * 32;
+
+struct BStageMeta {
+  uint32_t f, nt;   // field, tiles in the stage (0: end of the walk)
+  uint64_t t0;      // first tile of the stage, local to the field
+};
+
+// Byte ranges of local tiles [t0, t0 + nt) of a stream, from its prefixes at
+// t0 (pv0) and at t0 + nt (pv1).
+__device__ __forceinline__ SSpan tile_range_span(const Info& h, uint64_t t0, uint32_t nt,
+                                                 ulonglong2 pv0, ulonglong2 pv1) {
+  SSpan sp;
+  const uint64_t b0 = (uint64_t)TILE * t0;
+  const uint64_t rate_end = align16(h.nb), out_end = align16(4 * h.nb);
+  sp.rb = (unsigned)umin64((uint64_t)TILE * nt, rate_end - b0);
+  sp.ob = (unsigned)umin64(4ull * TILE * nt, out_end - 4 * b0);
+  const uint64_t sa = h.o_sign + 8 * pv0.x, se = h.o_sign + 8 * pv1.x;
+  const uint64_t pa = h.o_plane + 8 * pv0.y, pe = h.o_plane + 8 * pv1.y;
+  sp.sa16 = sa & ~15ull;
+  sp.pa16 = pa & ~15ull;
+  sp.sbytes = (pv1.x > pv0.x) ? (unsigned)(align16(se) - sp.sa16) : 0u;
+  sp.pbytes = (pv1.y > pv0.y) ? (unsigned)(align16(pe) - sp.pa16) : 0u;
+  if (sp.pbytes > 8u * STILE_PLANE_WORDS_MAX) sp.pbytes = 8u * STILE_PLANE_WORDS_MAX;
+  if (sp.sbytes > 8u * (STB + 2)) sp.sbytes = 8u * (STB + 2);
+  sp.sbase = (uint32_t)((sa - sp.sa16) >> 3);
+  sp.pbase = (uint32_t)((pa - sp.pa16) >> 3);
+  return sp;
+}
+
+// Adds a warp's sums of field f to the field's accumulators; the warp whose
+// tiles complete the field finishes it (lane 0 holds s1 / s2 after the warp
+// reduction inside).
+template <bool VAR>
+__device__ __forceinline__ void bflush(const BField* F, uint32_t f, __int128 s1, U128 s2,
+                                       unsigned int cnt, unsigned long long* acc,
+                                       unsigned int* done, double* results) {
+  s1 = warp_sum_i128(s1);
+  if (VAR) s2 = warp_sum_u128(s2);
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    unsigned long long* a = acc + 4 * (uint64_t)f;
+    atomic_add_u128(a, (unsigned long long)s1, (unsigned long long)((unsigned __int128)s1 >> 64));
+    if (VAR) atomic_add_u128(a + 2, s2.lo, s2.hi);
+    __threadfence();
+    const unsigned int need = (unsigned int)F[f].ntiles;
+    const unsigned int prev = atomicAdd(&done[f], cnt);
+    if (prev + cnt == need) {  // this warp completes the field
+      __threadfence();
+      const volatile unsigned long long* va = a;
+      const __int128 S1 = (__int128)(((unsigned __int128)va[1] << 64) | va[0]);
+      U128 S2 = {va[2], va[3]};
+      const Info& h = F[f].h;
+      results[f] = moment_finish(S1, S2, h.n, h.eps_q, VAR);
+      a[0] = a[1] = a[2] = a[3] = 0;
+      done[f] = 0;
+    }
+  }
+}
+
+template <bool VAR>
+__global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
+    const BField* __restrict__ F, uint32_t nf, uint64_t total_tiles,
+    const unsigned long long* __restrict__ pre, unsigned long long* acc, unsigned int* done,
+    double* results, int* status) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  SStage* stages = reinterpret_cast<SStage*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + BS_STAGES);
+  __shared__ uint64_t full[BS_STAGES], empty[BS_STAGES];
+  __shared__ BStageMeta s_meta[BS_STAGES];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const uint64_t G = gridDim.x;
+  const uint64_t t_begin = total_tiles * blockIdx.x / G;
+  const uint64_t t_end = total_tiles * (blockIdx.x + 1) / G;
+  if (tid == 0) {
+    for (int k = 0; k < BS_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], BS_GW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (w == BS_NCW) {
+    __shared__ uint32_t s_beg[BS_STAGES];
+    PlaneRing<BS_STAGES, BS_RING> pr;
+    pr.init(ring, s_beg);
+    uint32_t k_rel = 0;
+    auto release_one = [&]() {
+      mbar_wait(&empty[k_rel % BS_STAGES], (k_rel / BS_STAGES) & 1, status);
+      k_rel++;
+    };
+    Walk wk;
+    wk.f = ~0u;
+    uint64_t t = t_begin;
+    int ends = 0;
+    for (uint32_t k = 0; ends < BS_GROUPS; k++) {
+      const int sk = (int)(k % BS_STAGES);
+      while (k_rel + BS_STAGES <= k) release_one();
+      if (t >= t_end) {
+        if (lane == 0) {
+          s_meta[sk].nt = 0;
+          mbar_arrive(&full[sk]);
+        }
+        ends++;
+        __syncwarp();
+        continue;
+      }
+      wk.to_tile(F, nf, t);
+      const uint64_t lt = t - wk.tile0;
+      const uint32_t nt = (uint32_t)umin64(umin64(STILES, wk.ntiles - lt), t_end - t);
+      // the stream's prefixes at the stage's tile boundaries (lanes 0 .. nt)
+      ulonglong2 pv = make_ulonglong2(0, 0);
+      if (lane <= (int)nt)
+        pv = __ldg(reinterpret_cast<const ulonglong2*>(pre + wk.pre0 + 2 * (lt + lane)));
+      const ulonglong2 pv0 = make_ulonglong2(__shfl_sync(0xffffffffu, pv.x, 0),
+                                             __shfl_sync(0xffffffffu, pv.y, 0));
+      const ulonglong2 pv1 = make_ulonglong2(__shfl_sync(0xffffffffu, pv.x, nt),
+                                             __shfl_sync(0xffffffffu, pv.y, nt));
+      const SSpan sp = tile_range_span(wk.h, lt, nt, pv0, pv1);
+      const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
+      const uint32_t at = pr.commit(k, p0, sp.plane_words());
+      SStage* sg = &stages[sk];
+      if (lane < (int)nt) {
+        sg->tnc[lane] = (uint32_t)(pv.x - pv0.x);
+        sg->tr[lane] = (uint32_t)(pv.y - pv0.y);
+      }
+      __syncwarp();  // the tile bases are ordered before lane 0's arrival on full[]
+      if (lane == 0) {
+        s_meta[sk].f = wk.f;
+        s_meta[sk].nt = nt;
+        s_meta[sk].t0 = lt;
+        sg->sbase = sp.sbase;
+        sg->pbase = sp.pbase;
+        sg->pring = at;
+        fence_proxy_async();
+        mbar_expect_tx(&full[sk], sp.rb + sp.ob + sp.sbytes + sp.pbytes);
+        const uint64_t b0 = (uint64_t)TILE * lt;
+        bulk_g2s(sg->rate, wk.c + HOSZP_HEADER_BYTES + b0, sp.rb, &full[sk]);
+        bulk_g2s(sg->outlier, wk.c + wk.h.o_out + 4 * b0, sp.ob, &full[sk]);
+        if (sp.sbytes) bulk_g2s(sg->sign, wk.c + sp.sa16, sp.sbytes, &full[sk]);
+        if (sp.pbytes) bulk_g2s(ring + at, wk.c + sp.pa16, sp.pbytes, &full[sk]);
+      }
+      __syncwarp();
+      t += nt;
+    }
+  } else if (w < BS_NCW) {
+    const int grp = w / BS_GW, ti = w % BS_GW;
+    const int j = lane & 7, gq = lane >> 3;
+    const OctetSel S = octet_sel(j);
+    MeanAcc A;
+    A.init();
+    long long v1 = 0;
+    U128 v2 = {0, 0};
+    uint32_t cur = ~0u;
+    unsigned int cnt = 0;
+    auto flush = [&]() {
+      if (VAR) {
+        bflush<true>(F, cur, (__int128)v1, v2, cnt, acc, done, results);
+        v1 = 0;
+        v2 = {0, 0};
+      } else {
+        A.flush();
+        bflush<false>(F, cur, A.s1, U128{0, 0}, cnt, acc, done, results);
+        A.s1 = 0;
+      }
+      cnt = 0;
+    };
+    for (uint64_t k = 0;; k++) {
+      const uint64_t u = k * BS_GROUPS + grp;  // stage use taken by this group
+      const int sk = (int)(u % BS_STAGES);
+      mbar_wait(&full[sk], (uint32_t)((u / BS_STAGES) & 1), status);
+      const BStageMeta meta = s_meta[sk];
+      if (meta.nt == 0) break;
+      if (meta.f != cur) {
+        if (cur != ~0u) flush();
+        cur = meta.f;
+      }
+      if (ti < (int)meta.nt) {  // warp-uniform
+        const SStage& sg = stages[sk];
+        const Info& h = F[cur].h;
+        const uint64_t tile = meta.t0 + ti;
+        const uint64_t ntiles = F[cur].ntiles;
+        const int lastlen = (int)(h.n - (h.nb - 1) * L);
+        const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+        const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
+        const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
+        if (!VAR) {
+#pragma unroll 1
+          for (int jj = 0; jj < 2; jj++) {  // blocks 2 lane and 2 lane + 1
+            const int b = 2 * lane + jj;
+            const uint32_t r = jj ? tr.r1 : tr.r0, ex = jj ? tr.e1 : tr.e0;
+            const int len = (b < tr.nvt - 1) ? L
+                            : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+            const int O = sg.outlier[TILE * ti + b];
+            const uint64_t sw = r ? sgn[ex >> 16] : 0ull;
+            mean_block((int)r, len, O, sw, reinterpret_cast<const uint2*>(pls + (ex & 0xffffu)), A);
+          }
+        } else {
+          const int steps = (tr.nvt + 3) >> 2;
+          for (int it = 0; it < steps; it++) {
+            const int b = 4 * it + gq;
+            uint32_t r, ex;
+            tile_block(tr, b, r, ex);
+            BlockRef br;
+            br.rate = (int)r;
+            br.outlier = sg.outlier[TILE * ti + b];
+            br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+            br.planes = pls + (ex & 0xffffu);
+            br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
+            const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+            int d[8], q[8];
+            octet_deltas(br, kmax, j, S, d);
+            octet_values(br, d, j, q);
+            long long a = 0;
+            unsigned long long b2 = 0;
+#pragma unroll
+            for (int t2 = 0; t2 < 8; t2++) {
+              const int qq = (8 * j + t2 < br.len) ? q[t2] : 0;
+              a += qq;
+              b2 += (unsigned long long)((long long)qq * qq);
+            }
+            v1 += a;
+            add_u64(v2, b2);
+          }
+        }
+        cnt++;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+    if (cur != ~0u) flush();
+  }
+}
+
+template <bool VAR>
+cudaError_t launch_bsuper(int num_sms, cudaStream_t s, const BField* F, uint32_t nf,
+                          uint64_t total_tiles, const unsigned long long* pre,
+                          unsigned long long* acc, unsigned int* done, double* results,
+                          int* status) {
+  const size_t smem = BS_STAGES * sizeof(SStage) + BS_RING * sizeof(uint64_t);
+  static std::once_flag once;
+  std::call_once(once, [&]() {
+    cudaFuncSetAttribute(k_bsuper<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  k_bsuper<VAR><<<persistent_grid(k_bsuper<VAR>, BS_THREADS, num_sms, smem), BS_THREADS, smem, s>>>(
+      F, nf, total_tiles, pre, acc, done, results, status);
+  return cudaGetLastError();
+}
+
 template <bool VAR, int STAGES>
 cudaError_t launch_bmoments(int grid, cudaStream_t s, const BField* F, uint32_t nf,
                             uint64_t total_tiles, const unsigned long long* pre,
@@ -362,8 +623,8 @@ using namespace hz;
 
 // Autotuned launch shape of one reduction: pipeline depth (variant) and CTAs per SM.
 struct BatchCfg {
-  int variant;  // 0: 8 stages, 1: 4 stages
-  int cps;      // CTAs per SM (1 or 2)
+  int variant;  // 0: tile pipeline, 8 stages; 1: tile pipeline, 4 stages; 2: super-tile pipeline
+  int cps;      // CTAs per SM (1 or 2; the super-tile pipeline takes one)
 };
 
 struct hoszp_batch {
@@ -386,7 +647,12 @@ int run_moments(hoszp_batch* b, bool var, const BatchCfg& c, double* d_results,
                 cudaStream_t s) {
   const int grid = b->num_sms * c.cps;
   cudaError_t e;
-  if (var)
+  if (c.variant == 2)
+    e = var ? launch_bsuper<true>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
+                                  b->d_acc, b->d_done, d_results, b->status)
+            : launch_bsuper<false>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
+                                   b->d_acc, b->d_done, d_results, b->status);
+  else if (var)
     e = c.variant == 0 ? launch_bmoments<true, 8>(grid, s, b->d_fields, b->nf, b->total_tiles,
                                                    b->d_pre, b->d_acc, b->d_done, d_results,
                                                    b->status)
@@ -465,7 +731,7 @@ int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_st
   b->total_tiles = tiles;
   b->total_ch[0] = ch[0];
   b->total_ch[1] = ch[1];
-  b->cfg[0] = b->cfg[1] = BatchCfg{0, 2};
+  b->cfg[0] = b->cfg[1] = BatchCfg{2, 1};
   const size_t fbytes = (nfields * sizeof(BField) + 255) / 256 * 256;
   const size_t pbytes = (pre_words * 8 + 255) / 256 * 256;
   const size_t abytes = (nfields * 32 + 255) / 256 * 256;
@@ -576,7 +842,7 @@ int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
   if (!b || !d_results) return HOSZP_ERR_ARG;
   DeviceGuard guard(b->device);
   const cudaStream_t s = (cudaStream_t)stream;
-  const BatchCfg cands[4] = {{0, 2}, {0, 1}, {1, 2}, {1, 1}};
+  const BatchCfg cands[5] = {{2, 1}, {0, 2}, {0, 1}, {1, 2}, {1, 1}};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return rc_of(cudaErrorUnknown);
@@ -609,7 +875,7 @@ int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
 
 int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm) {
   if (!b || op < 0 || op > 1) return HOSZP_ERR_ARG;
-  if (stages) *stages = b->cfg[op].variant == 0 ? 8 : 4;
+  if (stages) *stages = b->cfg[op].variant == 0 ? 8 : b->cfg[op].variant == 1 ? 4 : BS_STAGES;
   if (ctas_per_sm) *ctas_per_sm = b->cfg[op].cps;
   return HOSZP_OK;
 }
