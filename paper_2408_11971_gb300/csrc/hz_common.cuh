@@ -421,12 +421,13 @@ __device__ __forceinline__ void encode_planes(const uint32_t mag[8], int r, int 
                                               const OctetSel& S) {
   for (int k = 0; k < kmax; k++) {
     const int sh = 8 * k;
-    uint32_t b0 = (mag[0] >> sh) & 0xffu, b1 = (mag[1] >> sh) & 0xffu;
-    uint32_t b2 = (mag[2] >> sh) & 0xffu, b3 = (mag[3] >> sh) & 0xffu;
-    uint32_t b4 = (mag[4] >> sh) & 0xffu, b5 = (mag[5] >> sh) & 0xffu;
-    uint32_t b6 = (mag[6] >> sh) & 0xffu, b7 = (mag[7] >> sh) & 0xffu;
-    uint32_t lo = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-    uint32_t hi = b4 | (b5 << 8) | (b6 << 16) | (b7 << 24);
+    // byte k of each magnitude, gathered with byte permutes: (m0.k, m1.k) then
+    // the two pairs side by side
+    const uint32_t sel = (uint32_t)k | ((uint32_t)(4 + k) << 4);
+    uint32_t lo = __byte_perm(__byte_perm(mag[0], mag[1], sel), __byte_perm(mag[2], mag[3], sel),
+                              0x5410u);
+    uint32_t hi = __byte_perm(__byte_perm(mag[4], mag[5], sel), __byte_perm(mag[6], mag[7], sel),
+                              0x5410u);
     tr8x8_d(lo, hi);             // byte p' = bit 8k+p' of the 8 magnitudes
     byte_transpose8(lo, hi, S);  // lane j: plane word 8k+j
     int p = sh + j;
