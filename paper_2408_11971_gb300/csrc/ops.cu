@@ -20,6 +20,12 @@ struct MulPlan {
   bool fast;
   long long P;
   int sh;
+  // 32-bit path: when sh >= 32 and every |q * rho| < 2^31, t = q * rho fits a
+  // 32-bit integer, t * M + 2^(sh-1) is one wide multiply-add, and the result
+  // is its high word shifted by sh - 32; |q'| < 2^23 then, so no range check
+  bool f32;
+  int rho32, M32, sh2;
+  long long half;
 };
 
 __device__ __forceinline__ MulPlan mul_plan(float e, long long rho, uint32_t qbound) {
@@ -34,7 +40,19 @@ __device__ __forceinline__ MulPlan mul_plan(float e, long long rho, uint32_t qbo
   // |q| <= qbound < 2^30 ; require qbound * |P| < 2^62
   const unsigned __int128 prod = (unsigned __int128)aP * (unsigned __int128)(qbound + 1ull);
   p.fast = p.sh >= 1 && p.sh <= 62 && prod < ((unsigned __int128)1 << 62);
+  const unsigned long long arho = (unsigned long long)(rho < 0 ? -rho : rho);
+  p.f32 = p.fast && p.sh >= 32 && arho * (qbound + 1ull) < (1ull << 31);
+  p.rho32 = (int)rho;
+  p.M32 = (int)p.M;
+  p.sh2 = p.sh - 32;
+  p.half = p.sh >= 1 ? (1ll << (p.sh - 1)) : 0;
   return p;
+}
+
+__device__ __forceinline__ int mul_requant_f32(int q, const MulPlan& p) {
+  const int t = q * p.rho32;
+  const long long v = (long long)t * p.M32 + p.half;  // floor(2e q rho + 1/2) * 2^sh, exact
+  return (int)(v >> 32) >> p.sh2;
 }
 
 __device__ __forceinline__ int mul_requant_fast(int q, const MulPlan& p, bool& ovf) {
@@ -300,7 +318,10 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
         for (int t = 0; t < 8; t++)
           if (8 * j + t >= br.len) q[t] = 0;
       }
-      if (mp.fast) {
+      if (mp.f32) {
+#pragma unroll
+        for (int t = 0; t < 8; t++) q[t] = mul_requant_f32(q[t], mp);
+      } else if (mp.fast) {
 #pragma unroll
         for (int t = 0; t < 8; t++) q[t] = mul_requant_fast(q[t], mp, ovf);
       } else {
