@@ -43,8 +43,8 @@ REL = 1e-4
 DEFAULT_SHAPE = SHAPE
 SCALAR_ADD = 0.5
 SCALAR_MUL = 3.14
-KERNELS_PER_STEP = 21  # compress A: range, compress, scan_agg, place; compress B: compress, scan_agg, place;
-# negate 1; add_scalar 1; mul: scan, mul, scan_agg, place; add: 2 scans, add, scan_agg, place;
+KERNELS_PER_STEP = 19  # compress A: range, compress, scan_agg, place; compress B: compress, scan_agg, place;
+# negate 1; add_scalar 1; mul: scan, mul, scan_agg, place; add: add, scan_agg, place;
 # mean: k_mean; var: k_var; decompress: k_decompress
 
 
