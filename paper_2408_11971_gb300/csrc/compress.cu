@@ -202,22 +202,31 @@ __global__ void __launch_bounds__(CMP_THREADS, 2) k_compress(
       if ((tid & 31) == 0) mbar_arrive(&empty[s]);
       rp.next<CMP_STAGES>();
       int q[8];
+      quantize8(v, Q, q, bad);
+      const bool past_end = i0 + 8 > n;  // only in the stream's last block
+      if (past_end) {
 #pragma unroll
-      for (int t = 0; t < 8; t++) {
-        q[t] = quantize(v[t], Q, bad);
-        if (i0 + t >= n) q[t] = 0;
-        qmax = max(qmax, (uint32_t)abs(q[t]));
+        for (int t = 0; t < 8; t++)
+          if (i0 + t >= n) q[t] = 0;
       }
+#pragma unroll
+      for (int t = 0; t < 8; t++) qmax = max(qmax, (uint32_t)abs(q[t]));
       // Eq. 4 inside the block: delta_i = q_i - q_{i-1}, delta_0 := 0 (outlier)
       const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
+      int d[8];
+#pragma unroll
+      for (int t = 0; t < 8; t++) d[t] = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
+      if (past_end) {
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+          if (i0 + t >= n) d[t] = 0;
+      }
       uint32_t mag[8];
       uint32_t sb = 0;
 #pragma unroll
       for (int t = 0; t < 8; t++) {
-        int d = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
-        if (i0 + t >= n) d = 0;
-        mag[t] = (uint32_t)abs(d);
-        sb |= (d < 0 ? 1u : 0u) << t;
+        mag[t] = (uint32_t)abs(d[t]);
+        sb |= (d[t] < 0 ? 1u : 0u) << t;
       }
       const int rate = octet_rate(mag);
       produce_tile(srate, k, tile, nb, mag, sb, rate, q[0], b < nb, g, j, out, ws.staging,

@@ -403,6 +403,33 @@ __device__ __forceinline__ int quantize(float x, const Quant& Q, int& bad) {
   return q;
 }
 
+// Eq. 3 for 8 values. Fast path, taken when it holds for all 8: y = x r +
+// 1.5 2^23 (one rounding) lies in [2^23, 2^24), so k = y - 1.5 2^23 is an
+// integer read off y's bits, and d = x - 2e k (one rounding) has |d| < e.
+// Rounding is monotone and e is a float, so then the exact |x - 2e k| < e as
+// well: k is the one integer with (x + e) / 2e in (k, k + 1), which is Eq. 3's
+// q. Otherwise (a value on or near a cell edge, a large or non-finite x)
+// quantize() settles all 8 exactly. Either way q is the exact Eq. 3 value.
+__device__ __forceinline__ void quantize8(const float v[8], const Quant& Q, int q[8], int& bad) {
+  const float MAGIC = 12582912.0f;  // 1.5 * 2^23
+  uint32_t span = 0;
+  bool inside = true;
+#pragma unroll
+  for (int t = 0; t < 8; t++) {
+    const float y = __fmaf_rn(v[t], Q.r, MAGIC);
+    const uint32_t yb = __float_as_uint(y);
+    span |= yb ^ 0x4B000000u;  // < 2^23 iff y in [2^23, 2^24)
+    const float kf = __fsub_rn(y, MAGIC);
+    const float d = __fmaf_rn(-kf, Q.e2, v[t]);
+    inside = inside && (fabsf(d) < Q.e);
+    q[t] = (int)yb - 0x4B400000;
+  }
+  if (span >= 0x800000u || !inside) {
+#pragma unroll
+    for (int t = 0; t < 8; t++) q[t] = quantize(v[t], Q, bad);
+  }
+}
+
 // x' = float(q) * 2e (reverse quantization). For |q| < 2^22 the conversion is
 // done with the magic-number trick (FP32 pipe), otherwise with I2F.
 __device__ __forceinline__ float dequant_small(int q, float e2) {
@@ -416,23 +443,31 @@ __device__ __forceinline__ float dequant_any(int q, float e2) {
 // ---------------------------------------------------------------- octet codec
 // Encode: lane j holds magnitudes of its 8 positions; writes plane words
 // 8k+j (< r) of the block to planes_out. kmax warp-uniform >= ceil(r/8).
-__device__ __forceinline__ void encode_planes(const uint32_t mag[8], int r, int kmax, int j,
-                                              uint64_t* planes_out, uint64_t limit_words,
-                                              const OctetSel& S) {
-  for (int k = 0; k < kmax; k++) {
-    const int sh = 8 * k;
+template <int K>
+__device__ __forceinline__ void encode_groups(const uint32_t mag[8], int r, int j,
+                                              uint64_t* planes_out, const OctetSel& S) {
+#pragma unroll
+  for (int k = 0; k < K; k++) {
     // byte k of each magnitude, gathered with byte permutes: (m0.k, m1.k) then
     // the two pairs side by side
-    const uint32_t sel = (uint32_t)k | ((uint32_t)(4 + k) << 4);
+    const uint32_t sel = (uint32_t)k | ((4u + (uint32_t)k) << 4);
     uint32_t lo = __byte_perm(__byte_perm(mag[0], mag[1], sel), __byte_perm(mag[2], mag[3], sel),
                               0x5410u);
     uint32_t hi = __byte_perm(__byte_perm(mag[4], mag[5], sel), __byte_perm(mag[6], mag[7], sel),
                               0x5410u);
     tr8x8_d(lo, hi);             // byte p' = bit 8k+p' of the 8 magnitudes
     byte_transpose8(lo, hi, S);  // lane j: plane word 8k+j
-    int p = sh + j;
-    if (p < r && (uint64_t)p < limit_words)
-      planes_out[p] = ((uint64_t)hi << 32) | lo;
+    const int p = 8 * k + j;
+    if (p < r) planes_out[p] = ((uint64_t)hi << 32) | lo;
+  }
+}
+__device__ __forceinline__ void encode_planes(const uint32_t mag[8], int r, int kmax, int j,
+                                              uint64_t* planes_out, const OctetSel& S) {
+  switch (kmax) {
+    case 1: encode_groups<1>(mag, r, j, planes_out, S); break;
+    case 2: encode_groups<2>(mag, r, j, planes_out, S); break;
+    case 3: encode_groups<3>(mag, r, j, planes_out, S); break;
+    default: encode_groups<4>(mag, r, j, planes_out, S); break;
   }
 }
 

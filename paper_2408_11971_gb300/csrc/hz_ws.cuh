@@ -286,7 +286,7 @@ __device__ __forceinline__ void produce_tile(uint8_t (*srate)[TILE], uint64_t kt
   if (r > 0) reinterpret_cast<uint8_t*>(slot + off.nc_excl)[j] = (uint8_t)sb;
   const int kmax = __reduce_max_sync(0xffffffffu, (r + 7) >> 3);
   if (kmax > 0)
-    encode_planes(mag, r, kmax, j, slot + off.agg_nc + off.r_excl, (uint64_t)r, S);
+    encode_planes(mag, r, kmax, j, slot + off.agg_nc + off.r_excl, S);
   if (threadIdx.x == 0) agg[tile] = ((unsigned long long)off.agg_nc << 32) | off.agg_r;
 }
 

@@ -328,19 +328,23 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
 #pragma unroll
         for (int t = 0; t < 8; t++) q[t] = mul_requant(q[t], mp, ovf);
       }
+      if (br.len < L) {
 #pragma unroll
-      for (int t = 0; t < 8; t++) {
-        if (8 * j + t >= br.len) q[t] = 0;
-        qmax = max(qmax, (uint32_t)abs(q[t]));
+        for (int t = 0; t < 8; t++)
+          if (8 * j + t >= br.len) q[t] = 0;
       }
+#pragma unroll
+      for (int t = 0; t < 8; t++) qmax = max(qmax, (uint32_t)abs(q[t]));
       // Lorenzo on the new integers
       const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
       const int outlier = __shfl_sync(0xffffffffu, q[0], (tid & 31) & ~7);
       int nd[8];
 #pragma unroll
-      for (int t = 0; t < 8; t++) {
-        const int v = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
-        nd[t] = (8 * j + t < br.len) ? v : 0;
+      for (int t = 0; t < 8; t++) nd[t] = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
+      if (br.len < L) {
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+          if (8 * j + t >= br.len) nd[t] = 0;
       }
       uint32_t mag[8], sb;
       octet_mag_sign(nd, mag, sb);
