@@ -75,6 +75,9 @@ def _load():
     lib.orc_add.argtypes = [P, SZ, P, SZ, P, SZ, P]
     lib.orc_sub.argtypes = [P, SZ, P, SZ, P, SZ, P]
     lib.orc_sums.argtypes = [P, SZ, P, P, P, P, P, P]
+    lib.orc_sub_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
+    lib.orc_block_means.argtypes = [P, SZ, P, U64]
+    lib.orc_cov_sums.argtypes = [P, SZ, P, SZ, P, P, P, P, P, P, P]
     lib.orc_header.argtypes = [P, SZ, P, P, P, P, P, P]
     lib.orc_eps_q.argtypes = [ctypes.c_double, P]
     lib.orc_quantize.argtypes = [ctypes.c_float, ctypes.c_float, P]
@@ -201,6 +204,11 @@ def add_scalar(c, s: float) -> np.ndarray:
     return _unary(_load().orc_add_scalar, c, ctypes.c_double(s))
 
 
+def sub_scalar(c, s: float) -> np.ndarray:
+    """Scalar subtraction (Sec. V-A): O' = O - rho_s, rho_s = Eq. 3 of s."""
+    return _unary(_load().orc_sub_scalar, c, ctypes.c_double(s))
+
+
 def mul_scalar(c, s: float) -> np.ndarray:
     return _unary(_load().orc_mul_scalar, c, ctypes.c_double(s))
 
@@ -256,3 +264,45 @@ def var(c) -> float:
         raise OracleError(-1, "var")
     a = 2 * Fraction(float(e))
     return float(a * a * Fraction(n * s2 - s1 * s1, n * n))
+
+
+def std(c) -> float:
+    """Sec. V-B standard deviation: the square root of the population variance
+    (the variance rounded once to double, then a correctly rounded square root)."""
+    import math
+
+    return math.sqrt(var(c))
+
+
+def block_means(c) -> np.ndarray:
+    """Sec. V-B block-wise means: (S1_b / L_b) * 2 eps_q per block, in FP64."""
+    c = _stream(c)
+    nb = (header(c)["n"] + 63) // 64
+    out = np.zeros(max(nb, 1), np.float64)
+    _check(_load().orc_block_means(_ptr(c), c.size, _ptr(out), nb), "block_means")
+    return out[:nb].copy()
+
+
+def cov_sums(a, b):
+    """Exact (S_AB, S1_A, S1_B, n) of two streams of one length (Sec. V-D)."""
+    a = _stream(a)
+    b = _stream(b)
+    hi = [np.zeros(1, np.int64) for _ in range(3)]
+    lo = [np.zeros(1, np.uint64) for _ in range(3)]
+    n = np.zeros(1, np.uint64)
+    _check(_load().orc_cov_sums(_ptr(a), a.size, _ptr(b), b.size, _ptr(hi[0]), _ptr(lo[0]),
+                                _ptr(hi[1]), _ptr(lo[1]), _ptr(hi[2]), _ptr(lo[2]), _ptr(n)),
+           "cov_sums")
+    sab, s1a, s1b = ((int(h[0]) << 64) + int(l[0]) for h, l in zip(hi, lo))
+    return sab, s1a, s1b, int(n[0])
+
+
+def cov(a, b) -> float:
+    """Sec. V-D population covariance of the dequantized values of two streams,
+    2 eps_A 2 eps_B (n S_AB - S1_A S1_B) / n^2 from exact sums, rounded once."""
+    sab, s1a, s1b, n = cov_sums(a, b)
+    if n == 0:
+        raise OracleError(-1, "cov")
+    ea = 2 * Fraction(float(header(a)["eps_q"]))
+    eb = 2 * Fraction(float(header(b)["eps_q"]))
+    return float(ea * eb * Fraction(n * sab - s1a * s1b, n * n))

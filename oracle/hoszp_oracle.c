@@ -468,6 +468,32 @@ int orc_add_scalar(const uint8_t* c, size_t bytes, double s, uint8_t* out, size_
   return ORC_OK;
 }
 
+/* Scalar subtraction (Sec. V-A "Scalar Subtraction"): the scalar's bin
+ * rho_s (Eq. 3 applied to s) is deducted from every block's outlier,
+ * O' = O - rho_s; the rest of the stream is copied. The result bound is
+ * qbound + |rho_s|. */
+int orc_sub_scalar(const uint8_t* c, size_t bytes, double s, uint8_t* out, size_t cap,
+                   uint64_t* out_bytes) {
+  orc_hdr h;
+  int rc = read_header(c, bytes, &h);
+  if (rc) return rc;
+  int64_t rho;
+  rc = orc_quantize_scalar(s, h.eps_q, &rho);
+  if (rc) return rc == ORC_ERR_ARG ? ORC_ERR_ARG : ORC_ERR_RANGE;
+  int64_t arho = rho < 0 ? -rho : rho;
+  if ((int64_t)h.qbound + arho > ORC_QLIM) return ORC_ERR_OVERFLOW;
+  uint64_t nb = nblocks(h.n), size = stream_size(nb, h.nnc, h.R);
+  if (size > cap) return ORC_ERR_CAPACITY;
+  memmove(out, c, size);
+  for (uint64_t b = 0; b < nb; b++) {
+    int64_t o = (int32_t)(uint32_t)rd_le(out + off_outlier(nb) + 4 * b, 4);
+    wr_le(out + off_outlier(nb) + 4 * b, (uint64_t)(uint32_t)(int32_t)(o - rho), 4);
+  }
+  wr_le(out + 56, (uint64_t)(h.qbound + arho), 4);
+  *out_bytes = size;
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* workflows 2 and 3, written as decode -> integer op -> encode          */
 /* ------------------------------------------------------------------ */
@@ -581,6 +607,69 @@ int orc_sums(const uint8_t* c, size_t bytes, int64_t* s1_hi, uint64_t* s1_lo, ui
   *s2_lo = (uint64_t)s2;
   *n_out = n;
   *eps_q_out = h.eps_q;
+  return ORC_OK;
+}
+
+/* Block-wise means (Sec. V-B "Mean", last sentences): the quantized values
+ * of each block are summed and the sum is divided by the number of values in
+ * the block, then scaled by 2 eps_q: mean_b = (S1_b / L_b) * 2 eps_q in FP64
+ * (S1_b exact, |S1_b| < 2^37; the same two rounded operations as the mean of
+ * the whole stream). out has nb = ceil(n / 64) doubles. */
+int orc_block_means(const uint8_t* c, size_t bytes, double* out, uint64_t nb_out) {
+  orc_hdr h;
+  int rc = read_header(c, bytes, &h);
+  if (rc) return rc;
+  uint64_t n = h.n, nb = nblocks(n);
+  if (nb_out != nb) return ORC_ERR_ARG;
+  int64_t* q = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  if (!q) return ORC_ERR_ARG;
+  decode_q(c, bytes, &h, q);
+  const double e2 = 2.0 * (double)h.eps_q;
+  for (uint64_t b = 0; b < nb; b++) {
+    uint64_t i0 = b * ORC_L, i1 = i0 + ORC_L < n ? i0 + ORC_L : n;
+    int64_t s1 = 0;
+    for (uint64_t i = i0; i < i1; i++) s1 += q[i];
+    out[b] = ((double)s1 / (double)(i1 - i0)) * e2;
+  }
+  free(q);
+  return ORC_OK;
+}
+
+/* The exact sums behind the covariance of two streams of the same length
+ * (Sec. V-D "Covariance", done like the variance of Sec. V-B over two
+ * fields): S_AB = sum q_A q_B (signed 128-bit), S1_A = sum q_A, S1_B = sum q_B.
+ * The population covariance is 2 eps_A 2 eps_B (n S_AB - S1_A S1_B) / n^2.
+ * The two streams may have different error bounds; their lengths must agree. */
+int orc_cov_sums(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_bytes,
+                 int64_t* sab_hi, uint64_t* sab_lo, int64_t* s1a_hi, uint64_t* s1a_lo,
+                 int64_t* s1b_hi, uint64_t* s1b_lo, uint64_t* n_out) {
+  orc_hdr ha, hb;
+  int rc = read_header(a, a_bytes, &ha);
+  if (rc) return rc;
+  rc = read_header(b, b_bytes, &hb);
+  if (rc) return rc;
+  if (ha.n != hb.n) return ORC_ERR_MISMATCH;
+  uint64_t n = ha.n;
+  int64_t* qa = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  int64_t* qb = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  if (!qa || !qb) { free(qa); free(qb); return ORC_ERR_ARG; }
+  decode_q(a, a_bytes, &ha, qa);
+  decode_q(b, b_bytes, &hb, qb);
+  i128 sab = 0, sa = 0, sb = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    sab += (i128)qa[i] * qb[i];
+    sa += qa[i];
+    sb += qb[i];
+  }
+  free(qa);
+  free(qb);
+  *sab_hi = (int64_t)(sab >> 64);
+  *sab_lo = (uint64_t)sab;
+  *s1a_hi = (int64_t)(sa >> 64);
+  *s1a_lo = (uint64_t)sa;
+  *s1b_hi = (int64_t)(sb >> 64);
+  *s1b_lo = (uint64_t)sb;
+  *n_out = n;
   return ORC_OK;
 }
 

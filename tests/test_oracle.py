@@ -399,3 +399,100 @@ def test_errors():
     with pytest.raises(O.OracleError) as ex:
         O.add_scalar(big, 1e9)
     assert ex.value.name in ("RANGE", "OVERFLOW")
+
+
+# ---------------------------------------------------------------- scalar subtraction, std,
+# block-wise means, covariance (Sec. V-A, V-B, V-D)
+def test_sub_scalar(pair):
+    ca, _ = pair
+    e = parse(ca)["eps_q"]
+    q = values(parse(ca))
+    for s in (0.5, -3.25, 0.0, 1e-9, 123.456):
+        rho = bin_search_q(s, e)
+        assert rho == eq3_fraction(s, e)
+        out = O.sub_scalar(ca, s)
+        so = parse(out)
+        assert np.array_equal(values(so), q - rho)  # O' = O - rho_s, deltas untouched
+        assert so["qbound"] == parse(ca)["qbound"] + abs(rho)
+        assert np.array_equal(so["sign"], parse(ca)["sign"])
+        assert np.array_equal(so["plane"], parse(ca)["plane"])
+        # subtracting after adding the same scalar restores every byte but the bound
+        back = O.sub_scalar(O.add_scalar(ca, s), s)
+        assert np.array_equal(np.delete(back, range(56, 60)), np.delete(ca, range(56, 60)))
+
+
+def test_sub_scalar_differs_from_adding_the_negated_scalar_only_at_ties():
+    # Eq. 3 rounds half up: at s = (2k + 1) eps the bins of s and -s are not opposite
+    x = np.array(GOLD["quantize_lorenzo"]["A1"], np.float32)
+    c = O.compress(x, dims=(2, 2), eb=0.01)
+    e = parse(c)["eps_q"]
+    s_tie = float(np.float32(3) * e)  # exactly 3 eps_q
+    assert eq3_fraction(s_tie, e) == 2 and eq3_fraction(-s_tie, e) == -1
+    assert np.array_equal(values(parse(O.sub_scalar(c, s_tie))), values(parse(c)) - 2)
+    assert np.array_equal(values(parse(O.add_scalar(c, -s_tie))), values(parse(c)) - 1)
+    s = 0.3  # not a tie: both readings agree
+    assert np.array_equal(values(parse(O.sub_scalar(c, s))), values(parse(O.add_scalar(c, -s))))
+
+
+def test_std():
+    e = 0.01
+    k = 37
+    x = np.where(np.arange(1000) % 2 == 0, 2 * k * e, -2 * k * e).astype(np.float32)
+    c = O.compress(x, eb=e)
+    q = values(parse(c))
+    assert set(q.tolist()) == {k, -k}
+    ea = Fraction(float(parse(c)["eps_q"]))
+    assert O.std(c) == float(2 * ea * k)  # alternating +-k: std = 2 eps k exactly
+    assert O.std(O.compress(np.full(300, 1.5, np.float32), eb=e)) == 0.0
+    xs = datagen.sines_1d(20_000, seed=5)
+    cs = O.compress(xs, eb=1e-3, mode="rel")
+    assert O.std(cs) ** 2 == pytest.approx(O.var(cs), rel=1e-15)
+    assert O.std(cs) == pytest.approx(float(np.std(O.decompress(cs).astype(np.float64))), rel=1e-6)
+
+
+def test_block_means(pair):
+    ca, _ = pair
+    s = parse(ca)
+    q = values(s)
+    e2 = 2.0 * float(s["eps_q"])
+    bm = O.block_means(ca)
+    nb = (q.size + L - 1) // L
+    assert bm.shape == (nb,) and nb * L > q.size  # the pair has a ragged last block
+    for b in range(nb):
+        blk = [int(v) for v in q[b * L:(b + 1) * L]]
+        assert bm[b] == (float(sum(blk)) / len(blk)) * e2
+    # length-weighted average of the block means is the mean, within rounding
+    w = np.array([min(L, q.size - b * L) for b in range(nb)], np.float64)
+    assert float(np.sum(bm * w) / q.size) == pytest.approx(O.mean(ca), rel=1e-12)
+    # the paper's worked block (Sec. V-B): sum -8 over 4 values, mean -0.04
+    g = GOLD["mean"]
+    c = O.compress(np.array(GOLD["quantize_lorenzo"]["A1"], np.float32), dims=(2, 2), eb=0.01)
+    assert O.block_means(c)[0] == pytest.approx(g["mean"], rel=1e-7)
+
+
+def test_cov(pair):
+    ca, cb = pair
+    qa = [int(v) for v in values(parse(ca))]
+    qb = [int(v) for v in values(parse(cb))]
+    sab, s1a, s1b, n = O.cov_sums(ca, cb)
+    assert (sab, s1a, s1b, n) == (sum(a * b for a, b in zip(qa, qb)), sum(qa), sum(qb), len(qa))
+    ea = 2 * Fraction(float(parse(ca)["eps_q"]))
+    eb = 2 * Fraction(float(parse(cb)["eps_q"]))
+    ma, mb = Fraction(sum(qa), n), Fraction(sum(qb), n)
+    two_pass = sum((a - ma) * (b - mb) for a, b in zip(qa, qb)) / n
+    assert O.cov(ca, cb) == float(ea * eb * two_pass)
+    assert O.cov(ca, cb) == O.cov(cb, ca)
+    assert O.cov(ca, ca) == O.var(ca)  # covariance with itself is the variance
+    assert O.cov(ca, O.negate(ca)) == -O.var(ca)
+    xa = O.decompress(ca).astype(np.float64)
+    xb = O.decompress(cb).astype(np.float64)
+    assert O.cov(ca, cb) == pytest.approx(float(np.cov(xa, xb, bias=True)[0, 1]), rel=1e-6)
+    # different error bounds are allowed: each side scales by its own 2 eps
+    cc = O.compress(datagen.sines_1d(30_011, seed=8), eb=3e-3)
+    qc = [int(v) for v in values(parse(cc))]
+    ec = 2 * Fraction(float(parse(cc)["eps_q"]))
+    mc = Fraction(sum(qc), n)
+    assert O.cov(ca, cc) == float(ea * ec * sum((a - ma) * (c - mc) for a, c in zip(qa, qc)) / n)
+    with pytest.raises(O.OracleError) as ex:
+        O.cov(ca, O.compress(np.ones(101, np.float32), eb=0.1))
+    assert ex.value.name == "MISMATCH"
