@@ -584,6 +584,36 @@ def main():
         base[op] = {"ms": round(tms, 4), "speedup_homomorphic": tms / per_op_ms[op]}
     ctx.check("baseline")
 
+    # operators outside the step (Sec. V-A scalar subtraction, Sec. V-B standard
+    # deviation and block-wise means), each timed alone
+    nbk = (n + 63) // 64
+    bmeans = torch.empty(nbk, dtype=torch.float64, device=dev)
+
+    def xop(op):
+        if op == "sub_scalar":
+            hz.sub_scalar(sa, SCALAR_ADD, out=outb, out_bytes=outs, ctx=ctx, sync=False)
+        elif op == "std":
+            hz.std(sa, out=res[0:1], ctx=ctx, sync=False)
+        elif op == "block_means":
+            hz.block_means(sa, out=bmeans, ctx=ctx, sync=False)
+
+    xalg = {"sub_scalar": 2 * C["ca"], "std": C["ca"], "block_means": C["ca"] + 8 * nbk}
+    extra = {}
+    for op, nbytes in xalg.items():
+        for _ in range(3):
+            xop(op)
+        e0, e1 = ev(), ev()
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            xop(op)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xms = e0.elapsed_time(e1) / reps
+        extra[op] = {"ms": round(xms, 4), "orig_gbs": N4 / xms / 1e6,
+                     "alg_gbs": nbytes / xms / 1e6, "frac_of_measured_hbm": nbytes / xms / 1e6 / peak}
+    ctx.check("operators outside the step")
+
     # roofline of the dominant operator (largest share of the step)
     dom = max(ops, key=lambda o: per_op_ms[o])
     kern_of = {"compress A": "k_compress", "compress B": "k_compress", "negate": "k_meta",
@@ -662,6 +692,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
             "compressed_bytes": C, "per_op": per_op, "decompress_op_recompress": base,
+            "extra_ops": extra,
             "batched": batched, "serving": serving}
     print(json.dumps(line))
     if dist is not None:

@@ -139,6 +139,15 @@ int hoszp_negate(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, void* d_out, s
 int hoszp_add_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
                      size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
 
+/* Scalar subtraction, Sec. V-A "Scalar Subtraction", workflow 1: rho_s = Eq. 3
+ * quantization of s is deducted from every outlier, O' = O - rho_s; rates,
+ * signs and planes are copied. In place allowed. Same arguments and errors as
+ * hoszp_add_scalar; the header bound becomes qbound + |rho_s|. At a tie of
+ * Eq. 3 (s an odd multiple of eps_q) this differs from adding -s, whose bin is
+ * not -rho_s. */
+int hoszp_sub_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
+                     size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
+
 /* Scalar multiplication, Sec. V-A "Scalar Multiplication", workflow 3: decode
  * to q, q' = floor(2 eps_q * q * rho_s + 1/2) (Eq. 3 applied to the product of
  * the dequantized values), then Lorenzo + BF re-encode. Output stream is
@@ -169,6 +178,22 @@ int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result
  * exact integer sums of q and q^2, finished in FP64 into *d_result. */
 int hoszp_var(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
               hoszp_stream_t stream);
+
+/* Standard deviation, Sec. V-B "Standard Deviation": the square root of the
+ * population variance above, taken in FP64 (correctly rounded) after the
+ * same finish, into the device double *d_result. Same errors as hoszp_var. */
+int hoszp_std(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
+              hoszp_stream_t stream);
+
+/* Block-wise means, Sec. V-B "Mean" (its last sentences: the same kernel sums
+ * each block's quantized values and divides by the block's length): d_out
+ * (device, nb doubles, 8-byte aligned) gets mean_b = (S1_b / L_b) * 2 eps_q in
+ * FP64 for every block b, with S1_b the exact sum of the block's q and L_b its
+ * length (64; the last block may be shorter). nb must be the stream's block
+ * count ceil(n / 64) (device status MISMATCH otherwise); nb = 0 writes
+ * nothing. */
+int hoszp_block_means(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_out, uint64_t nb,
+                      hoszp_stream_t stream);
 
 /* The exact integer sums behind mean and variance (Sec. V-B), for combining
  * shards of one field held by several devices or processes: d_sums (device,

@@ -27,11 +27,14 @@ from ._binding import (  # noqa: F401
     decompress,
     negate,
     add_scalar,
+    sub_scalar,
     mul_scalar,
     add,
     sub,
     mean,
     var,
+    std,
+    block_means,
     sums,
     header,
     fop_axpb,
@@ -41,6 +44,6 @@ from ._binding import (  # noqa: F401
 
 __all__ = [
     "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library", "default_context",
-    "compress_bound", "compress", "decompress", "negate", "add_scalar", "mul_scalar", "add", "sub",
-    "mean", "var", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
+    "compress_bound", "compress", "decompress", "negate", "add_scalar", "sub_scalar", "mul_scalar", "add",
+    "sub", "mean", "var", "std", "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

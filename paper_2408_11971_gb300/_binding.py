@@ -73,12 +73,15 @@ def load_library():
             "hoszp_decompress": (I, [P, P, SZ, P, U64, P]),
             "hoszp_negate": (I, [P, P, SZ, P, SZ, P, P]),
             "hoszp_add_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
+            "hoszp_sub_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_mul_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_add": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_sub": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
             "hoszp_sums": (I, [P, P, SZ, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
+            "hoszp_std": (I, [P, P, SZ, P, P]),
+            "hoszp_block_means": (I, [P, P, SZ, P, U64, P]),
             "hoszp_batch_create": (I, [P, ctypes.c_uint32, P, P, ctypes.POINTER(P)]),
             "hoszp_batch_destroy": (None, [P]),
             "hoszp_batch_info": (I, [P, P, P]),
@@ -295,6 +298,13 @@ def add_scalar(c, s: float, out=None, out_bytes=None, inplace: bool = False, str
                   out_bytes, inplace, stream, ctx, sync, check)
 
 
+def sub_scalar(c, s: float, out=None, out_bytes=None, inplace: bool = False, stream=None,
+               ctx=None, sync: bool = True, check: bool = True):
+    """Scalar subtraction in fully compressed space (Sec. V-A): O' = O - rho_s."""
+    return _unary(load_library().hoszp_sub_scalar, "sub_scalar", c, (ctypes.c_double(s),), out,
+                  out_bytes, inplace, stream, ctx, sync, check)
+
+
 def mul_scalar(c, s: float, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
                check: bool = True):
     """Scalar multiplication through the quantized integers (Sec. V-A)."""
@@ -367,6 +377,27 @@ def mean(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = Tr
 def var(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
     """Population variance from exact integer sums (Sec. V-B)."""
     return _moment(load_library().hoszp_var, "var", c, out, stream, ctx, sync, check)
+
+
+def std(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
+    """Standard deviation: square root of the population variance (Sec. V-B)."""
+    return _moment(load_library().hoszp_std, "std", c, out, stream, ctx, sync, check)
+
+
+def block_means(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
+    """Block-wise means (Sec. V-B): a float64 CUDA tensor with one mean per
+    64-value block, (S1_b / L_b) * 2 eps_q."""
+    torch = _torch()
+    c = _stream_tensor(c)
+    ctx = _ctx(ctx, c)
+    nb = (header(c)["n"] + 63) // 64
+    if out is None:
+        out = torch.empty(max(nb, 1), dtype=torch.float64, device=c.device)
+    _check(load_library().hoszp_block_means(ctx.handle, _dev_ptr(c), c.numel(), _dev_ptr(out), nb,
+                                            _stream_ptr(stream)), "block_means")
+    if sync and check:
+        ctx.check("block_means")
+    return out[:nb]
 
 
 # ---------------------------------------------------------------- traditional workflow (float ops)

@@ -303,6 +303,21 @@ int hoszp_add_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
                                    ctx->ws));
 }
 
+int hoszp_sub_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
+                     size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+  if (!ctx || !d_c || !d_out || !d_out_bytes || c_bytes < HOSZP_HEADER_BYTES) return HOSZP_ERR_ARG;
+  if (!std::isfinite(s)) return HOSZP_ERR_ARG;
+  if (!aligned16(d_c) || !aligned16(d_out) || !aligned8(d_out_bytes)) return HOSZP_ERR_ARG;
+  const uint8_t* a = (const uint8_t*)d_c;
+  uint8_t* o = (uint8_t*)d_out;
+  if (o != a && o < a + c_bytes && a < o + cap) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = ensure_ws(ctx, 1, 16);
+  if (rc) return rc;
+  return cuda_rc(launch_sub_scalar(lc_of(ctx, stream), a, c_bytes, s, o, cap, d_out_bytes,
+                                   ctx->ws));
+}
+
 int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
                      size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
   if (!ctx || !d_c || !d_out || !d_out_bytes || c_bytes < HOSZP_HEADER_BYTES) return HOSZP_ERR_ARG;
@@ -359,14 +374,30 @@ int hoszp_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, 
 }
 
 static int moments(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
-                   hoszp_stream_t stream, bool var) {
+                   hoszp_stream_t stream, bool var, bool take_sqrt = false) {
   if (!ctx || !d_c || !d_result || c_bytes < HOSZP_HEADER_BYTES) return HOSZP_ERR_ARG;
   if (!aligned16(d_c) || !aligned8(d_result)) return HOSZP_ERR_ARG;
   DeviceGuard g(ctx->device);
   int rc = ensure_ws(ctx, tiles_from_bytes(c_bytes), 16);
   if (rc) return rc;
-  return cuda_rc(
-      launch_moments(lc_of(ctx, stream), (const uint8_t*)d_c, c_bytes, d_result, var, ctx->ws));
+  return cuda_rc(launch_moments(lc_of(ctx, stream), (const uint8_t*)d_c, c_bytes, d_result, var,
+                                ctx->ws, nullptr, take_sqrt));
+}
+
+int hoszp_std(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
+              hoszp_stream_t stream) {
+  return moments(ctx, d_c, c_bytes, d_result, stream, true, true);
+}
+
+int hoszp_block_means(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_out, uint64_t nb,
+                      hoszp_stream_t stream) {
+  if (!ctx || !d_c || (nb > 0 && !d_out) || c_bytes < HOSZP_HEADER_BYTES) return HOSZP_ERR_ARG;
+  if (!aligned16(d_c) || (nb > 0 && !aligned8(d_out))) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = ensure_ws(ctx, ntiles_of(nb) + 1, 16);
+  if (rc) return rc;
+  return cuda_rc(launch_block_means(lc_of(ctx, stream), (const uint8_t*)d_c, c_bytes, d_out, nb,
+                                    ctx->ws));
 }
 
 int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums,

@@ -22,6 +22,7 @@
 #include "hz_moments.cuh"
 #include "hz_scalar.cuh"
 #include "hz_super.cuh"
+#include "hz_var.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
@@ -341,10 +342,13 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
     PlaneRing<BS_STAGES, BS_RING> pr;
     pr.init(ring, s_beg);
     uint32_t k_rel = 0;
+    bool dead = false;  // a wait gave up: issue nothing more, wait for nothing more
     auto release_one = [&]() {
-      mbar_wait(&empty[k_rel % BS_STAGES], (k_rel / BS_STAGES) & 1, status);
+      if (!dead && !mbar_wait_warp(&empty[k_rel % BS_STAGES], (k_rel / BS_STAGES) & 1, status))
+        dead = true;
       k_rel++;
     };
+    uint32_t k_end = 0;  // stage uses issued so far
     Walk wk;
     wk.f = ~0u;
     uint64_t t = t_begin;
@@ -352,6 +356,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
     for (uint32_t k = 0; ends < BS_GROUPS; k++) {
       const int sk = (int)(k % BS_STAGES);
       while (k_rel + BS_STAGES <= k) release_one();
+      if (dead) break;  // no end markers either: a stage may still be in flight
       if (t >= t_end) {
         if (lane == 0) {
           s_meta[sk].nt = 0;
@@ -374,6 +379,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
                                              __shfl_sync(0xffffffffu, pv.y, nt));
       const SSpan sp = tile_range_span(wk.h, lt, nt, pv0, pv1);
       const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
+      if (dead) break;
       const uint32_t at = pr.commit(k, p0, sp.plane_words());
       SStage* sg = &stages[sk];
       if (lane < (int)nt) {
@@ -398,11 +404,15 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
       }
       __syncwarp();
       t += nt;
+      k_end = k + 1;
     }
+    // after a wait gave up, the copies already issued land before the CTA exits
+    if (dead)
+      for (uint32_t u = k_rel; u < k_end; u++)
+        mbar_wait(&full[u % BS_STAGES], (u / BS_STAGES) & 1, status);
   } else if (w < BS_NCW) {
     const int grp = w / BS_GW, ti = w % BS_GW;
-    const int j = lane & 7, gq = lane >> 3;
-    const OctetSel S = octet_sel(j);
+    const lanes::Shifts K = lanes::make_shifts(nf != 0 ? 1u : 0u);
     MeanAcc A;
     A.init();
     long long v1 = 0;
@@ -424,7 +434,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
     for (uint64_t k = 0;; k++) {
       const uint64_t u = k * BS_GROUPS + grp;  // stage use taken by this group
       const int sk = (int)(u % BS_STAGES);
-      mbar_wait(&full[sk], (uint32_t)((u / BS_STAGES) & 1), status);
+      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / BS_STAGES) & 1), status)) break;
       const BStageMeta meta = s_meta[sk];
       if (meta.nt == 0) break;
       if (meta.f != cur) {
@@ -452,32 +462,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
             mean_block((int)r, len, O, sw, reinterpret_cast<const uint2*>(pls + (ex & 0xffffu)), A);
           }
         } else {
-          const int steps = (tr.nvt + 3) >> 2;
-          for (int it = 0; it < steps; it++) {
-            const int b = 4 * it + gq;
-            uint32_t r, ex;
-            tile_block(tr, b, r, ex);
-            BlockRef br;
-            br.rate = (int)r;
-            br.outlier = sg.outlier[TILE * ti + b];
-            br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
-            br.planes = pls + (ex & 0xffffu);
-            br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
-            const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-            int d[8], q[8];
-            octet_deltas(br, kmax, j, S, d);
-            octet_values(br, d, j, q);
-            long long a = 0;
-            unsigned long long b2 = 0;
-#pragma unroll
-            for (int t2 = 0; t2 < 8; t2++) {
-              const int qq = (8 * j + t2 < br.len) ? q[t2] : 0;
-              a += qq;
-              b2 += (unsigned long long)((long long)qq * qq);
-            }
-            v1 += a;
-            add_u64(v2, b2);
-          }
+          var_tile(sg, ring, ti, tr, tile, ntiles, lastlen, h.qbound < (1u << 13), K, v1, v2);
         }
         cnt++;
       }

@@ -4,121 +4,13 @@
 #include <cfloat>
 
 #include "hz_moments.cuh"
+#include "hz_var.cuh"
 #include "hz_super.cuh"
 #include "hz_kernels.cuh"
 
 namespace hz {
 
 // ---------------------------------------------------------------- mean / variance
-constexpr int MOM_STAGES = 8;
-constexpr uint32_t MOM_RING = 8192;  // plane-ring words (64 KB)
-
-template <bool VAR>
-__global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_moments(
-    const uint8_t* __restrict__ c, uint64_t c_bytes, double* result,
-    const unsigned long long* __restrict__ pre, Ws ws) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  InStage* stages = reinterpret_cast<InStage*>(dyn);
-  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MOM_STAGES);
-  __shared__ uint64_t full[MOM_STAGES], ready[MOM_STAGES], empty[MOM_STAGES];
-  __shared__ unsigned long long stage_tile[MOM_STAGES];
-  __shared__ long long s_s1[CONSUMER_THREADS / 32];
-  __shared__ U128 s_s2[CONSUMER_THREADS / 32];
-  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
-  const Info h = parse_header(c, c_bytes);
-  int bad = 0;
-  uint64_t ntiles = 0;
-  if (!h.ok) bad = HOSZP_ERR_FORMAT;
-  else if (prescan_ok(h, pre, ws.max_tiles)) ntiles = ntiles_of(h.nb);
-  long long s1 = 0;  // per thread: |q| <= 2^30, far fewer than 2^32 values per thread
-  U128 s2 = {0, 0};
-  const OctetSel S = octet_sel(j);
-  uint32_t wlo, whi;
-  mean_weights(j, wlo, whi);
-  ring_init3<MOM_STAGES>(full, ready, empty);
-  if (w >= LOADER_WARP) {
-    const uint64_t G = gridDim.x;
-    __shared__ ulonglong2 s_win[32][2];
-    PreWindow pw;
-    pw.init(s_win);
-    __shared__ uint32_t s_beg[MOM_STAGES];
-    PlaneRing<MOM_STAGES, MOM_RING> pr;
-    pr.init(ring, s_beg);
-    loader_warps<MOM_STAGES>(
-        w - LOADER_WARP, stage_tile, full, ready, empty, ntiles, ws.status,
-        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t, uint32_t k, const uint32_t& k_rel,
-            auto&& release_one) {
-          unsigned long long pv[4];
-          pw.get(pre, k, blockIdx.x, G, ntiles, pv);
-          const TileSpan sp = tile_span(h, t, pv);
-          const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
-          const uint32_t at = pr.commit(k, p0, sp.plane_words());
-          if ((tid & 31) == 0) issue_in_tile(&stages[sk], &full[sk], c, h, t, sp, ring, at);
-        },
-        [&](int sk, unsigned long long t) { prepare_tile(stages[sk], t, h); });
-  } else {
-    RingPos rp{0, 0u};
-    for (;;) {
-      mbar_wait(&ready[rp.s], rp.par, ws.status);
-      const unsigned long long tile = stage_tile[rp.s];
-      if (tile >= ntiles) break;
-      const int st = rp.s;
-      moments_octet<VAR>(stages[st], ring, g, j, w, S, wlo, whi, s1, s2, [&]() {
-        __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[st]);
-      });
-      rp.next<MOM_STAGES>();
-    }
-  }
-  // CTA reduction -> per-CTA partial
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    if (VAR) {
-      U128 t;
-      t.lo = __shfl_xor_sync(0xffffffffu, s2.lo, o);
-      t.hi = __shfl_xor_sync(0xffffffffu, s2.hi, o);
-      add_u128(s2, t);
-    }
-  }
-  if ((tid & 31) == 0) {
-    s_s1[tid >> 5] = s1;
-    s_s2[tid >> 5] = s2;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __int128 t1 = 0;
-    U128 t2 = {0, 0};
-    for (int w = 0; w < CONSUMER_THREADS / 32; w++) {
-      t1 += s_s1[w];
-      add_u128(t2, s_s2[w]);
-    }
-    Partial p;
-    p.s1_lo = (long long)(unsigned long long)t1;
-    p.s1_hi = (long long)(t1 >> 64);
-    p.s2_lo = t2.lo;
-    p.s2_hi = t2.hi;
-    ws.partials[blockIdx.x] = p;
-  }
-  if (bad) set_status(ws.status, bad);
-  if (launch_end_is_last(ws) && w == 0) {
-    __int128 S1;
-    U128 S2;
-    sum_partials_warp(ws.partials, gridDim.x, S1, S2);
-    if (tid == 0) {
-      double res = 0.0;
-      if (h.ok && h.n == 0) {
-        set_status(ws.status, HOSZP_ERR_ARG);
-      } else if (h.ok) {
-        res = moment_finish(S1, S2, h.n, h.eps_q, VAR);
-      }
-      *result = res;
-      launch_reset(ws);
-    }
-  }
-}
-
 // Mean alone: the bit-sliced column sums of hz_moments.cuh over the
 // super-tile pipeline of hz_super.cuh. MEAN_GROUPS groups of STILES compute
 // warps take the stages in turn; warp i of a group takes tile i of the stage,
@@ -185,7 +77,7 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
     for (uint64_t k = 0;; k++) {
       const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
       const int sk = (int)(u % MEAN_STAGES);
-      mbar_wait(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status);
+      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status)) break;
       const unsigned long long s = stage_st[sk];
       if (s == ~0ull) break;
       const SStage& sg = stages[sk];
@@ -231,11 +123,11 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_mean(
 }
 
 // Variance over the same super-tile pipeline: warp i of a group takes tile i
-// of the stage and decodes it 4 blocks at a time (8 lanes per block, octet
-// layout of hz_decode.cuh) to the quantized integers, summing q and q^2.
+// of the stage and decodes it 16 blocks at a time, two lanes per block (one
+// per 32-position half, hz_lanes.cuh), summing q and q^2 exactly.
 __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
     const uint8_t* __restrict__ c, uint64_t c_bytes, double* result, unsigned long long* sums,
-    Ws ws) {
+    int take_sqrt, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   SStage* stages = reinterpret_cast<SStage*>(dyn);
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + MEAN_STAGES);
@@ -267,65 +159,19 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
                                                        c, h, rg, s_ts, ws, epoch);
   } else if (w < MEAN_NCW) {
     const int grp = w / MEAN_GW, ti = w % MEAN_GW;
-    const int j = lane & 7, gq = lane >> 3;
-    const OctetSel S = octet_sel(j);
     const int lastlen = (int)(h.n - (h.nb - 1) * L);
-    const bool small = h.qbound < (1u << 13);  // the header bounds every |q|
+    const bool qsmall = h.qbound < (1u << 13);  // the header bounds every |q|
+    const lanes::Shifts K = lanes::make_shifts(c_bytes != 0 ? 1u : 0u);
     for (uint64_t k = 0;; k++) {
       const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
       const int sk = (int)(u % MEAN_STAGES);
-      mbar_wait(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status);
+      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status)) break;
       const unsigned long long s = stage_st[sk];
       if (s == ~0ull) break;
       const SStage& sg = stages[sk];
       const uint64_t tile = (uint64_t)STILES * s + ti;
       const TileRates tr = tile_rates(sg, ti, tile, h.nb);
-      const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
-      const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
-      const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
-      for (int it = 0; it < steps; it++) {
-        const int b = 4 * it + gq;
-        uint32_t r, ex;
-        tile_block(tr, b, r, ex);
-        BlockRef br;
-        br.rate = (int)r;
-        br.outlier = sg.outlier[TILE * ti + b];
-        br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
-        br.planes = pls + (ex & 0xffffu);
-        br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
-        const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-        int d[8], q[8];
-        octet_deltas(br, kmax, j, S, d);
-        octet_values(br, d, j, q);
-        long long a = 0;
-        unsigned long long b2 = 0;  // 8 squares of |q| <= 2^30 stay below 2^63
-        if (small && br.len == L) {  // |q| < 2^13: 8 squares fit 32 bits
-          int a32 = 0;
-          uint32_t b32 = 0;
-#pragma unroll
-          for (int t = 0; t < 8; t++) {
-            a32 += q[t];
-            b32 += (uint32_t)(q[t] * q[t]);
-          }
-          a = a32;
-          b2 = b32;
-        } else if (br.len == L) {
-#pragma unroll
-          for (int t = 0; t < 8; t++) {
-            a += q[t];
-            b2 += (unsigned long long)((long long)q[t] * q[t]);
-          }
-        } else {
-#pragma unroll
-          for (int t = 0; t < 8; t++) {
-            const int qq = (8 * j + t < br.len) ? q[t] : 0;
-            a += qq;
-            b2 += (unsigned long long)((long long)qq * qq);
-          }
-        }
-        s1 += a;
-        add_u64(s2, b2);
-      }
+      var_tile(sg, ring, ti, tr, tile, ntiles, lastlen, qsmall, K, s1, s2);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sk]);
     }
@@ -372,6 +218,7 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
         set_status(ws.status, HOSZP_ERR_ARG);
       } else if (h.ok) {
         res = moment_finish(S1, S2, h.n, h.eps_q, true);
+        if (take_sqrt) res = sqrt(res);  // standard deviation (Sec. V-B), correctly rounded
       }
       if (result) *result = res;
       if (sums) {  // the exact sums themselves (for combining shards)
@@ -388,11 +235,15 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
 
 // ---------------------------------------------------------------- decompression
 // Full decompression (inverse of every pipeline step, Fig. 2) over the
-// super-tile pipeline: warp i of a group decodes tile i of the stage 4 blocks
-// at a time (octet layout) to q, dequantizes x' = float(q) * 2 eps_q and
-// stores each block's 64 floats (a warp writes 1 KB contiguous per step).
+// super-tile pipeline: warp i of a group decodes tile i of the stage 16
+// blocks at a time, two lanes per block (hz_lanes.cuh), to q, dequantizes
+// x' = float(q) * 2 eps_q and stores each half's 32 floats (a warp writes
+// 4 KB contiguous per step). With MEANS, the same pass writes the block-wise
+// means instead (Sec. V-B): out is a double per block and n_expect the block
+// count.
+template <bool MEANS>
 __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
-    const uint8_t* __restrict__ c, uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect,
+    const uint8_t* __restrict__ c, uint64_t c_bytes, void* __restrict__ out, uint64_t n_expect,
     Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   SStage* stages = reinterpret_cast<SStage*>(dyn);
@@ -406,7 +257,7 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
   int bad = 0;
   bool ok = h.ok;
   if (!h.ok) bad = HOSZP_ERR_FORMAT;
-  else if (h.n != n_expect) {
+  else if ((MEANS ? h.nb : h.n) != n_expect) {
     bad = HOSZP_ERR_MISMATCH;
     ok = false;
   }
@@ -427,51 +278,25 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
                                                        c, h, rg, s_ts, ws, epoch);
   } else if (w < MEAN_NCW) {
     const int grp = w / MEAN_GW, ti = w % MEAN_GW;
-    const int j = lane & 7, gq = lane >> 3;
-    const OctetSel S = octet_sel(j);
     const int lastlen = (int)(h.n - (h.nb - 1) * L);
     const float e2 = 2.0f * h.eps_q;
     const bool small = h.qbound < (1u << 22);
+    const lanes::Shifts K = lanes::make_shifts(c_bytes != 0 ? 1u : 0u);
     for (uint64_t k = 0;; k++) {
       const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
       const int sk = (int)(u % MEAN_STAGES);
-      mbar_wait(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status);
+      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status)) break;
       const unsigned long long s = stage_st[sk];
       if (s == ~0ull) break;
       const SStage& sg = stages[sk];
       const uint64_t tile = (uint64_t)STILES * s + ti;
       const TileRates tr = tile_rates(sg, ti, tile, h.nb);
-      const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
-      const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
-      const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
-      for (int it = 0; it < steps; it++) {
-        const int b = 4 * it + gq;
-        uint32_t r, ex;
-        tile_block(tr, b, r, ex);
-        BlockRef br;
-        br.rate = (int)r;
-        br.outlier = sg.outlier[TILE * ti + b];
-        br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
-        br.planes = pls + (ex & 0xffffu);
-        br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
-        const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-        int d[8], q[8];
-        octet_deltas(br, kmax, j, S, d);
-        octet_values(br, d, j, q);
-        float v[8];
-#pragma unroll
-        for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
-        const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
-        if (br.len == L) {
-          float4* o = reinterpret_cast<float4*>(x + i0);
-          __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
-          __stcs(o + 1, make_float4(v[4], v[5], v[6], v[7]));
-        } else {
-#pragma unroll
-          for (int t = 0; t < 8; t++)
-            if (8 * j + t < br.len) x[i0 + t] = v[t];
-        }
-      }
+      if (MEANS)
+        block_means_tile(sg, ring, ti, tr, tile, ntiles, lastlen, 2.0 * (double)h.eps_q, K,
+                         static_cast<double*>(out));
+      else
+        decompress_tile(sg, ring, ti, tr, tile, ntiles, lastlen, e2, small, K,
+                        static_cast<float*>(out));
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sk]);
     }
@@ -492,31 +317,31 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_decompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_decompress<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr = true;
   }
-  const int grid = persistent_grid(k_decompress, MEAN_THREADS, lc.grid, smem);
-  k_decompress<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
+  const int grid = persistent_grid(k_decompress<false>, MEAN_THREADS, lc.grid, smem);
+  k_decompress<false><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
   return cudaGetLastError();
 }
 
-template <bool VAR>
-static cudaError_t launch_moments_t(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
-                                    double* result, Ws ws) {
-  const size_t smem = MOM_STAGES * sizeof(InStage) + MOM_RING * sizeof(uint64_t);
+cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* out,
+                               uint64_t nb, Ws ws) {
+  const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_moments<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_decompress<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr = true;
   }
-  k_moments<VAR><<<persistent_grid(k_moments<VAR>, CONSUMER_THREADS, lc.grid, smem),
-                   CONSUMER_THREADS, smem, lc.stream>>>(
-      c, c_bytes, result, ws.pre[0], ws);
+  const int grid = persistent_grid(k_decompress<true>, MEAN_THREADS, lc.grid, smem);
+  k_decompress<true><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, out, nb, ws);
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
-                           bool variance, Ws ws, unsigned long long* sums) {
+                           bool variance, Ws ws, unsigned long long* sums, bool take_sqrt) {
   // both kernels find the rate prefix themselves (range_sums): no pre-scan
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
@@ -529,7 +354,7 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                                       : persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem);
   if (variance || sums)
     k_var<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, variance ? result : nullptr, sums,
-                                                   ws);
+                                                   take_sqrt ? 1 : 0, ws);
   else
     k_mean<<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, result, ws);
   return cudaGetLastError();

@@ -34,11 +34,16 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
                               uint64_t n, Ws ws);
 // sums (optional, 5 words): S1 (two's complement, lo, hi), S2 (lo, hi), n
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
-                           bool variance, Ws ws, unsigned long long* sums = nullptr);
+                           bool variance, Ws ws, unsigned long long* sums = nullptr,
+                           bool take_sqrt = false);
+cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* out,
+                               uint64_t nb, Ws ws);
 // ops.cu
 cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, uint8_t* out,
                           uint64_t cap, uint64_t* out_bytes, Ws ws);
 cudaError_t launch_add_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
+                              uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
+cudaError_t launch_sub_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws);

@@ -40,16 +40,24 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // Bounded wait: after about a second the status word gets TIMEOUT and the wait
 // gives up (the data in the stage is then not used for a valid result). The
 // clock is read once per 256 polls.
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* st) {
-  if (mbar_try_wait(bar, parity)) return;
+// Returns false when the wait gave up (status TIMEOUT set): callers then stop
+// their loops, so a stalled pipeline costs about a second, not a second per
+// remaining stage.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* st) {
+  if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   for (unsigned spins = 1;; spins++) {
-    if (mbar_try_wait(bar, parity)) return;
+    if (mbar_try_wait(bar, parity)) return true;
     if ((spins & 255u) == 0 && globaltimer_ns() - t0 > MBAR_TIMEOUT_NS) {
       set_status(st, HOSZP_ERR_TIMEOUT);
-      return;
+      return false;
     }
   }
+}
+// The same for a whole warp, with one answer for all its lanes (each lane
+// times out on its own clock).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, unsigned parity, int* st) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, st));
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

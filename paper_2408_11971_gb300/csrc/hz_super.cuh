@@ -290,8 +290,9 @@ __device__ __forceinline__ void super_loader_n(SStageT<NT>* stages, uint64_t* ri
   PlaneRing<S, RW> pr;
   pr.init(ring, s_beg);
   uint32_t k_rel = 0;
+  bool dead = false;  // a wait gave up: issue nothing more, wait for nothing more
   auto release_one = [&]() {
-    mbar_wait(&empty[k_rel % S], (k_rel / S) & 1, ws.status);
+    if (!dead && !mbar_wait_warp(&empty[k_rel % S], (k_rel / S) & 1, ws.status)) dead = true;
     k_rel++;
   };
   const uint64_t ntiles = ntiles_of(h[0].nb);
@@ -307,11 +308,13 @@ __device__ __forceinline__ void super_loader_n(SStageT<NT>* stages, uint64_t* ri
   if (bad && lane == 0) set_status(ws.status, bad);
   bool stop = false;
   int ends = 0;
+  uint32_t k_end = 0;  // stage uses issued so far
   // lanes 16q .. 16q + NT - 1 hold the tile sums of stream q
   const int ks = lane >> 4, ti = lane & 15;
   for (uint32_t k = 0; ends < GROUPS; k++) {
     const int sk = (int)(k % S);
     while (k_rel + S <= k) release_one();
+    if (dead) break;  // no end markers either: a stage may still be in flight
     const uint64_t s = rg.s0 + k;
     uint32_t pk = 0;
     if (!stop && s < rg.s1 && ks < NS && ti < NT && (uint64_t)NT * s + ti < ntiles) {
@@ -363,6 +366,7 @@ __device__ __forceinline__ void super_loader_n(SStageT<NT>* stages, uint64_t* ri
       all += words[q];
     }
     const uint32_t p0 = pr.reserve(k, all, k_rel, release_one);
+    if (dead) break;
     const uint32_t at = pr.commit(k, p0, all);
     if (ks < NS && ti < NT) {
       SStageT<NT>* sg = &stages[ks * S + sk];
@@ -404,7 +408,13 @@ __device__ __forceinline__ void super_loader_n(SStageT<NT>* stages, uint64_t* ri
       nc[q] = nc1[q];
       r[q] = r1[q];
     }
+    k_end = k + 1;
   }
+  // After a wait gave up, consumers may have left: the copies already issued
+  // must land before the CTA exits (bounded waits; a use not yet released is
+  // the last use of its stage, so its parity is unambiguous).
+  if (dead)
+    for (uint32_t u = k_rel; u < k_end; u++) mbar_wait(&full[u % S], (u / S) & 1, ws.status);
   if (bad) set_status(ws.status, bad);
 }
 

@@ -93,8 +93,8 @@ __device__ __forceinline__ int mul_requant(int q, const MulPlan& p, bool& ovf) {
 // shifted by rho) and, for negation, every sign word inverted.
 template <bool NEG>
 __global__ void __launch_bounds__(512) k_meta(const uint8_t* c, uint64_t c_bytes, double s,
-                                              uint8_t* out, uint64_t cap, uint64_t* out_bytes,
-                                              Ws ws) {
+                                              int sub, uint8_t* out, uint64_t cap,
+                                              uint64_t* out_bytes, Ws ws) {
   const Info h = parse_header(c, c_bytes);
   __shared__ int s_ok;
   __shared__ long long s_rho;
@@ -110,9 +110,12 @@ __global__ void __launch_bounds__(512) k_meta(const uint8_t* c, uint64_t c_bytes
       if (!quantize_scalar(s, h.eps_q, rho)) {
         ok = 0;
         if (blockIdx.x == 0) set_status(ws.status, HOSZP_ERR_RANGE);
-      } else if ((long long)h.qbound + (rho < 0 ? -rho : rho) > HOSZP_QLIM) {
-        ok = 0;
-        if (blockIdx.x == 0) set_status(ws.status, HOSZP_ERR_OVERFLOW);
+      } else {
+        if (sub) rho = -rho;  // scalar subtraction: O' = O - rho_s
+        if ((long long)h.qbound + (rho < 0 ? -rho : rho) > HOSZP_QLIM) {
+          ok = 0;
+          if (blockIdx.x == 0) set_status(ws.status, HOSZP_ERR_OVERFLOW);
+        }
       }
     }
     s_ok = ok;
@@ -182,13 +185,21 @@ __global__ void __launch_bounds__(512) k_meta(const uint8_t* c, uint64_t c_bytes
 
 cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, uint8_t* out,
                           uint64_t cap, uint64_t* out_bytes, Ws ws) {
-  k_meta<true><<<persistent_grid(k_meta<true>, 512, lc.grid), 512, 0, lc.stream>>>(c, c_bytes, 0.0, out, cap, out_bytes, ws);
+  k_meta<true><<<persistent_grid(k_meta<true>, 512, lc.grid), 512, 0, lc.stream>>>(c, c_bytes, 0.0, 0, out, cap, out_bytes, ws);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws) {
-  k_meta<false><<<persistent_grid(k_meta<false>, 512, lc.grid), 512, 0, lc.stream>>>(c, c_bytes, s, out, cap, out_bytes, ws);
+  k_meta<false><<<persistent_grid(k_meta<false>, 512, lc.grid), 512, 0, lc.stream>>>(c, c_bytes, s, 0, out, cap, out_bytes, ws);
+  return cudaGetLastError();
+}
+
+// Scalar subtraction (Sec. V-A "Scalar Subtraction"): the same pass with the
+// scalar's bin deducted, O' = O - rho_s.
+cudaError_t launch_sub_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
+                              uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws) {
+  k_meta<false><<<persistent_grid(k_meta<false>, 512, lc.grid), 512, 0, lc.stream>>>(c, c_bytes, s, 1, out, cap, out_bytes, ws);
   return cudaGetLastError();
 }
 
@@ -464,7 +475,7 @@ __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
     const int g = lt >> 1, hf = lt & 1;  // block of the tile, half (positions 32hf..32hf+31)
     for (uint64_t k = 0;; k++) {
       const int st = (int)(k % ADD_STAGES);
-      mbar_wait(&full[st], (uint32_t)((k / ADD_STAGES) & 1), ws.status);
+      mbar_wait(&full[st], (uint32_t)((k / ADD_STAGES) & 1), ws.status);  // add_bar below: no early exit
       const unsigned long long s = stage_st[st];
       if (s == ~0ull) break;
       const St& sa = stages[st];

@@ -1,0 +1,134 @@
+"""Scalar subtraction, standard deviation and block-wise means (Sec. V-A,
+V-B) on the CUDA path against the oracle, through the C ABI.
+
+Bit-exact: produced streams and block-wise means (exact block sums, the same
+two FP64 operations). Within 1e-12 relative: standard deviation (exact
+integer sums, FP64 finish)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def hz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2408_11971_gb300 as hz
+    from paper_2408_11971_gb300 import build
+
+    build.build()
+    O.build()
+    return hz
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def close(a, b, tol=REL_TOL):
+    return abs(a - b) <= tol * max(abs(b), 1e-300)
+
+
+CASES = datagen.small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES.keys()))
+@pytest.mark.parametrize("eb,mode", [(1e-2, "rel"), (1e-4, "rel"), (0.05, "abs")])
+def test_small_cases(hz, name, eb, mode):
+    x = CASES[name]
+    c = hz.compress(dev(x), eb=eb, mode=mode, dims=(x.size,))
+    oc = O.compress(x, dims=(x.size,), eb=eb, mode=mode)
+    assert np.array_equal(host(c), oc)
+    for s in (0.5, -3.25, 0.0):
+        assert np.array_equal(host(hz.sub_scalar(c, s)), O.sub_scalar(oc, s)), s
+    assert np.array_equal(host(hz.block_means(c)), O.block_means(oc))
+    # negated input: sign bits set at zero magnitudes (position 0, tail, zeros)
+    assert np.array_equal(host(hz.block_means(hz.negate(c))), O.block_means(O.negate(oc)))
+    if x.size > 0:
+        assert close(hz.std(c), O.std(oc))
+        assert close(hz.var(hz.negate(c)), O.var(oc))
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 37), (100, 50, 50), (449, 45, 23)])
+@pytest.mark.parametrize("rel", [1e-2, 1e-4])
+def test_grf_shapes(hz, shape, rel):
+    x = datagen.grf(shape, seed=11).reshape(-1)
+    c = hz.compress(dev(x), eb=rel, mode="rel", dims=shape)
+    oc = O.compress(x, dims=shape, eb=rel, mode="rel")
+    assert np.array_equal(host(c), oc)
+    assert np.array_equal(host(hz.block_means(c)), O.block_means(oc))
+    assert np.array_equal(host(hz.sub_scalar(c, 0.25)), O.sub_scalar(oc, 0.25))
+    assert close(hz.std(c), O.std(oc))
+
+
+def test_sub_scalar_inplace_and_errors(hz):
+    x = datagen.sines_1d(40_000, seed=3)
+    c = hz.compress(dev(x), eb=1e-3, mode="rel")
+    oc = host(c)
+    w = c.clone()
+    hz.sub_scalar(w, 1.5, inplace=True)
+    assert np.array_equal(host(w), O.sub_scalar(oc, 1.5))
+    hz.add_scalar(w, 1.5, inplace=True)
+    assert np.array_equal(np.delete(host(w), range(56, 60)), np.delete(oc, range(56, 60)))
+    big = hz.compress(dev(np.full(64, 8e5, np.float32)), eb=0.1)
+    with pytest.raises(hz.HoszpError) as ex:
+        hz.sub_scalar(big, 1e9)
+    assert ex.value.name in ("RANGE", "OVERFLOW")
+
+
+def test_widest_rates(hz):
+    # deltas near 2^31 (rates up to 31): decode, variance, std, block means
+    n = 64 * 37 + 11
+    x = np.where(np.arange(n) % 2 == 0, 4194304.0, -4194304.0).astype(np.float32)
+    x[200:400] = 7.0
+    c = hz.compress(dev(x), eb=0.5)
+    m = hz.mul_scalar(c, 120.0)
+    z = hz.add(m, m)
+    om = O.mul_scalar(O.compress(x, eb=0.5), 120.0)
+    oz = O.add(om, om)
+    assert np.array_equal(host(z), oz)
+    for t, o in ((m, om), (z, oz), (hz.negate(z), O.negate(oz))):
+        assert np.array_equal(host(hz.decompress(t)), O.decompress(o))
+        assert np.array_equal(host(hz.block_means(t)), O.block_means(o))
+        assert close(hz.var(t), O.var(o))
+        assert close(hz.std(t), O.std(o))
+        assert close(hz.mean(t), O.mean(o))
+
+
+def test_mixed_rates_every_width(hz):
+    # blocks of every rate 0..31 side by side in one warp's 16 blocks
+    rng = np.random.default_rng(5)
+    n = 64 * 512 + 17
+    q = np.zeros(n, np.int64)
+    for b in range((n + 63) // 64):
+        r = b % 32
+        lo = b * 64
+        hi = min(n, lo + 64)
+        if r == 0:
+            q[lo:hi] = rng.integers(-1000, 1000)
+            continue
+        d = rng.integers(-(1 << (r - 1)), 1 << (r - 1), hi - lo)
+        d[0] = rng.integers(-(1 << 20), 1 << 20)
+        q[lo:hi] = np.cumsum(d)
+    q = np.clip(q, -(1 << 22), 1 << 22)
+    x = (q.astype(np.float64) * 2 * 0.5).astype(np.float32)  # eps = 0.5: bins of width 1
+    c = hz.compress(dev(x), eb=0.5)
+    oc = O.compress(x, eb=0.5)
+    assert np.array_equal(host(c), oc)
+    for t, o in ((c, oc), (hz.mul_scalar(c, 50.0), O.mul_scalar(oc, 50.0))):
+        assert np.array_equal(host(t), o)
+        assert np.array_equal(host(hz.decompress(t)), O.decompress(o))
+        assert np.array_equal(host(hz.block_means(t)), O.block_means(o))
+        assert close(hz.var(t), O.var(o))
+        assert close(hz.std(t), O.std(o))
