@@ -279,26 +279,71 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
   } else if (w < MEAN_NCW) {
     const int grp = w / MEAN_GW, ti = w % MEAN_GW;
     const int lastlen = (int)(h.n - (h.nb - 1) * L);
-    const float e2 = 2.0f * h.eps_q;
-    const bool small = h.qbound < (1u << 22);
-    const lanes::Shifts K = lanes::make_shifts(c_bytes != 0 ? 1u : 0u);
-    for (uint64_t k = 0;; k++) {
-      const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
-      const int sk = (int)(u % MEAN_STAGES);
-      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status)) break;
-      const unsigned long long s = stage_st[sk];
-      if (s == ~0ull) break;
-      const SStage& sg = stages[sk];
-      const uint64_t tile = (uint64_t)STILES * s + ti;
-      const TileRates tr = tile_rates(sg, ti, tile, h.nb);
-      if (MEANS)
-        block_means_tile(sg, ring, ti, tr, tile, ntiles, lastlen, 2.0 * (double)h.eps_q, K,
-                         static_cast<double*>(out));
-      else
-        decompress_tile(sg, ring, ti, tr, tile, ntiles, lastlen, e2, small, K,
-                        static_cast<float*>(out));
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[sk]);
+    if (MEANS) {
+      const lanes::Shifts K = lanes::make_shifts(c_bytes != 0 ? 1u : 0u);
+      const double e2d = 2.0 * (double)h.eps_q;
+      for (uint64_t k = 0;; k++) {
+        const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
+        const int sk = (int)(u % MEAN_STAGES);
+        if (!mbar_wait_warp(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status)) break;
+        const unsigned long long s = stage_st[sk];
+        if (s == ~0ull) break;
+        const SStage& sg = stages[sk];
+        const uint64_t tile = (uint64_t)STILES * s + ti;
+        const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+        block_means_tile(sg, ring, ti, tr, tile, ntiles, lastlen, e2d, K, static_cast<double*>(out));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sk]);
+      }
+    } else {
+      float* __restrict__ x = static_cast<float*>(out);
+      const int j = lane & 7, gq = lane >> 3;
+      const OctetSel S = octet_sel(j);
+      const float e2 = 2.0f * h.eps_q;
+      const bool small = h.qbound < (1u << 22);
+      for (uint64_t k = 0;; k++) {
+        const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
+        const int sk = (int)(u % MEAN_STAGES);
+        if (!mbar_wait_warp(&full[sk], (uint32_t)((u / MEAN_STAGES) & 1), ws.status)) break;
+        const unsigned long long s = stage_st[sk];
+        if (s == ~0ull) break;
+        const SStage& sg = stages[sk];
+        const uint64_t tile = (uint64_t)STILES * s + ti;
+        const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+        const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
+        const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
+        const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
+        for (int it = 0; it < steps; it++) {
+          const int b = 4 * it + gq;
+          uint32_t r, ex;
+          tile_block(tr, b, r, ex);
+          BlockRef br;
+          br.rate = (int)r;
+          br.outlier = sg.outlier[TILE * ti + b];
+          br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+          br.planes = pls + (ex & 0xffffu);
+          br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
+          const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+          int d[8], q[8];
+          octet_deltas(br, kmax, j, S, d);
+          octet_values(br, d, j, q);
+          float v[8];
+#pragma unroll
+          for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+          const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
+          if (br.len == L) {
+            float4* o = reinterpret_cast<float4*>(x + i0);
+            __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
+            __stcs(o + 1, make_float4(v[4], v[5], v[6], v[7]));
+          } else {
+#pragma unroll
+            for (int t = 0; t < 8; t++)
+              if (8 * j + t < br.len) x[i0 + t] = v[t];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sk]);
+      }
     }
   }
   if (bad) set_status(ws.status, bad);

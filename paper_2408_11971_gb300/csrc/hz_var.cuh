@@ -98,62 +98,6 @@ __device__ __forceinline__ void var_tile(const St& sg, const uint64_t* ring, int
   }
 }
 
-// Decompression of tile `ti` of stage sg into x (Fig. 2, every step inverted):
-// the warp takes 16 blocks per step, lane 2m + hf half hf of block 16 it + m,
-// and stores x' = float(q) * e2 for its valid positions. small: the header
-// bounds every |q| below 2^22 (integer-to-float conversion by the magic
-// constant).
-template <class St>
-__device__ __forceinline__ void decompress_tile(const St& sg, const uint64_t* ring, int ti,
-                                                const TileRates& tr, uint64_t tile,
-                                                uint64_t ntiles, int lastlen, float e2, bool small,
-                                                const lanes::Shifts& K, float* __restrict__ x) {
-  const int lane = threadIdx.x & 31;
-  const int hf = lane & 1, m = lane >> 1;
-  const uint32_t* sgn = reinterpret_cast<const uint32_t*>(sg.sign + sg.sbase + sg.tnc[ti]);
-  const uint32_t* pls = reinterpret_cast<const uint32_t*>(ring + sg.pring + sg.pbase + sg.tr[ti]);
-  const int steps = (tr.nvt + 15) >> 4;  // warp-uniform
-  const uint32_t one = steps > 0 ? 1u : 0u;  // 1 wherever it is used
-  for (int it = 0; it < steps; it++) {
-    const int b = 16 * it + m;
-    uint32_t r, ex;
-    tile_block(tr, b, r, ex);
-    const int len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
-    const int nval = min(max(len - 32 * hf, 0), 32);
-    const int O = len ? sg.outlier[TILE * ti + b] : 0;
-    const uint32_t sw = r ? sgn[2 * (ex >> 16) + hf] : 0u;
-    const int Rw = (int)__reduce_max_sync(0xffffffffu, r);
-    uint32_t t[32];
-    lanes::twos_planes_any(Rw, pls + 2 * (ex & 0xffffu) + hf, (int)r, sw, t);
-    int p[32];
-    half_prefix_any(Rw, t, hf == 0, K, p);
-    const int tot0 = __shfl_xor_sync(0xffffffffu, p[31], 1);
-    const int base = O + (hf ? tot0 : 0);
-    float v[32];
-    if (small) {  // |q| < 2^22: the float of q is (q + 1.5 2^23) - 1.5 2^23, exactly
-      const uint32_t mb = (uint32_t)base + 0x4B400000u;
-#pragma unroll
-      for (int i = 0; i < 32; i++)
-        v[i] = __fmul_rn(__fsub_rn(__uint_as_float(lanes::mad((uint32_t)p[i], one, mb)),
-                                   12582912.0f), e2);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 32; i++) v[i] = dequant_any(base + p[i], e2);
-    }
-    float* o = x + (tile * TILE + b) * L + 32 * hf;
-    if (nval == 32) {
-      float4* o4 = reinterpret_cast<float4*>(o);
-#pragma unroll
-      for (int c = 0; c < 8; c++)
-        __stcs(o4 + c, make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]));
-    } else {
-#pragma unroll
-      for (int i = 0; i < 32; i++)
-        if (i < nval) o[i] = v[i];
-    }
-  }
-}
-
 // Block-wise means (Sec. V-B, "Mean", last sentences) of tile `ti`: the warp
 // takes 16 blocks per step, lane 2m + hf half hf of block 16 it + m; the
 // block's exact sum S1_b = sum of its q is formed from both halves and lane
@@ -196,7 +140,9 @@ __device__ __forceinline__ void block_means_tile(const St& sg, const uint64_t* r
     const long long base = O + (hf ? (long long)tot0 : 0ll);
     const long long s1h = (long long)nval * base + hs.sp;
     const long long s1 = s1h + __shfl_xor_sync(0xffffffffu, s1h, 1);
-    if (hf == 0 && len > 0) out[tile * TILE + b] = ((double)s1 / (double)len) * e2;
+    // a full block divides by 64, exactly a scaling by 2^-6 (no FP64 divide)
+    const double mb = (len == L) ? (double)s1 * 0.015625 : (double)s1 / (double)len;
+    if (hf == 0 && len > 0) out[tile * TILE + b] = mb * e2;
   }
 }
 
