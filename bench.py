@@ -585,7 +585,8 @@ def main():
     ctx.check("baseline")
 
     # operators outside the step (Sec. V-A scalar subtraction, Sec. V-B standard
-    # deviation and block-wise means), each timed alone
+    # deviation and block-wise means, Sec. V-D covariance), each timed alone;
+    # algorithmic bytes: what the operator must read and write
     nbk = (n + 63) // 64
     bmeans = torch.empty(nbk, dtype=torch.float64, device=dev)
 
@@ -596,8 +597,12 @@ def main():
             hz.std(sa, out=res[0:1], ctx=ctx, sync=False)
         elif op == "block_means":
             hz.block_means(sa, out=bmeans, ctx=ctx, sync=False)
+        elif op == "cov":
+            hz.cov(sa, sb, out=res[1:2], ctx=ctx, sync=False)
 
-    xalg = {"sub_scalar": 2 * C["ca"], "std": C["ca"], "block_means": C["ca"] + 8 * nbk}
+    # covariance reads A and B twice and writes and reads A + B (composition of exact operators)
+    xalg = {"sub_scalar": 2 * C["ca"], "std": C["ca"], "block_means": C["ca"] + 8 * nbk,
+            "cov": C["ca"] + C["cb"]}
     extra = {}
     for op, nbytes in xalg.items():
         for _ in range(3):
@@ -610,9 +615,15 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         xms = e0.elapsed_time(e1) / reps
-        extra[op] = {"ms": round(xms, 4), "orig_gbs": N4 / xms / 1e6,
+        extra[op] = {"ms": round(xms, 4), "orig_gbs": (2 if op == "cov" else 1) * N4 / xms / 1e6,
                      "alg_gbs": nbytes / xms / 1e6, "frac_of_measured_hbm": nbytes / xms / 1e6 / peak}
     ctx.check("operators outside the step")
+
+    # compression ratio (Sec. VI-B3, Table 8): this layout stores no per-block
+    # lengths; an SZp-style layout would add one 2-byte length per block
+    # (a block's words are at most 264 bytes)
+    cr = {"hoszp": N4 / C["ca"], "szp_style_per_block_lengths": N4 / (C["ca"] + 2 * nbk),
+          "field": "A"}
 
     # roofline of the dominant operator (largest share of the step)
     dom = max(ops, key=lambda o: per_op_ms[o])
@@ -692,7 +703,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
             "compressed_bytes": C, "per_op": per_op, "decompress_op_recompress": base,
-            "extra_ops": extra,
+            "extra_ops": extra, "compression_ratio": cr,
             "batched": batched, "serving": serving}
     print(json.dumps(line))
     if dist is not None:

@@ -34,6 +34,7 @@ from ._binding import (  # noqa: F401
     mean,
     var,
     std,
+    cov,
     block_means,
     sums,
     header,
@@ -45,5 +46,5 @@ from ._binding import (  # noqa: F401
 __all__ = [
     "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library", "default_context",
     "compress_bound", "compress", "decompress", "negate", "add_scalar", "sub_scalar", "mul_scalar", "add",
-    "sub", "mean", "var", "std", "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
+    "sub", "mean", "var", "std", "cov", "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

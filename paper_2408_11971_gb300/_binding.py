@@ -81,6 +81,7 @@ def load_library():
             "hoszp_sums": (I, [P, P, SZ, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
             "hoszp_std": (I, [P, P, SZ, P, P]),
+            "hoszp_cov": (I, [P, P, SZ, P, SZ, P, P]),
             "hoszp_block_means": (I, [P, P, SZ, P, U64, P]),
             "hoszp_batch_create": (I, [P, ctypes.c_uint32, P, P, ctypes.POINTER(P)]),
             "hoszp_batch_destroy": (None, [P]),
@@ -382,6 +383,24 @@ def var(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = Tru
 def std(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
     """Standard deviation: square root of the population variance (Sec. V-B)."""
     return _moment(load_library().hoszp_std, "std", c, out, stream, ctx, sync, check)
+
+
+def cov(a, b, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
+    """Population covariance of two streams with the same bound, from exact
+    integer sums (Sec. V-D)."""
+    torch = _torch()
+    a = _stream_tensor(a)
+    b = _stream_tensor(b)
+    ctx = _ctx(ctx, a)
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=a.device)
+    _check(load_library().hoszp_cov(ctx.handle, _dev_ptr(a), a.numel(), _dev_ptr(b), b.numel(),
+                                    _dev_ptr(out), _stream_ptr(stream)), "cov")
+    if not sync:
+        return out
+    if check:
+        ctx.check("cov")
+    return float(out.item())
 
 
 def block_means(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):

@@ -38,6 +38,9 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                            bool take_sqrt = false);
 cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* out,
                                uint64_t nb, Ws ws);
+cudaError_t launch_cov_finish(cudaStream_t s, const uint8_t* a, uint64_t a_bytes,
+                              const unsigned long long* sa, const unsigned long long* sb,
+                              const unsigned long long* sab, double* result, int* status);
 // ops.cu
 cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, uint8_t* out,
                           uint64_t cap, uint64_t* out_bytes, Ws ws);

@@ -101,4 +101,50 @@ __device__ __forceinline__ double moment_finish(__int128 S1, const U128& S2, uin
   return (u256_to_double(D) / (dn * dn)) * (e2 * e2);
 }
 
+
+// Population covariance (Sec. V-D) from exact sums: 2 eps_A 2 eps_B
+// (n S_AB - S1_A S1_B) / n^2, the numerator formed exactly in signed 256-bit
+// (sign and magnitude), then the same FP64 steps as the variance.
+__device__ __forceinline__ bool ge_u256(const U256& a, const U256& b) {
+  for (int i = 3; i >= 0; i--)
+    if (a.w[i] != b.w[i]) return a.w[i] > b.w[i];
+  return true;
+}
+__device__ __forceinline__ U256 add_u256(const U256& a, const U256& b) {
+  U256 r;
+  unsigned long long carry = 0;
+  for (int i = 0; i < 4; i++) {
+    const unsigned long long t = a.w[i] + carry;
+    const unsigned long long c1 = (t < carry) ? 1ull : 0ull;
+    r.w[i] = t + b.w[i];
+    carry = c1 + ((r.w[i] < t) ? 1ull : 0ull);
+  }
+  return r;
+}
+__device__ __forceinline__ double cov_finish(__int128 SAB, __int128 S1A, __int128 S1B, uint64_t n,
+                                             float eps_a, float eps_b) {
+  const bool neg1 = SAB < 0;
+  const bool neg2 = (S1A < 0) != (S1B < 0);
+  const U256 P1 = mul_u128_u128((unsigned __int128)(neg1 ? -SAB : SAB), (unsigned __int128)n);
+  const U256 P2 = mul_u128_u128((unsigned __int128)(S1A < 0 ? -S1A : S1A),
+                                (unsigned __int128)(S1B < 0 ? -S1B : S1B));
+  // N = (+-P1) - (+-P2)
+  U256 mag;
+  bool neg;
+  if (neg1 != neg2) {
+    mag = add_u256(P1, P2);
+    neg = neg1;
+  } else if (ge_u256(P1, P2)) {
+    mag = sub_u256(P1, P2);
+    neg = neg1;
+  } else {
+    mag = sub_u256(P2, P1);
+    neg = !neg1;
+  }
+  const double dn = (double)n;
+  const double e2a = 2.0 * (double)eps_a, e2b = 2.0 * (double)eps_b;
+  const double v = (u256_to_double(mag) / (dn * dn)) * (e2a * e2b);
+  return neg ? -v : v;
+}
+
 }  // namespace hz

@@ -1,5 +1,16 @@
-"""Mean and variance of one field whose compressed shards live on several
-devices or processes (one per rank).
+"""Reductions over compressed data held by several devices or processes (one
+per rank).
+
+Sum of fields (the distributed experiment of Sec. VI-B5: every node compresses
+its data and the streams are summed at a root): `reduce_sum` adds the ranks'
+streams of one field shape with the homomorphic element-wise addition (Sec.
+V-C) along a binomial tree -- log2(P) rounds; in round k a rank whose bit k is
+set sends its partial stream to the rank 2^k below it, which adds -- so no
+stream is ever decompressed and the root receives the stream of the sum. The
+result does not depend on the tree: q-sums are exact and the encoding of a
+q-field is unique.
+
+Mean and variance of one field whose compressed shards live on the ranks:
 
 Each rank holds a stream of whole blocks of the field, compressed with the same
 absolute bound (the same eps_q bits). The library returns each shard's exact
@@ -96,3 +107,50 @@ def mean_var(c_local, eps_q: float, group=None, ctx=None):
 
     s = from_words(B.sums(c_local, ctx=ctx))
     return finish(allreduce(s, group), eps_q)
+
+
+def _send_stream(t, dst, group=None):
+    import torch
+    import torch.distributed as dist
+
+    n = torch.tensor([t.numel()], dtype=torch.int64, device=t.device)
+    dist.send(n, dst, group=group)
+    dist.send(t.contiguous(), dst, group=group)
+
+
+def _recv_stream(src, device, group=None):
+    import torch
+    import torch.distributed as dist
+
+    n = torch.zeros(1, dtype=torch.int64, device=device)
+    dist.recv(n, src, group=group)
+    t = torch.empty(int(n.item()), dtype=torch.uint8, device=device)
+    dist.recv(t, src, group=group)
+    return t
+
+
+def reduce_sum(c_local, group=None, add=None):
+    """Sum of the fields whose streams (uint8 tensors, one per rank, the same n
+    and eps_q) the ranks hold, by a binomial tree of homomorphic additions.
+    Returns the stream of the sum on rank 0 and None elsewhere. `add(a, b)`
+    adds two streams (default: the library's hoszp_add on the tensors' device;
+    the tensors travel on that device, so use a backend that can carry it)."""
+    import torch.distributed as dist
+
+    if add is None:
+        from . import _binding as B
+
+        add = B.add
+    rank = dist.get_rank(group)
+    world = dist.get_world_size(group)
+    cur = c_local
+    step = 1
+    while step < world:
+        if rank % (2 * step) == step:  # send to the partner below and stop
+            _send_stream(cur, rank - step, group)
+            return None
+        if rank % (2 * step) == 0 and rank + step < world:
+            other = _recv_stream(rank + step, cur.device, group)
+            cur = add(cur, other)
+        step *= 2
+    return cur

@@ -132,3 +132,52 @@ def test_mixed_rates_every_width(hz):
         assert np.array_equal(host(hz.block_means(t)), O.block_means(o))
         assert close(hz.var(t), O.var(o))
         assert close(hz.std(t), O.std(o))
+
+
+@pytest.mark.parametrize("name", [k for k in CASES.keys() if CASES[k].size > 0])
+def test_cov_small_cases(hz, name):
+    x = CASES[name]
+    y = (x[::-1].copy() * np.float32(-0.75) + np.float32(0.125)).astype(np.float32)
+    c = hz.compress(dev(x), eb=0.05, dims=(x.size,))
+    d = hz.compress(dev(y), eb=0.05, dims=(y.size,))
+    oc, od = host(c), host(d)
+    assert np.array_equal(oc, O.compress(x, dims=(x.size,), eb=0.05))
+    assert np.array_equal(od, O.compress(y, dims=(y.size,), eb=0.05))
+    assert close(hz.cov(c, d), O.cov(oc, od))
+    assert close(hz.cov(d, c), O.cov(od, oc))
+    assert close(hz.cov(hz.negate(c), d), O.cov(O.negate(oc), od))
+    assert hz.cov(c, c) == hz.var(c)  # S_AA = S2 exactly, then the same FP64 steps
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 37), (449, 45, 23)])
+def test_cov_grf_pairs(hz, shape):
+    x = datagen.grf(shape, seed=21).reshape(-1)
+    y = datagen.grf(shape, seed=22).reshape(-1)
+    y = (0.6 * x + 0.8 * y).astype(np.float32)  # correlated
+    c = hz.compress(dev(x), eb=1e-4, mode="rel", dims=shape)
+    e = float(O.header(host(c))["eps_q"])
+    d = hz.compress(dev(y), eb=e, dims=shape)  # the same bound
+    oc, od = host(c), host(d)
+    assert np.array_equal(od, O.compress(y, dims=shape, eb=e))
+    assert close(hz.cov(c, d), O.cov(oc, od))
+    m = hz.mul_scalar(d, 7.5)
+    assert close(hz.cov(c, m), O.cov(oc, O.mul_scalar(od, 7.5)))
+
+
+def test_cov_wide_rates_and_errors(hz):
+    n = 64 * 37 + 11
+    x = np.where(np.arange(n) % 2 == 0, 4194304.0, -4194304.0).astype(np.float32)
+    x[200:400] = 7.0
+    c = hz.compress(dev(x), eb=0.5)
+    m = hz.mul_scalar(c, 120.0)  # rates near 30, qbound about 5e8
+    y = (1000.0 * np.sin(0.013 * np.arange(n)) + 0.5 * np.cos(0.7 * np.arange(n))).astype(np.float32)
+    d = hz.compress(dev(y), eb=0.5)
+    om, od = host(m), host(d)
+    assert close(hz.cov(m, d), O.cov(om, od))
+    assert close(hz.cov(m, hz.negate(m)), O.cov(om, O.negate(om)))
+    with pytest.raises(hz.HoszpError) as ex:  # different bounds
+        hz.cov(c, hz.compress(dev(x), eb=1.0))
+    assert ex.value.name == "MISMATCH"
+    with pytest.raises(hz.HoszpError) as ex:  # different lengths
+        hz.cov(c, hz.compress(dev(np.ones(n + 1, np.float32)), eb=0.5))
+    assert ex.value.name == "MISMATCH"

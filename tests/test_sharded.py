@@ -87,3 +87,59 @@ def test_sums_words_roundtrip():
         s = sharded.from_words(w)
         assert (s.s1, s.s2, s.n) == (s1, s2, n)
         assert sharded._from_limbs(sharded._to_limbs(s)) == s
+
+
+def _reduce_rank(rank, world, port, q):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import datagen
+    import oracle as O
+    from paper_2408_11971_gb300 import sharded
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x = datagen.sines_1d(50_011, seed=100 + rank)  # each node's own field, one shape
+    c = torch.from_numpy(O.compress(x, eb=2e-3))  # one absolute bound for all nodes
+
+    def add(a, b):  # the oracle's homomorphic addition stands in for hoszp_add here
+        return torch.from_numpy(O.add(a.numpy(), b.numpy()))
+
+    out = sharded.reduce_sum(c, add=add)
+    q.put((rank, None if out is None else out.numpy().tobytes()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [3, 4])
+def test_reduce_sum_binomial_tree(world):
+    """The sum of the nodes' compressed fields, added along a binomial tree of
+    homomorphic additions (Sec. VI-B5), is the stream of the summed integers:
+    byte for byte the same as adding the streams one after another."""
+    import multiprocessing as mp
+
+    import datagen
+    import oracle as O
+
+    O.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    ps = [ctx.Process(target=_reduce_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    got = dict(q.get(timeout=180) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(got[r] is None for r in range(1, world))
+    cs = [O.compress(datagen.sines_1d(50_011, seed=100 + r), eb=2e-3) for r in range(world)]
+    chain = cs[0]
+    for c in cs[1:]:
+        chain = O.add(chain, c)
+    assert got[0] == chain.tobytes()
+    qsum = sum(O.decode_q(c).astype(np.int64) for c in cs)
+    assert np.array_equal(O.decode_q(np.frombuffer(got[0], np.uint8)), qsum)
