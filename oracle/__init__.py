@@ -76,6 +76,7 @@ def _load():
     lib.orc_sub.argtypes = [P, SZ, P, SZ, P, SZ, P]
     lib.orc_sums.argtypes = [P, SZ, P, P, P, P, P, P]
     lib.orc_sub_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
+    lib.orc_mul_scalar_exact.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
     lib.orc_block_means.argtypes = [P, SZ, P, U64]
     lib.orc_cov_sums.argtypes = [P, SZ, P, SZ, P, P, P, P, P, P, P]
     lib.orc_header.argtypes = [P, SZ, P, P, P, P, P, P]
@@ -211,6 +212,11 @@ def sub_scalar(c, s: float) -> np.ndarray:
 
 def mul_scalar(c, s: float) -> np.ndarray:
     return _unary(_load().orc_mul_scalar, c, ctypes.c_double(s))
+
+
+def mul_scalar_exact(c, s: float) -> np.ndarray:
+    """Multiplication by the scalar itself: q' = floor(q s + 1/2), exactly."""
+    return _unary(_load().orc_mul_scalar_exact, c, ctypes.c_double(s))
 
 
 def add(a, b) -> np.ndarray:

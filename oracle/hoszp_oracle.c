@@ -525,6 +525,58 @@ int orc_mul_scalar(const uint8_t* c, size_t bytes, double s, uint8_t* out, size_
   return rc;
 }
 
+/* Scalar multiplication by the scalar itself (the variant that avoids the
+ * scalar's quantization; Sec. V-A multiplies by the bin rho_s instead):
+ * q' = floor(q s + 1/2), evaluated exactly (s = M 2^E with a 53-bit M). Unlike
+ * the paper's form, a scalar below eps does not collapse the field to zero. */
+static int mul_requant_s(int64_t q, double s, int64_t* out) {
+  if (q == 0 || s == 0.0) { *out = 0; return ORC_OK; }
+  int64_t M;
+  int E;
+  split_double(s, &M, &E);     /* s = M 2^E, |M| < 2^53 */
+  i128 KM = (i128)q * (i128)M; /* |KM| < 2^84 */
+  i128 r;
+  if (E >= 0) {
+    if (E > 40 || (KM > 0 ? KM : -KM) > ((i128)ORC_QLIM >> E)) return ORC_ERR_OVERFLOW;
+    r = KM * ((i128)1 << E);
+  } else if (-E >= 120) {
+    r = 0; /* |q s| < 2^-36 */
+  } else {
+    int sh = -E;
+    i128 num = 2 * KM + ((i128)1 << sh); /* 2^(sh+1) (q s + 1/2) */
+    i128 den = (i128)1 << (sh + 1);
+    r = num / den;
+    if ((num % den != 0) && (num < 0)) r -= 1;
+  }
+  if (r > ORC_QLIM || r < -ORC_QLIM) return ORC_ERR_OVERFLOW;
+  *out = (int64_t)r;
+  return ORC_OK;
+}
+
+int orc_mul_scalar_exact(const uint8_t* c, size_t bytes, double s, uint8_t* out, size_t cap,
+                         uint64_t* out_bytes) {
+  orc_hdr h;
+  int rc = read_header(c, bytes, &h);
+  if (rc) return rc;
+  if (!isfinite(s)) return ORC_ERR_ARG;
+  uint64_t n = h.n;
+  int64_t* q = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  if (!q) return ORC_ERR_ARG;
+  decode_q(c, bytes, &h, q);
+  int64_t qmax = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    int64_t r;
+    rc = mul_requant_s(q[i], s, &r);
+    if (rc) { free(q); return rc; }
+    q[i] = r;
+    if ((r < 0 ? -r : r) > qmax) qmax = r < 0 ? -r : r;
+  }
+  h.qbound = (uint32_t)qmax;
+  rc = encode_q(q, &h, out, cap, out_bytes);
+  free(q);
+  return rc;
+}
+
 /* Element-wise addition (Sec. V-C): O' = O_A + O_B and delta' = delta_A + delta_B,
  * i.e. q' = q_A + q_B, re-encoded. The result bound is qbound_A + qbound_B. */
 int orc_add(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_bytes, uint8_t* out,

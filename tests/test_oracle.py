@@ -496,3 +496,30 @@ def test_cov(pair):
     with pytest.raises(O.OracleError) as ex:
         O.cov(ca, O.compress(np.ones(101, np.float32), eb=0.1))
     assert ex.value.name == "MISMATCH"
+
+
+def test_mul_scalar_exact(pair):
+    """q' = floor(q s + 1/2) with s itself (no quantization of the scalar)."""
+    ca, _ = pair
+    q = values(parse(ca))
+    idx = np.random.default_rng(4).choice(q.size, 300, replace=False)
+    for s in (3.14, -0.5, 2.0, 1e-5, 0.37, -7.25):
+        out = O.mul_scalar_exact(ca, s)
+        q2 = values(parse(out))
+        for i in idx:  # exact rational rounding, half up
+            assert q2[i] == math.floor(Fraction(int(q[i])) * Fraction(s) + Fraction(1, 2))
+        _check_stream_q(out, q2)
+    # special cases that reduce to known streams
+    assert np.array_equal(O.mul_scalar_exact(ca, 1.0), ca)  # identity, byte for byte
+    assert np.array_equal(values(parse(O.mul_scalar_exact(ca, 2.0))), 2 * q)
+    assert np.array_equal(values(parse(O.mul_scalar_exact(ca, -1.0))), -q)
+    assert np.array_equal(values(parse(O.mul_scalar_exact(ca, 0.0))), 0 * q)
+    # a scalar below eps does not zero the field (the paper's rho_s would be 0)
+    e = float(parse(ca)["eps_q"])
+    assert eq3_fraction(e / 4, e) == 0
+    small = values(parse(O.mul_scalar_exact(ca, 1000.0 * e)))
+    assert np.array_equal(small, [math.floor(Fraction(int(v)) * Fraction(1000.0 * e) + Fraction(1, 2))
+                                  for v in q])
+    with pytest.raises(O.OracleError) as ex:
+        O.mul_scalar_exact(O.compress(np.full(64, 8e5, np.float32), eb=0.1), 1000.0)
+    assert ex.value.name == "OVERFLOW"
