@@ -77,6 +77,7 @@ def _load():
     lib.orc_sums.argtypes = [P, SZ, P, P, P, P, P, P]
     lib.orc_sub_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
     lib.orc_mul_scalar_exact.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
+    lib.orc_hadamard.argtypes = [P, SZ, P, SZ, P, SZ, P]
     lib.orc_block_means.argtypes = [P, SZ, P, U64]
     lib.orc_cov_sums.argtypes = [P, SZ, P, SZ, P, P, P, P, P, P, P]
     lib.orc_header.argtypes = [P, SZ, P, P, P, P, P, P]
@@ -227,6 +228,18 @@ def add(a, b) -> np.ndarray:
     nbytes = np.zeros(1, np.uint64)
     _check(_load().orc_add(_ptr(a), a.size, _ptr(b), b.size, _ptr(out), cap, _ptr(nbytes)),
            "add")
+    return out[: int(nbytes[0])].copy()
+
+
+def hadamard(a, b) -> np.ndarray:
+    """Hadamard product (Sec. V-C): q' = floor(2 eps q_A q_B + 1/2), re-encoded."""
+    a = _stream(a)
+    b = _stream(b)
+    cap = bound(header(a)["n"])
+    out = np.zeros(cap, np.uint8)
+    nbytes = np.zeros(1, np.uint64)
+    _check(_load().orc_hadamard(_ptr(a), a.size, _ptr(b), b.size, _ptr(out), cap, _ptr(nbytes)),
+           "hadamard")
     return out[: int(nbytes[0])].copy()
 
 

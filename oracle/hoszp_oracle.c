@@ -603,6 +603,40 @@ int orc_add(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_bytes, 
   return rc;
 }
 
+/* Hadamard product (Sec. V-C "Hadamard Product": like the scalar
+ * multiplication, with the other field's quantized values in place of the
+ * scalar's bin): q' = floor(2e q_A q_B + 1/2), Eq. 3 applied to the product of
+ * the dequantized values, re-encoded. The streams must agree in n and eps_q. */
+int orc_hadamard(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_bytes,
+                 uint8_t* out, size_t cap, uint64_t* out_bytes) {
+  orc_hdr ha, hb;
+  int rc = read_header(a, a_bytes, &ha);
+  if (rc) return rc;
+  rc = read_header(b, b_bytes, &hb);
+  if (rc) return rc;
+  if (ha.n != hb.n || float_to_bits(ha.eps_q) != float_to_bits(hb.eps_q)) return ORC_ERR_MISMATCH;
+  uint64_t n = ha.n;
+  int64_t* qa = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  int64_t* qb = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  if (!qa || !qb) { free(qa); free(qb); return ORC_ERR_ARG; }
+  decode_q(a, a_bytes, &ha, qa);
+  decode_q(b, b_bytes, &hb, qb);
+  int64_t qmax = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    int64_t r;
+    rc = mul_requant(qa[i], qb[i], ha.eps_q, &r);
+    if (rc) { free(qa); free(qb); return rc; }
+    qa[i] = r;
+    if ((r < 0 ? -r : r) > qmax) qmax = r < 0 ? -r : r;
+  }
+  orc_hdr h = ha;
+  h.qbound = (uint32_t)qmax;
+  rc = encode_q(qa, &h, out, cap, out_bytes);
+  free(qa);
+  free(qb);
+  return rc;
+}
+
 /* Element-wise subtraction (Sec. V-C, "Element-wise Subtraction"): as the
  * addition with B's quantized values negated, q' = q_A - q_B, re-encoded. The
  * result bound is qbound_A + qbound_B. */

@@ -523,3 +523,33 @@ def test_mul_scalar_exact(pair):
     with pytest.raises(O.OracleError) as ex:
         O.mul_scalar_exact(O.compress(np.full(64, 8e5, np.float32), eb=0.1), 1000.0)
     assert ex.value.name == "OVERFLOW"
+
+
+def test_hadamard(pair):
+    """Hadamard product (Sec. V-C): q' = floor(2 eps q_A q_B + 1/2)."""
+    ca, _ = pair
+    e = float(parse(ca)["eps_q"])
+    b = datagen.sines_1d(30_011, seed=9)
+    cb = O.compress(b, eb=e)  # the same bound
+    qa, qb = values(parse(ca)), values(parse(cb))
+    z = O.hadamard(ca, cb)
+    qz = values(parse(z))
+    idx = np.random.default_rng(6).choice(qa.size, 400, replace=False)
+    E2 = 2 * Fraction(e)
+    for i in idx:  # Eq. 3 applied to (2e q_A)(2e q_B), exactly
+        assert qz[i] == math.floor(E2 * int(qa[i]) * int(qb[i]) + Fraction(1, 2))
+    _check_stream_q(z, qz)
+    zr = O.hadamard(cb, ca)  # commutative: the same sections (the header takes A's fields)
+    assert np.array_equal(zr[64:], z[64:]) and np.array_equal(values(parse(zr)), qz)
+    # a constant field s reduces it to the scalar multiplication by s (q_B = rho_s)
+    s = 3.14
+    cs = O.compress(np.full(qa.size, s, np.float32), eb=e)
+    assert set(values(parse(cs)).tolist()) == {eq3_fraction(np.float32(s), e)}
+    assert np.array_equal(O.hadamard(ca, cs), O.mul_scalar(ca, float(np.float32(s))))
+    with pytest.raises(O.OracleError) as ex:
+        O.hadamard(ca, O.compress(b, eb=2 * e))
+    assert ex.value.name == "MISMATCH"
+    big = O.compress(np.full(64, 8e5, np.float32), eb=0.1)  # q = 4e6: q^2 0.2 = 3.2e12
+    with pytest.raises(O.OracleError) as ex:
+        O.hadamard(big, big)
+    assert ex.value.name == "OVERFLOW"
