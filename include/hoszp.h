@@ -155,6 +155,16 @@ int hoszp_sub_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
 int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
                      size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
 
+/* Multiplication by the scalar itself: q' = floor(q s + 1/2) evaluated exactly
+ * (s = M 2^E, 53-bit M), i.e. Eq. 3 applied to the dequantized value times s
+ * without first quantizing s to its bin rho_s as Sec. V-A does. The paper's
+ * form turns every scalar with |s| < eps into 0 (rho_s = 0); this variant does
+ * not. Same arguments and errors as hoszp_mul_scalar, except that no scalar is
+ * out of range: a product beyond HOSZP_QLIM is OVERFLOW on the device. */
+int hoszp_mul_scalar_exact(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s,
+                           void* d_out, size_t cap, uint64_t* d_out_bytes,
+                           hoszp_stream_t stream);
+
 /* Element-wise addition, Sec. V-C, workflow 2: outliers add, signed deltas add,
  * blockwise fixed-length re-encode (no Lorenzo inverse). Streams must agree in
  * n, block length and eps_q (MISMATCH otherwise). OVERFLOW if the sum of the

@@ -29,6 +29,7 @@ from ._binding import (  # noqa: F401
     add_scalar,
     sub_scalar,
     mul_scalar,
+    mul_scalar_exact,
     add,
     sub,
     mean,
@@ -44,7 +45,8 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
-    "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library", "default_context",
-    "compress_bound", "compress", "decompress", "negate", "add_scalar", "sub_scalar", "mul_scalar", "add",
-    "sub", "mean", "var", "std", "cov", "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
+    "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library",
+    "default_context", "compress_bound", "compress", "decompress", "negate", "add_scalar",
+    "sub_scalar", "mul_scalar", "mul_scalar_exact", "add", "sub", "mean", "var", "std", "cov",
+    "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

@@ -75,6 +75,7 @@ def load_library():
             "hoszp_add_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_sub_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_mul_scalar": (I, [P, P, SZ, D, P, SZ, P, P]),
+            "hoszp_mul_scalar_exact": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_add": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_sub": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
@@ -275,8 +276,9 @@ def _unary(fn, what, c, extra, out, out_bytes, inplace, stream, ctx, sync, check
     if inplace:
         out = c
     elif out is None:
-        out = torch.empty(c.numel() if what != "mul_scalar" else max(
-            c.numel(), compress_bound(header(c)["n"])), dtype=torch.uint8, device=c.device)
+        grows = what in ("mul_scalar", "mul_scalar_exact")  # outputs that can outgrow the input
+        out = torch.empty(max(c.numel(), compress_bound(header(c)["n"])) if grows else c.numel(),
+                          dtype=torch.uint8, device=c.device)
     if out_bytes is None:
         out_bytes = torch.zeros(1, dtype=torch.int64, device=c.device)
     rc = fn(ctx.handle, _dev_ptr(c), c.numel(), *extra, _dev_ptr(out), out.numel(),
@@ -311,6 +313,14 @@ def mul_scalar(c, s: float, out=None, out_bytes=None, stream=None, ctx=None, syn
     """Scalar multiplication through the quantized integers (Sec. V-A)."""
     return _unary(load_library().hoszp_mul_scalar, "mul_scalar", c, (ctypes.c_double(s),), out,
                   out_bytes, False, stream, ctx, sync, check)
+
+
+def mul_scalar_exact(c, s: float, out=None, out_bytes=None, stream=None, ctx=None,
+                     sync: bool = True, check: bool = True):
+    """Multiplication by the scalar itself, q' = floor(q s + 1/2), through the
+    quantized integers."""
+    return _unary(load_library().hoszp_mul_scalar_exact, "mul_scalar_exact", c,
+                  (ctypes.c_double(s),), out, out_bytes, False, stream, ctx, sync, check)
 
 
 def _bivariate(fn, what, a, b, out, out_bytes, stream, ctx, sync, check):

@@ -1,6 +1,7 @@
 // api.cu — the C ABI of libhoszp (declared in include/hoszp.h): argument
 // checks, the context's device workspace, and kernel launches.
 #include <cfloat>
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -321,8 +322,8 @@ int hoszp_sub_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
                                    ctx->ws));
 }
 
-int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
-                     size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+static int mul_scalar_any(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
+                          size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream, bool exact) {
   if (!ctx || !d_c || !d_out || !d_out_bytes || c_bytes < HOSZP_HEADER_BYTES) return HOSZP_ERR_ARG;
   if (!std::isfinite(s)) return HOSZP_ERR_ARG;
   if (!aligned16(d_c) || !aligned16(d_out) || !aligned8(d_out_bytes)) return HOSZP_ERR_ARG;
@@ -333,14 +334,27 @@ int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, 
   const uint64_t tiles = tiles_from_bytes(c_bytes);
   // slot words: (1 + e) per non-constant input block + the input's plane words,
   // where e bounds the growth of a block's rate: |2e rho| <= 2|s| when rho != 0
-  const uint32_t e_bits = (uint32_t)std::ceil(std::log2(2.0 * std::fabs(s) + 1.0)) + 1u;
+  // (|q' - q'_prev| <= |s| |delta| + 1 for the exact variant too); no rate exceeds 31
+  const uint32_t e_bits =
+      std::min(31u, (uint32_t)std::ceil(std::log2(2.0 * std::fabs(s) + 1.0)) + 1u);
   const uint64_t nnc_bound = c_bytes / 21 + 1;  // a non-constant block takes >= 21 bytes
   int rc = ensure_ws(ctx, tiles, nnc_bound * (1ull + e_bits) + c_bytes / 8 + 64);
   if (rc) return rc;
   Launch lc = lc_of(ctx, stream);
-  rc = cuda_rc(launch_mul_scalar(lc, a, c_bytes, s, e_bits, o, cap, ctx->ws));
+  rc = cuda_rc(launch_mul_scalar(lc, a, c_bytes, s, exact, e_bits, o, cap, ctx->ws));
   if (rc) return rc;
   return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_MUL, e_bits, ctx->ws));
+}
+
+int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,
+                     size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+  return mul_scalar_any(ctx, d_c, c_bytes, s, d_out, cap, d_out_bytes, stream, false);
+}
+
+int hoszp_mul_scalar_exact(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s,
+                           void* d_out, size_t cap, uint64_t* d_out_bytes,
+                           hoszp_stream_t stream) {
+  return mul_scalar_any(ctx, d_c, c_bytes, s, d_out, cap, d_out_bytes, stream, true);
 }
 
 static int add_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b,

@@ -49,7 +49,7 @@ cudaError_t launch_add_scalar(const Launch& lc, const uint8_t* c, uint64_t c_byt
 cudaError_t launch_sub_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
-                              uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws);
+                              bool exact, uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws);
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, bool subtract, Ws ws);
 

@@ -49,6 +49,40 @@ __device__ __forceinline__ MulPlan mul_plan(float e, long long rho, uint32_t qbo
   return p;
 }
 
+// Plan for the multiplication by the scalar itself, q' = floor(q s + 1/2):
+// s = M 2^E with the trailing zero bits of its 53-bit significand removed (so
+// short scalars such as 2.5 reach the 64-bit path), the sign in rho.
+__device__ __forceinline__ MulPlan mul_plan_exact(double s, uint32_t qbound) {
+  MulPlan p;
+  p.rho = 0;
+  p.M = 0;
+  p.E = 0;
+  if (s != 0.0) {
+    int ex;
+    const double fr = frexp(fabs(s), &ex);
+    long long M = (long long)ldexp(fr, 53);
+    int E = ex - 53;
+    while ((M & 1) == 0) {
+      M >>= 1;
+      E++;
+    }
+    p.rho = s < 0.0 ? -1 : 1;
+    p.M = M;
+    p.E = E;
+  }
+  p.P = p.rho * p.M;
+  p.sh = -p.E;
+  const unsigned long long aP = (unsigned long long)(p.P < 0 ? -p.P : p.P);
+  const unsigned __int128 prod = (unsigned __int128)aP * (unsigned __int128)(qbound + 1ull);
+  p.fast = p.sh >= 1 && p.sh <= 62 && prod < ((unsigned __int128)1 << 62);
+  p.f32 = false;
+  p.rho32 = (int)p.rho;
+  p.M32 = 0;
+  p.sh2 = 0;
+  p.half = p.sh >= 1 && p.sh <= 62 ? (1ll << (p.sh - 1)) : 0;
+  return p;
+}
+
 __device__ __forceinline__ int mul_requant_f32(int q, const MulPlan& p) {
   const int t = q * p.rho32;
   const long long v = (long long)t * p.M32 + p.half;  // floor(2e q rho + 1/2) * 2^sh, exact
@@ -252,6 +286,7 @@ __device__ __forceinline__ void octet_mag_sign(const int d[8], uint32_t mag[8], 
 constexpr int MUL_STAGES = 8;
 constexpr uint32_t MUL_RING = 8192;  // plane-ring words (64 KB)
 
+template <bool EXACT>
 __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
     const uint8_t* __restrict__ c, uint64_t c_bytes, double s, uint8_t* __restrict__ out,
     uint64_t cap, uint32_t e_bits, const unsigned long long* __restrict__ pre, Ws ws) {
@@ -270,7 +305,7 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
     int ok = h.ok;
     long long rho = 0;
     if (!h.ok) bad = HOSZP_ERR_FORMAT;
-    else if (!quantize_scalar(s, h.eps_q, rho)) {
+    else if (!EXACT && !quantize_scalar(s, h.eps_q, rho)) {
       ok = 0;
       bad = HOSZP_ERR_RANGE;
     } else if (cap < off_sign(h.nb)) {
@@ -283,7 +318,8 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
   }
   ring_init3<MUL_STAGES>(full, ready, empty);
   const uint64_t ntiles = (s_ok && prescan_ok(h, pre, ws.max_tiles)) ? ntiles_of(h.nb) : 0;
-  const MulPlan mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
+  const MulPlan mp = EXACT ? mul_plan_exact(s, h.ok ? h.qbound : 0u)
+                           : mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
   const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   bool ovf = false;
@@ -371,18 +407,26 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
 }
 
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
-                              uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
+                              bool exact, uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
   const size_t smem = MUL_STAGES * sizeof(InStage) + MUL_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_mul_scalar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_mul_scalar<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_mul_scalar<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr = true;
   }
-  k_mul_scalar<<<persistent_grid(k_mul_scalar, PRODUCER_THREADS, lc.grid, smem),
-                 PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, out, cap, e_bits, ws.pre[0],
-                                                      ws);
+  if (exact)
+    k_mul_scalar<true><<<persistent_grid(k_mul_scalar<true>, PRODUCER_THREADS, lc.grid, smem),
+                         PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, out, cap, e_bits,
+                                                              ws.pre[0], ws);
+  else
+    k_mul_scalar<false><<<persistent_grid(k_mul_scalar<false>, PRODUCER_THREADS, lc.grid, smem),
+                          PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, out, cap, e_bits,
+                                                               ws.pre[0], ws);
   return cudaGetLastError();
 }
 

@@ -181,3 +181,31 @@ def test_cov_wide_rates_and_errors(hz):
     with pytest.raises(hz.HoszpError) as ex:  # different lengths
         hz.cov(c, hz.compress(dev(np.ones(n + 1, np.float32)), eb=0.5))
     assert ex.value.name == "MISMATCH"
+
+
+@pytest.mark.parametrize("name", list(CASES.keys()))
+def test_mul_scalar_exact_small_cases(hz, name):
+    x = CASES[name]
+    c = hz.compress(dev(x), eb=0.05, dims=(x.size,))
+    oc = host(c)
+    for s in (3.14, -0.37, 2.5, 1e-3, 1.0, -1.0, 0.0):
+        assert np.array_equal(host(hz.mul_scalar_exact(c, s)), O.mul_scalar_exact(oc, s)), s
+    assert np.array_equal(host(hz.mul_scalar_exact(c, 1.0)), oc)  # identity, byte for byte
+
+
+def test_mul_scalar_exact_grf_and_wide(hz):
+    shape = (449, 45, 23)
+    x = datagen.grf(shape, seed=31).reshape(-1)
+    c = hz.compress(dev(x), eb=1e-4, mode="rel", dims=shape)
+    oc = host(c)
+    for s in (3.14, -123.456, 7e-4):
+        assert np.array_equal(host(hz.mul_scalar_exact(c, s)), O.mul_scalar_exact(oc, s)), s
+    n = 64 * 37 + 11  # deltas near 2^31 after the product
+    w = np.where(np.arange(n) % 2 == 0, 4194304.0, -4194304.0).astype(np.float32)
+    cw = hz.compress(dev(w), eb=0.5)
+    ow = host(cw)
+    for s in (120.0, -127.9, 0.999):
+        assert np.array_equal(host(hz.mul_scalar_exact(cw, s)), O.mul_scalar_exact(ow, s)), s
+    with pytest.raises(hz.HoszpError) as ex:
+        hz.mul_scalar_exact(cw, 1000.0)
+    assert ex.value.name == "OVERFLOW"
