@@ -601,10 +601,13 @@ def main():
             hz.cov(sa, sb, out=res[1:2], ctx=ctx, sync=False)
         elif op == "mul_scalar_exact":
             hz.mul_scalar_exact(sa, SCALAR_MUL, out=outb, out_bytes=outs, ctx=ctx, sync=False)
+        elif op == "hadamard":
+            hz.hadamard(sa, sb, out=outb, out_bytes=outs, scratch=qscratch, ctx=ctx, sync=False)
 
     # covariance reads A and B twice and writes and reads A + B (composition of exact operators)
     xalg = {"sub_scalar": 2 * C["ca"], "std": C["ca"], "block_means": C["ca"] + 8 * nbk,
-            "cov": C["ca"] + C["cb"], "mul_scalar_exact": None}
+            "cov": C["ca"] + C["cb"], "mul_scalar_exact": None, "hadamard": None}
+    qscratch = torch.empty(n, dtype=torch.int32, device=dev)  # B's integers (Hadamard product)
     extra = {}
     for op, nbytes in xalg.items():
         for _ in range(3):
@@ -617,9 +620,10 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         xms = e0.elapsed_time(e1) / reps
-        if nbytes is None:  # a produced stream: input plus the output's size
-            nbytes = C["ca"] + int(outs.item())
-        extra[op] = {"ms": round(xms, 4), "orig_gbs": (2 if op == "cov" else 1) * N4 / xms / 1e6,
+        if nbytes is None:  # a produced stream: inputs plus the output's size
+            nbytes = C["ca"] + (C["cb"] if op == "hadamard" else 0) + int(outs.item())
+        extra[op] = {"ms": round(xms, 4),
+                     "orig_gbs": (2 if op in ("cov", "hadamard") else 1) * N4 / xms / 1e6,
                      "alg_gbs": nbytes / xms / 1e6, "frac_of_measured_hbm": nbytes / xms / 1e6 / peak}
     ctx.check("operators outside the step")
 

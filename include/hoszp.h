@@ -172,6 +172,18 @@ int hoszp_mul_scalar_exact(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, doub
 int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
               void* d_out, size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
 
+/* Hadamard product A o B, Sec. V-C "Hadamard Product" (the scalar
+ * multiplication with the other field's quantized values in place of the
+ * scalar's bin): q' = floor(2 eps_q q_A q_B + 1/2), Eq. 3 applied to the product
+ * of the dequantized values, evaluated exactly, then Lorenzo + BF re-encode.
+ * The streams must agree in n and eps_q (MISMATCH otherwise; n is the streams'
+ * value count). d_scratch: caller-owned device buffer of n int32 values
+ * (16-byte aligned) that receives B's quantized integers. Output stream is
+ * canonical. Errors: OVERFLOW (|q'| > HOSZP_QLIM), CAPACITY, MISMATCH. */
+int hoszp_hadamard(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b,
+                   size_t b_bytes, int32_t* d_scratch, uint64_t n, void* d_out, size_t cap,
+                   uint64_t* d_out_bytes, hoszp_stream_t stream);
+
 /* Element-wise subtraction A - B, Sec. V-C "Element-wise Subtraction": as
  * hoszp_add with B's signed deltas and outliers negated (O' = O_A - O_B,
  * delta' = delta_A - delta_B). Same arguments, checks and errors as

@@ -32,6 +32,7 @@ from ._binding import (  # noqa: F401
     mul_scalar_exact,
     add,
     sub,
+    hadamard,
     mean,
     var,
     std,
@@ -47,6 +48,6 @@ from ._binding import (  # noqa: F401
 __all__ = [
     "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library",
     "default_context", "compress_bound", "compress", "decompress", "negate", "add_scalar",
-    "sub_scalar", "mul_scalar", "mul_scalar_exact", "add", "sub", "mean", "var", "std", "cov",
-    "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
+    "sub_scalar", "mul_scalar", "mul_scalar_exact", "add", "sub", "hadamard", "mean", "var",
+    "std", "cov", "block_means", "sums", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

@@ -78,6 +78,7 @@ def load_library():
             "hoszp_mul_scalar_exact": (I, [P, P, SZ, D, P, SZ, P, P]),
             "hoszp_add": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
             "hoszp_sub": (I, [P, P, SZ, P, SZ, P, SZ, P, P]),
+            "hoszp_hadamard": (I, [P, P, SZ, P, SZ, P, U64, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
             "hoszp_sums": (I, [P, P, SZ, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
@@ -350,6 +351,28 @@ def sub(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True
     """Element-wise subtraction A - B of two streams (Sec. V-C)."""
     return _bivariate(load_library().hoszp_sub, "sub", a, b, out, out_bytes, stream, ctx, sync,
                       check)
+
+
+def hadamard(a, b, out=None, out_bytes=None, scratch=None, stream=None, ctx=None,
+             sync: bool = True, check: bool = True):
+    """Hadamard product of two streams (Sec. V-C), q' = floor(2 eps q_A q_B + 1/2).
+    `scratch`: an int32 CUDA tensor of n values (allocated when not given)."""
+    torch = _torch()
+    a = _stream_tensor(a)
+    b = _stream_tensor(b)
+    ctx = _ctx(ctx, a)
+    n = header(a)["n"]
+    if scratch is None:
+        scratch = torch.empty(max(n, 4), dtype=torch.int32, device=a.device)
+    if out is None:
+        out = torch.empty(compress_bound(n), dtype=torch.uint8, device=a.device)
+    if out_bytes is None:
+        out_bytes = torch.zeros(1, dtype=torch.int64, device=a.device)
+    rc = load_library().hoszp_hadamard(ctx.handle, _dev_ptr(a), a.numel(), _dev_ptr(b), b.numel(),
+                                       _dev_ptr(scratch), n, _dev_ptr(out), out.numel(),
+                                       _dev_ptr(out_bytes), _stream_ptr(stream))
+    _check(rc, "hadamard")
+    return _finish(ctx, out, out_bytes, sync, check, "hadamard")
 
 
 def _moment(fn, what, c, out, stream, ctx, sync, check):

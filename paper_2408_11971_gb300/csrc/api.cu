@@ -357,6 +357,34 @@ int hoszp_mul_scalar_exact(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, doub
   return mul_scalar_any(ctx, d_c, c_bytes, s, d_out, cap, d_out_bytes, stream, true);
 }
 
+int hoszp_hadamard(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b,
+                   size_t b_bytes, int32_t* d_scratch, uint64_t n, void* d_out, size_t cap,
+                   uint64_t* d_out_bytes, hoszp_stream_t stream) {
+  if (!ctx || !d_a || !d_b || !d_out || !d_out_bytes || a_bytes < HOSZP_HEADER_BYTES ||
+      b_bytes < HOSZP_HEADER_BYTES || (n > 0 && !d_scratch))
+    return HOSZP_ERR_ARG;
+  if (!aligned16(d_a) || !aligned16(d_b) || !aligned16(d_out) || !aligned8(d_out_bytes) ||
+      (n > 0 && !aligned16(d_scratch)))
+    return HOSZP_ERR_ARG;
+  const uint8_t* a = (const uint8_t*)d_a;
+  const uint8_t* b = (const uint8_t*)d_b;
+  uint8_t* o = (uint8_t*)d_out;
+  if ((o < a + a_bytes && a < o + cap) || (o < b + b_bytes && b < o + cap)) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  const uint64_t nt = ntiles_of(nblocks(n));
+  const uint64_t ta = tiles_from_bytes(a_bytes);
+  // full slots: a sign word and 31 planes per block
+  int rc = ensure_ws(ctx, (ta > nt + 1 ? ta : nt + 1), 32ull * TILE * (nt + 1) + 64);
+  if (rc) return rc;
+  Launch lc = lc_of(ctx, stream);
+  rc = cuda_rc(launch_decode_q(lc, b, b_bytes, (int*)d_scratch, n, ctx->ws));
+  if (rc) return rc;
+  rc = cuda_rc(launch_hadamard(lc, a, a_bytes, b, b_bytes, (const int*)d_scratch, o, cap,
+                               ctx->ws));
+  if (rc) return rc;
+  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_FULL, 0, ctx->ws));
+}
+
 static int add_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b,
                    size_t b_bytes, void* d_out, size_t cap, uint64_t* d_out_bytes,
                    hoszp_stream_t stream, bool subtract) {

@@ -238,10 +238,11 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_var(
 // super-tile pipeline: warp i of a group decodes tile i of the stage 16
 // blocks at a time, two lanes per block (hz_lanes.cuh), to q, dequantizes
 // x' = float(q) * 2 eps_q and stores each half's 32 floats (a warp writes
-// 4 KB contiguous per step). With MEANS, the same pass writes the block-wise
-// means instead (Sec. V-B): out is a double per block and n_expect the block
-// count.
-template <bool MEANS>
+// 4 KB contiguous per step). MODE 1 writes the block-wise means instead
+// (Sec. V-B): out is a double per block and n_expect the block count. MODE 2
+// writes the quantized integers q themselves (int32, one per value), the
+// other operand of the Hadamard product.
+template <int MODE>
 __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
     const uint8_t* __restrict__ c, uint64_t c_bytes, void* __restrict__ out, uint64_t n_expect,
     Ws ws) {
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
   int bad = 0;
   bool ok = h.ok;
   if (!h.ok) bad = HOSZP_ERR_FORMAT;
-  else if ((MEANS ? h.nb : h.n) != n_expect) {
+  else if ((MODE == 1 ? h.nb : h.n) != n_expect) {
     bad = HOSZP_ERR_MISMATCH;
     ok = false;
   }
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
   } else if (w < MEAN_NCW) {
     const int grp = w / MEAN_GW, ti = w % MEAN_GW;
     const int lastlen = (int)(h.n - (h.nb - 1) * L);
-    if (MEANS) {
+    if (MODE == 1) {
       const lanes::Shifts K = lanes::make_shifts(c_bytes != 0 ? 1u : 0u);
       const double e2d = 2.0 * (double)h.eps_q;
       for (uint64_t k = 0;; k++) {
@@ -327,10 +328,23 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
           int d[8], q[8];
           octet_deltas(br, kmax, j, S, d);
           octet_values(br, d, j, q);
+          const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
+          if (MODE == 2) {  // the integers themselves
+            int* qo = static_cast<int*>(out);
+            if (br.len == L) {
+              int4* o = reinterpret_cast<int4*>(qo + i0);
+              __stcs(o, make_int4(q[0], q[1], q[2], q[3]));
+              __stcs(o + 1, make_int4(q[4], q[5], q[6], q[7]));
+            } else {
+#pragma unroll
+              for (int t = 0; t < 8; t++)
+                if (8 * j + t < br.len) qo[i0 + t] = q[t];
+            }
+            continue;
+          }
           float v[8];
 #pragma unroll
           for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
-          const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
           if (br.len == L) {
             float4* o = reinterpret_cast<float4*>(x + i0);
             __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
@@ -362,12 +376,25 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_decompress<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_decompress<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr = true;
   }
-  const int grid = persistent_grid(k_decompress<false>, MEAN_THREADS, lc.grid, smem);
-  k_decompress<false><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
+  const int grid = persistent_grid(k_decompress<0>, MEAN_THREADS, lc.grid, smem);
+  k_decompress<0><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_q(const Launch& lc, const uint8_t* c, uint64_t c_bytes, int* q,
+                           uint64_t n, Ws ws) {
+  const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_decompress<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int grid = persistent_grid(k_decompress<2>, MEAN_THREADS, lc.grid, smem);
+  k_decompress<2><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, q, n, ws);
   return cudaGetLastError();
 }
 
@@ -376,12 +403,12 @@ cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_by
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_decompress<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_decompress<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr = true;
   }
-  const int grid = persistent_grid(k_decompress<true>, MEAN_THREADS, lc.grid, smem);
-  k_decompress<true><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, out, nb, ws);
+  const int grid = persistent_grid(k_decompress<1>, MEAN_THREADS, lc.grid, smem);
+  k_decompress<1><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, out, nb, ws);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,8 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
 cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* result,
                            bool variance, Ws ws, unsigned long long* sums = nullptr,
                            bool take_sqrt = false);
+cudaError_t launch_decode_q(const Launch& lc, const uint8_t* c, uint64_t c_bytes, int* q,
+                           uint64_t n, Ws ws);
 cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* out,
                                uint64_t nb, Ws ws);
 cudaError_t launch_cov_finish(cudaStream_t s, const uint8_t* a, uint64_t a_bytes,
@@ -50,6 +52,9 @@ cudaError_t launch_sub_scalar(const Launch& lc, const uint8_t* c, uint64_t c_byt
                               uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
 cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
                               bool exact, uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws);
+cudaError_t launch_hadamard(const Launch& lc, const uint8_t* a, uint64_t a_bytes,
+                            const uint8_t* b, uint64_t b_bytes, const int* qb, uint8_t* out,
+                            uint64_t cap, Ws ws);
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, bool subtract, Ws ws);
 

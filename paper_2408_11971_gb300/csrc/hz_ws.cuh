@@ -296,12 +296,15 @@ __device__ __forceinline__ void produce_tile(uint8_t (*srate)[TILE], uint64_t kt
 // Rule MUL: (1 + e) words per non-constant input block plus the input's plane
 // words (a constant block stays constant; a rate grows by at most e bits).
 // Rule EXPLICIT: the producer wrote each tile's slot offset into pre0[2t].
-enum SlotRule { SLOT_COMPRESS = 0, SLOT_ADD = 1, SLOT_MUL = 2, SLOT_EXPLICIT = 3 };
+// Rule FULL: 32 words per block (a sign word and 31 planes), for products of
+// two fields, whose rates the inputs' rates do not bound.
+enum SlotRule { SLOT_COMPRESS = 0, SLOT_ADD = 1, SLOT_MUL = 2, SLOT_EXPLICIT = 3, SLOT_FULL = 4 };
 
 __device__ __forceinline__ uint64_t slot_offset(int rule, uint64_t t,
                                                 const unsigned long long* pre0,
                                                 const unsigned long long* pre1, uint32_t e) {
   if (rule == SLOT_COMPRESS) return (uint64_t)TILE * 25 * t;
+  if (rule == SLOT_FULL) return (uint64_t)TILE * 32 * t;
   if (rule == SLOT_ADD) return pre0[2 * t] + pre0[2 * t + 1] + pre1[2 * t] + pre1[2 * t + 1];
   if (rule == SLOT_EXPLICIT) return pre0[2 * t];
   return pre0[2 * t] * (1ull + e) + pre0[2 * t + 1];

@@ -122,6 +122,23 @@ __device__ __forceinline__ int mul_requant(int q, const MulPlan& p, bool& ovf) {
   return (int)r;
 }
 
+// Hadamard product: q' = floor(2e q_A q_B + 1/2) with the multiplier q_B of the
+// value. In 64-bit integers when every |q_A q_B M| < 2^62 (plan.fast set for
+// the product of the two header bounds), else the 128-bit path of mul_requant.
+__device__ __forceinline__ int mul_requant_pair(int qa, int qb, const MulPlan& p, bool& ovf) {
+  if (p.fast) {
+    const long long r = ((long long)qa * qb * p.M + p.half) >> p.sh;  // floor
+    if (r > HOSZP_QLIM || r < -(long long)HOSZP_QLIM) {
+      ovf = true;
+      return 0;
+    }
+    return (int)r;
+  }
+  MulPlan t = p;
+  t.rho = qb;
+  return mul_requant(qa, t, ovf);
+}
+
 // ---------------------------------------------------------------- workflow 1
 // Stream copy (out of place) with every outlier transformed (negated or
 // shifted by rho) and, for negation, every sign word inverted.
@@ -286,10 +303,14 @@ __device__ __forceinline__ void octet_mag_sign(const int d[8], uint32_t mag[8], 
 constexpr int MUL_STAGES = 8;
 constexpr uint32_t MUL_RING = 8192;  // plane-ring words (64 KB)
 
-template <bool EXACT>
+// MODE 0: the paper's operator (multiplier rho_s); 1: the scalar itself;
+// 2: the Hadamard product, with the multiplier of each value read from qb (the
+// second stream b decoded to its integers).
+template <int MODE>
 __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
-    const uint8_t* __restrict__ c, uint64_t c_bytes, double s, uint8_t* __restrict__ out,
-    uint64_t cap, uint32_t e_bits, const unsigned long long* __restrict__ pre, Ws ws) {
+    const uint8_t* __restrict__ c, uint64_t c_bytes, double s, const uint8_t* __restrict__ b,
+    uint64_t b_bytes, const int* __restrict__ qb, uint8_t* __restrict__ out, uint64_t cap,
+    uint32_t e_bits, const unsigned long long* __restrict__ pre, Ws ws) {
   extern __shared__ __align__(16) uint8_t dyn[];
   InStage* ins = reinterpret_cast<InStage*>(dyn);
   uint64_t* ring = reinterpret_cast<uint64_t*>(ins + MUL_STAGES);
@@ -305,12 +326,23 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
     int ok = h.ok;
     long long rho = 0;
     if (!h.ok) bad = HOSZP_ERR_FORMAT;
-    else if (!EXACT && !quantize_scalar(s, h.eps_q, rho)) {
+    else if (MODE == 0 && !quantize_scalar(s, h.eps_q, rho)) {
       ok = 0;
       bad = HOSZP_ERR_RANGE;
     } else if (cap < off_sign(h.nb)) {
       ok = 0;
       bad = HOSZP_ERR_CAPACITY;
+    } else if (MODE == 2) {  // the multipliers' stream: same n and eps_q
+      const Info hb = parse_header(b, b_bytes);
+      if (!hb.ok) {
+        ok = 0;
+        bad = HOSZP_ERR_FORMAT;
+      } else if (hb.n != h.n || __float_as_uint(hb.eps_q) != __float_as_uint(h.eps_q)) {
+        ok = 0;
+        bad = HOSZP_ERR_MISMATCH;
+      } else {
+        rho = hb.qbound;  // the largest multiplier, for the plan
+      }
     }
     s_ok = ok;
     s_rho = rho;
@@ -318,8 +350,16 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
   }
   ring_init3<MUL_STAGES>(full, ready, empty);
   const uint64_t ntiles = (s_ok && prescan_ok(h, pre, ws.max_tiles)) ? ntiles_of(h.nb) : 0;
-  const MulPlan mp = EXACT ? mul_plan_exact(s, h.ok ? h.qbound : 0u)
-                           : mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
+  MulPlan mp;
+  if (MODE == 1) {
+    mp = mul_plan_exact(s, h.ok ? h.qbound : 0u);
+  } else if (MODE == 2) {
+    // plan for the largest multiplier: its 64-bit path bounds every product
+    mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
+    mp.f32 = false;
+  } else {
+    mp = mul_plan(h.ok ? h.eps_q : 1.0f, s_rho, h.ok ? h.qbound : 0u);
+  }
   const OctetSel S = octet_sel(j);
   uint32_t qmax = 0;
   bool ovf = false;
@@ -365,7 +405,21 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
         for (int t = 0; t < 8; t++)
           if (8 * j + t >= br.len) q[t] = 0;
       }
-      if (mp.f32) {
+      if (MODE == 2) {  // Hadamard product: this octet's multipliers
+        const uint64_t i0 = (tile * TILE + g) * L + 8 * j;
+        int m8[8];
+        if (br.len == L) {
+          const int4 u0 = __ldcs(reinterpret_cast<const int4*>(qb + i0));
+          const int4 u1 = __ldcs(reinterpret_cast<const int4*>(qb + i0) + 1);
+          m8[0] = u0.x; m8[1] = u0.y; m8[2] = u0.z; m8[3] = u0.w;
+          m8[4] = u1.x; m8[5] = u1.y; m8[6] = u1.z; m8[7] = u1.w;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; t++) m8[t] = (8 * j + t < br.len) ? qb[i0 + t] : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; t++) q[t] = mul_requant_pair(q[t], m8[t], mp, ovf);
+      } else if (mp.f32) {
 #pragma unroll
         for (int t = 0; t < 8; t++) q[t] = mul_requant_f32(q[t], mp);
       } else if (mp.fast) {
@@ -397,7 +451,8 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
       octet_mag_sign(nd, mag, sb);
       const int rate = octet_rate(mag);
       produce_tile(srate, k, tile, h.nb, mag, sb, rate, outlier, tile * TILE + g < h.nb, g, j,
-                   out, ws.staging, slot_offset(SLOT_MUL, tile, pre, nullptr, e_bits),
+                   out, ws.staging,
+                   slot_offset(MODE == 2 ? SLOT_FULL : SLOT_MUL, tile, pre, nullptr, e_bits),
                    ws.staging_words, ws.agg, S, bad);
     }
   }
@@ -406,28 +461,36 @@ __global__ void __launch_bounds__(PRODUCER_THREADS, 2) k_mul_scalar(
   if (bad) set_status(ws.status, bad);
 }
 
-cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
-                              bool exact, uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
+template <int MODE>
+static cudaError_t launch_mul_mode(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
+                                   const uint8_t* b, uint64_t b_bytes, const int* qb,
+                                   uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
   const size_t smem = MUL_STAGES * sizeof(InStage) + MUL_RING * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_mul_scalar<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaFuncSetAttribute(k_mul_scalar<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mul_scalar<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr = true;
   }
-  if (exact)
-    k_mul_scalar<true><<<persistent_grid(k_mul_scalar<true>, PRODUCER_THREADS, lc.grid, smem),
-                         PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, out, cap, e_bits,
-                                                              ws.pre[0], ws);
-  else
-    k_mul_scalar<false><<<persistent_grid(k_mul_scalar<false>, PRODUCER_THREADS, lc.grid, smem),
-                          PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, out, cap, e_bits,
-                                                               ws.pre[0], ws);
+  k_mul_scalar<MODE><<<persistent_grid(k_mul_scalar<MODE>, PRODUCER_THREADS, lc.grid, smem),
+                       PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, b, b_bytes, qb, out,
+                                                            cap, e_bits, ws.pre[0], ws);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mul_scalar(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double s,
+                              bool exact, uint32_t e_bits, uint8_t* out, uint64_t cap, Ws ws) {
+  return exact ? launch_mul_mode<1>(lc, c, c_bytes, s, nullptr, 0, nullptr, e_bits, out, cap, ws)
+               : launch_mul_mode<0>(lc, c, c_bytes, s, nullptr, 0, nullptr, e_bits, out, cap, ws);
+}
+
+// Hadamard product (Sec. V-C): b's integers already decoded into qb.
+cudaError_t launch_hadamard(const Launch& lc, const uint8_t* a, uint64_t a_bytes,
+                            const uint8_t* b, uint64_t b_bytes, const int* qb, uint8_t* out,
+                            uint64_t cap, Ws ws) {
+  return launch_mul_mode<2>(lc, a, a_bytes, 0.0, b, b_bytes, qb, 0u, out, cap, ws);
 }
 
 // ---------------------------------------------------------------- element-wise addition

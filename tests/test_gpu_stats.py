@@ -209,3 +209,42 @@ def test_mul_scalar_exact_grf_and_wide(hz):
     with pytest.raises(hz.HoszpError) as ex:
         hz.mul_scalar_exact(cw, 1000.0)
     assert ex.value.name == "OVERFLOW"
+
+
+@pytest.mark.parametrize("name", list(CASES.keys()))
+def test_hadamard_small_cases(hz, name):
+    x = CASES[name]
+    y = (x[::-1].copy() * np.float32(-0.75) + np.float32(0.125)).astype(np.float32)
+    c = hz.compress(dev(x), eb=0.05, dims=(x.size,))
+    d = hz.compress(dev(y), eb=0.05, dims=(y.size,))
+    oc, od = host(c), host(d)
+    assert np.array_equal(host(hz.hadamard(c, d)), O.hadamard(oc, od))
+    assert np.array_equal(host(hz.hadamard(hz.negate(c), d)), O.hadamard(O.negate(oc), od))
+
+
+def test_hadamard_grf_constant_and_errors(hz):
+    shape = (449, 45, 23)
+    x = datagen.grf(shape, seed=41).reshape(-1)
+    y = datagen.grf(shape, seed=42).reshape(-1)
+    c = hz.compress(dev(x), eb=1e-3, mode="rel", dims=shape)
+    e = float(O.header(host(c))["eps_q"])
+    d = hz.compress(dev(y), eb=e, dims=shape)
+    oc, od = host(c), host(d)
+    z = hz.hadamard(c, d)
+    assert np.array_equal(host(z), O.hadamard(oc, od))
+    # a constant field s: the scalar multiplication by s, byte for byte
+    s = np.float32(3.14)
+    k = hz.compress(dev(np.full(x.size, s, np.float32)), eb=e, dims=shape)
+    assert np.array_equal(host(hz.hadamard(c, k)), host(hz.mul_scalar(c, float(s))))
+    # large products: q_A up to 2^22, q_B up to 100
+    n = 64 * 37 + 11
+    w = np.where(np.arange(n) % 2 == 0, 4194304.0, -4194304.0).astype(np.float32)
+    v = (100.0 * np.sin(0.05 * np.arange(n))).astype(np.float32)
+    cw, cv = hz.compress(dev(w), eb=0.5), hz.compress(dev(v), eb=0.5)
+    assert np.array_equal(host(hz.hadamard(cw, cv)), O.hadamard(host(cw), host(cv)))
+    with pytest.raises(hz.HoszpError) as ex:
+        hz.hadamard(cw, cw)  # 2^44: beyond the integer range
+    assert ex.value.name == "OVERFLOW"
+    with pytest.raises(hz.HoszpError) as ex:
+        hz.hadamard(c, hz.compress(dev(y), eb=2 * e, dims=shape))
+    assert ex.value.name == "MISMATCH"
