@@ -354,6 +354,36 @@ def batched_bench(hz, xa, xb, nfields: int, seed: int = 3, reps: int = 5):
                      "batched_orig_gbs": orig / bms / 1e6,
                      "batched_frac_of_measured_hbm": cbytes / bms / 1e6 / measured_peak()[0],
                      "identical_to_per_field": bool(torch.equal(res, per))}
+    # decompression of every field in one launch against field-by-field calls
+    offs = np.concatenate([[0], np.cumsum((sizes.astype(np.int64) + 3) // 4 * 4)])
+    big = torch.empty(int(offs[-1]), dtype=torch.float32, device=xa.device)
+    outs = [big[int(offs[i]):int(offs[i]) + int(sizes[i])] for i in range(nfields)]
+    b.decompress(outs, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(reps):
+        b.decompress(outs, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / reps
+    b.check("decompress")
+    first = big.clone()
+    for i, c in enumerate(streams):  # warm the per-field path
+        hz.decompress(c, out=outs[i], check=False)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for i, c in enumerate(streams):
+        hz.decompress(c, out=outs[i], check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    fms = e0.elapsed_time(e1)
+    out["decompress"] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
+                         "batched_orig_gbs": orig / bms / 1e6,
+                         "batched_frac_of_measured_hbm": (cbytes + orig) / bms / 1e6 / measured_peak()[0],
+                         "identical_to_per_field": bool(torch.equal(first, big))}
+    del big, first, outs
     b.close()
     del streams
     torch.cuda.empty_cache()

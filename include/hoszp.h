@@ -291,6 +291,12 @@ int hoszp_batch_get_status(hoszp_batch* b, int* status);
 int hoszp_batch_mean(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
 int hoszp_batch_var(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
 
+/* Decompression of every field (Fig. 2) in one persistent launch: field f's n_f
+ * floats go to d_outs[f]. d_outs: device array of nfields device pointers, each
+ * 16-byte aligned with room for its field's n_f floats (caller-owned). Each
+ * output equals hoszp_decompress of field f, bit for bit. */
+int hoszp_batch_decompress(hoszp_batch* b, float* const* d_outs, hoszp_stream_t stream);
+
 /* In place on every field: negation (Sec. V-A), and scalar addition with the
  * same s for all fields, each field quantizing s with its own eps (Eq. 3).
  * A field whose rho_s or bound would leave the integer range is left

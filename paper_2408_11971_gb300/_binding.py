@@ -91,6 +91,7 @@ def load_library():
             "hoszp_batch_get_status": (I, [P, ctypes.POINTER(I)]),
             "hoszp_batch_mean": (I, [P, P, P]),
             "hoszp_batch_var": (I, [P, P, P]),
+            "hoszp_batch_decompress": (I, [P, P, P]),
             "hoszp_batch_negate": (I, [P, P]),
             "hoszp_batch_add_scalar": (I, [P, D, P]),
             "hoszp_batch_tune": (I, [P, P, P]),
@@ -556,6 +557,23 @@ class Batch:
     def var(self, out=None, stream=None, sync: bool = True, check: bool = True):
         """Per-field population variances (Sec. V-B), one launch."""
         return self._moment(self._lib.hoszp_batch_var, "batch_var", out, stream, sync, check)
+
+    def decompress(self, outs=None, stream=None, sync: bool = True, check: bool = True):
+        """Every field decompressed (Fig. 2), one launch: a list of float32 CUDA
+        tensors (allocated when not given, n_f values each)."""
+        torch = _torch()
+        if outs is None:
+            outs = [torch.empty(header(c)["n"], dtype=torch.float32, device=self.device)
+                    for c in self._streams]
+        ptrs = torch.tensor([o.data_ptr() for o in outs], dtype=torch.int64, device=self.device)
+        _check(self._lib.hoszp_batch_decompress(self.handle, _dev_ptr(ptrs), _stream_ptr(stream)),
+               "batch_decompress")
+        self._ptrs = ptrs  # kept alive until the next call (the launch reads it)
+        if sync:
+            torch.cuda.synchronize(self.device)
+            if check:
+                self.check("batch_decompress")
+        return outs
 
     def negate(self, stream=None):
         """Every field negated in place (Sec. V-A), one launch."""

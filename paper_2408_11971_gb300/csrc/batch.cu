@@ -315,11 +315,13 @@ __device__ __forceinline__ void bflush(const BField* F, uint32_t f, __int128 s1,
   }
 }
 
-template <bool VAR>
+// MODE 0: mean, 1: variance (per-field exact sums, finished by the warp that
+// completes a field), 2: decompression into each field's output outs[f].
+template <int MODE>
 __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
     const BField* __restrict__ F, uint32_t nf, uint64_t total_tiles,
     const unsigned long long* __restrict__ pre, unsigned long long* acc, unsigned int* done,
-    double* results, int* status) {
+    double* results, int* status, float* const* __restrict__ outs) {
   extern __shared__ __align__(16) uint8_t dyn[];
   SStage* stages = reinterpret_cast<SStage*>(dyn);
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + BS_STAGES);
@@ -420,11 +422,11 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
     uint32_t cur = ~0u;
     unsigned int cnt = 0;
     auto flush = [&]() {
-      if (VAR) {
+      if (MODE == 1) {
         bflush<true>(F, cur, (__int128)v1, v2, cnt, acc, done, results);
         v1 = 0;
         v2 = {0, 0};
-      } else {
+      } else if (MODE == 0) {
         A.flush();
         bflush<false>(F, cur, A.s1, U128{0, 0}, cnt, acc, done, results);
         A.s1 = 0;
@@ -450,7 +452,42 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
         const TileRates tr = tile_rates(sg, ti, tile, h.nb);
         const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
         const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
-        if (!VAR) {
+        if (MODE == 2) {  // octet decode, as the single-stream decompression
+          float* __restrict__ x = outs[cur];
+          const int j = lane & 7, gq = lane >> 3;
+          const OctetSel S = octet_sel(j);
+          const float e2 = 2.0f * h.eps_q;
+          const bool small = h.qbound < (1u << 22);
+          const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
+          for (int it = 0; it < steps; it++) {
+            const int b = 4 * it + gq;
+            uint32_t r, ex;
+            tile_block(tr, b, r, ex);
+            BlockRef br;
+            br.rate = (int)r;
+            br.outlier = sg.outlier[TILE * ti + b];
+            br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+            br.planes = pls + (ex & 0xffffu);
+            br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
+            const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
+            int d[8], q[8];
+            octet_deltas(br, kmax, j, S, d);
+            octet_values(br, d, j, q);
+            float v[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+            const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
+            if (br.len == L) {
+              float4* o = reinterpret_cast<float4*>(x + i0);
+              __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
+              __stcs(o + 1, make_float4(v[4], v[5], v[6], v[7]));
+            } else {
+#pragma unroll
+              for (int t = 0; t < 8; t++)
+                if (8 * j + t < br.len) x[i0 + t] = v[t];
+            }
+          }
+        } else if (MODE == 0) {
 #pragma unroll 1
           for (int jj = 0; jj < 2; jj++) {  // blocks 2 lane and 2 lane + 1
             const int b = 2 * lane + jj;
@@ -473,18 +510,18 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
   }
 }
 
-template <bool VAR>
+template <int MODE>
 cudaError_t launch_bsuper(int num_sms, cudaStream_t s, const BField* F, uint32_t nf,
                           uint64_t total_tiles, const unsigned long long* pre,
                           unsigned long long* acc, unsigned int* done, double* results,
-                          int* status) {
+                          int* status, float* const* outs = nullptr) {
   const size_t smem = BS_STAGES * sizeof(SStage) + BS_RING * sizeof(uint64_t);
   static std::once_flag once;
   std::call_once(once, [&]() {
-    cudaFuncSetAttribute(k_bsuper<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_bsuper<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_bsuper<VAR><<<persistent_grid(k_bsuper<VAR>, BS_THREADS, num_sms, smem), BS_THREADS, smem, s>>>(
-      F, nf, total_tiles, pre, acc, done, results, status);
+  k_bsuper<MODE><<<persistent_grid(k_bsuper<MODE>, BS_THREADS, num_sms, smem), BS_THREADS, smem,
+                   s>>>(F, nf, total_tiles, pre, acc, done, results, status, outs);
   return cudaGetLastError();
 }
 
@@ -633,10 +670,10 @@ int run_moments(hoszp_batch* b, bool var, const BatchCfg& c, double* d_results,
   const int grid = b->num_sms * c.cps;
   cudaError_t e;
   if (c.variant == 2)
-    e = var ? launch_bsuper<true>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
-                                  b->d_acc, b->d_done, d_results, b->status)
-            : launch_bsuper<false>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
-                                   b->d_acc, b->d_done, d_results, b->status);
+    e = var ? launch_bsuper<1>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
+                               b->d_acc, b->d_done, d_results, b->status)
+            : launch_bsuper<0>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
+                               b->d_acc, b->d_done, d_results, b->status);
   else if (var)
     e = c.variant == 0 ? launch_bmoments<true, 8>(grid, s, b->d_fields, b->nf, b->total_tiles,
                                                    b->d_pre, b->d_acc, b->d_done, d_results,
@@ -802,6 +839,14 @@ int hoszp_batch_var(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
   if (!b || !d_results || ((uintptr_t)d_results & 7u)) return HOSZP_ERR_ARG;
   DeviceGuard guard(b->device);
   return run_moments(b, true, b->cfg[1], d_results, (cudaStream_t)stream);
+}
+
+int hoszp_batch_decompress(hoszp_batch* b, float* const* d_outs, hoszp_stream_t stream) {
+  if (!b || !d_outs || ((uintptr_t)d_outs & 7u)) return HOSZP_ERR_ARG;
+  DeviceGuard guard(b->device);
+  return rc_of(launch_bsuper<2>(b->num_sms, (cudaStream_t)stream, b->d_fields, b->nf,
+                                b->total_tiles, b->d_pre, b->d_acc, b->d_done, nullptr, b->status,
+                                d_outs));
 }
 
 int hoszp_batch_negate(hoszp_batch* b, hoszp_stream_t stream) {

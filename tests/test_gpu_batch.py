@@ -86,6 +86,21 @@ def test_batch_reductions(hz, fields):
     assert np.array_equal(host(b.mean()), m) and np.array_equal(host(b.var()), v)
 
 
+def test_batch_decompress(hz, fields):
+    """One launch decompresses every field: bit for bit the single-stream
+    decompression and the oracle's."""
+    _, _, cs, ocs = fields
+    b = hz.Batch([c.clone() for c in cs])
+    outs = b.decompress()
+    for f, (c, oc) in enumerate(zip(cs, ocs)):
+        got = host(outs[f])
+        assert np.array_equal(got, host(hz.decompress(c))), f
+        assert np.array_equal(got, O.decompress(oc)), f
+    again = b.decompress()  # repeated launches
+    for f in range(len(cs)):
+        assert np.array_equal(host(again[f]), host(outs[f])), f
+
+
 def test_batch_in_place_operators(hz, fields):
     _, _, cs, ocs = fields
     work = [c.clone() for c in cs]
