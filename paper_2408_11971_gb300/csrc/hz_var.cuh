@@ -30,29 +30,6 @@ __device__ __forceinline__ lanes::HalfSums half_sums_any(int Rw, bool full, bool
   return lanes::half_sums<4, true, true>(t, nval, zero0, K);
 }
 
-// half_visit of hz_lanes.cuh for the warp's widest rate Rw.
-template <class F>
-__device__ __forceinline__ void half_visit_any(int Rw, const uint32_t t[32], bool zero0,
-                                               const lanes::Shifts& K, F&& f) {
-  switch ((Rw + 8) >> 3) {
-    case 1: lanes::half_visit<1>(t, zero0, K, f); break;
-    case 2: lanes::half_visit<2>(t, zero0, K, f); break;
-    case 3: lanes::half_visit<3>(t, zero0, K, f); break;
-    default: lanes::half_visit<4>(t, zero0, K, f); break;
-  }
-}
-
-// Local prefixes p[0..31] of this lane's half for the warp's widest rate Rw.
-__device__ __forceinline__ void half_prefix_any(int Rw, const uint32_t t[32], bool zero0,
-                                                const lanes::Shifts& K, int p[32]) {
-  switch ((Rw + 8) >> 3) {
-    case 1: lanes::half_prefix<1>(t, zero0, K, p); break;
-    case 2: lanes::half_prefix<2>(t, zero0, K, p); break;
-    case 3: lanes::half_prefix<3>(t, zero0, K, p); break;
-    default: lanes::half_prefix<4>(t, zero0, K, p); break;
-  }
-}
-
 // Tile `ti` of stage sg (rates in tr, tile index `tile` of a stream of
 // `ntiles` tiles whose last block holds `lastlen` values): adds this lane's
 // share of S1 and S2. The warp takes 16 blocks per step; lane 2m + hf holds
