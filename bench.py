@@ -90,7 +90,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: HOSZP_CLOCK_DIR if set, else the system's temporary directory
+        import tempfile
+
+        d = os.environ.get("HOSZP_CLOCK_DIR", tempfile.gettempdir())
+        self.path = os.path.join(d, f"hoszp_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
