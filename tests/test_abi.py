@@ -55,6 +55,14 @@ def test_compress_bound_and_host_checks(lib):
     assert L.hoszp_ctx_create(None, 0) == -1
     assert L.hoszp_compress(None, None, 0, None, 1, 1.0, 0, None, 0, None, None) == -1
     assert L.hoszp_mean(None, None, 0, None, None) == -1
+    # the operators beyond the step: null context or buffers are argument errors
+    assert L.hoszp_sub_scalar(None, None, 0, 1.0, None, 0, None, None) == -1
+    assert L.hoszp_mul_scalar_exact(None, None, 0, 1.0, None, 0, None, None) == -1
+    assert L.hoszp_std(None, None, 0, None, None) == -1
+    assert L.hoszp_block_means(None, None, 0, None, 0, None) == -1
+    assert L.hoszp_cov(None, None, 0, None, 0, None, None) == -1
+    assert L.hoszp_hadamard(None, None, 0, None, 0, None, 0, None, 0, None, None) == -1
+    assert L.hoszp_batch_decompress(None, None, None) == -1
 
 
 def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
