@@ -1,0 +1,124 @@
+// Host check of the two-lanes-per-block decode (hz_lanes.cuh) against brute
+// force: random blocks of every rate 0..31 (Delta_0 := 0, signs on zero
+// magnitudes, bits at position 0 that must be ignored, short last blocks, the
+// narrow and wide accumulations), each decoded as two 32-position halves and
+// recombined into the block's exact sums S1 = sum q and S2 = sum q^2.
+// The device intrinsics (byte permute, high multiply) run as the header's
+// host definitions.
+#include <cstdint>
+#include <cstdio>
+
+#include "hz_lanes.cuh"
+
+using namespace hz::lanes;
+
+static uint64_t g_state = 0x9E3779B97F4A7C15ull;
+static uint64_t rnd() {
+  g_state ^= g_state << 13;
+  g_state ^= g_state >> 7;
+  g_state ^= g_state << 17;
+  return g_state;
+}
+
+template <int G, bool FULL, bool WIDE>
+static HalfSums run(const uint32_t t[32], int nval, bool z0) {
+  return half_sums<G, FULL, WIDE>(t, nval, z0, make_shifts(1u));
+}
+static HalfSums run_any(int G, bool full, bool wide, const uint32_t t[32], int nval, bool z0) {
+  if (!full) wide = true;
+  switch (G) {
+    case 1: return !full ? run<1, false, true>(t, nval, z0) : wide ? run<1, true, true>(t, nval, z0) : run<1, true, false>(t, nval, z0);
+    case 2: return !full ? run<2, false, true>(t, nval, z0) : wide ? run<2, true, true>(t, nval, z0) : run<2, true, false>(t, nval, z0);
+    case 3: return !full ? run<3, false, true>(t, nval, z0) : wide ? run<3, true, true>(t, nval, z0) : run<3, true, false>(t, nval, z0);
+    default: return !full ? run<4, false, true>(t, nval, z0) : wide ? run<4, true, true>(t, nval, z0) : run<4, true, false>(t, nval, z0);
+  }
+}
+
+int main() {
+  // the 8x8 bit transpose is a transpose
+  for (int it = 0; it < 2000; it++) {
+    const uint32_t lo = (uint32_t)rnd(), hi = (uint32_t)rnd();
+    uint32_t a = lo, b = hi;
+    tr8x8(a, b, make_shifts(1u));
+    for (int t = 0; t < 8; t++)
+      for (int k = 0; k < 8; k++) {
+        const uint32_t in = (k < 4 ? lo >> (8 * k) : hi >> (8 * (k - 4))) & 0xffu;
+        const uint32_t out = (t < 4 ? a >> (8 * t) : b >> (8 * (t - 4))) & 0xffu;
+        if (((out >> k) & 1u) != ((in >> t) & 1u)) {
+          printf("tr8x8 differs\n");
+          return 1;
+        }
+      }
+  }
+  const long long QL = (1ll << 30) - 1;
+  long fails = 0;
+  for (int it = 0; it < 100000; it++) {
+    const int Rw = (int)(rnd() % 32);
+    int r = Rw ? (int)(rnd() % (Rw + 1)) : 0;
+    if (rnd() % 4 == 0) r = Rw;
+    int len = 64;
+    if (rnd() % 5 == 0) len = 1 + (int)(rnd() % 64);
+    const bool qsmall = (rnd() % 2) == 0;
+    const long long lim = qsmall ? (1ll << 13) - 1 : QL;
+    long long O = (long long)(rnd() % (2 * lim + 1)) - lim;
+    uint64_t mag[64], sign = 0, planes[32] = {0};
+    long long q = O;
+    for (int i = 0; i < 64; i++) {
+      long long m = r ? (long long)(rnd() & ((1ull << r) - 1)) : 0;
+      long long d = (rnd() & 1) ? -m : m;
+      if (i == 0) d = 0;
+      if (q + d > lim || q + d < -lim) d = -d;
+      if (q + d > lim) d = lim - q;
+      if (q + d < -lim) d = -lim - q;
+      q += d;
+      mag[i] = (uint64_t)(d < 0 ? -d : d);
+      if (d < 0) sign |= 1ull << i;
+      else if (r && rnd() % 7 == 0) sign |= 1ull << i;  // a sign on a zero magnitude
+      if (d > 0) sign &= ~(1ull << i);
+    }
+    if (r && (rnd() % 2)) mag[0] = rnd() & ((1ull << r) - 1);  // ignored: Delta_0 := 0
+    for (int p = 0; p < r; p++)
+      for (int i = 0; i < 64; i++) planes[p] |= ((mag[i] >> p) & 1ull) << i;
+    __int128 S1 = 0, S2 = 0;
+    long long v = O;
+    for (int i = 0; i < len; i++) {
+      const long long d = (i == 0) ? 0 : (((sign >> i) & 1) ? -(long long)mag[i] : (long long)mag[i]);
+      v += d;
+      S1 += v;
+      S2 += (__int128)v * v;
+    }
+    uint32_t half_words[64];
+    for (int p = 0; p < 32; p++) {
+      half_words[2 * p] = (uint32_t)planes[p];
+      half_words[2 * p + 1] = (uint32_t)(planes[p] >> 32);
+    }
+    const int G = (Rw + 8) >> 3;
+    const bool wide = !(Rw <= 8 || qsmall) || (rnd() % 2);
+    HalfSums hs[2];
+    int nv[2];
+    for (int h = 0; h < 2; h++) {
+      uint32_t t[32];
+      twos_planes_any(Rw, half_words + h, r, r ? (uint32_t)(sign >> (32 * h)) : 0u, t);
+      nv[h] = len - 32 * h < 0 ? 0 : (len - 32 * h > 32 ? 32 : len - 32 * h);
+      hs[h] = run_any(G, len == 64, wide, t, nv[h], h == 0);
+    }
+    __int128 T1 = 0, T2 = 0;
+    for (int h = 0; h < 2; h++) {
+      const long long base = O + (h ? hs[0].tot : 0);
+      const __int128 sq = (wide || len != 64) ? (((__int128)hs[h].sqh << 64) | hs[h].sq)
+                                             : (__int128)hs[h].sq;
+      T1 += (__int128)nv[h] * base + hs[h].sp;
+      T2 += (__int128)nv[h] * base * base + (__int128)2 * base * hs[h].sp + sq;
+    }
+    if (T1 != S1 || T2 != S2) {
+      if (fails < 5) printf("differs: Rw %d r %d len %d\n", Rw, r, len);
+      fails++;
+    }
+  }
+  if (fails) {
+    printf("%ld blocks differ\n", fails);
+    return 1;
+  }
+  printf("ok\n");
+  return 0;
+}
