@@ -638,7 +638,7 @@ def main():
         elif op == "hadamard":
             hz.hadamard(sa, sb, out=outb, out_bytes=outs, scratch=qscratch, ctx=ctx, sync=False)
 
-    # covariance reads A and B twice and writes and reads A + B (composition of exact operators)
+    # covariance reads A and B once (one pass, exact sums)
     xalg = {"sub_scalar": 2 * C["ca"], "std": C["ca"], "block_means": C["ca"] + 8 * nbk,
             "cov": C["ca"] + C["cb"], "mul_scalar_exact": None, "hadamard": None}
     qscratch = torch.empty(n, dtype=torch.int32, device=dev)  # B's integers (Hadamard product)

@@ -218,15 +218,13 @@ int hoszp_block_means(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d
                       hoszp_stream_t stream);
 
 /* Population covariance of two streams, Sec. V-D "Covariance" (done like the
- * variance of Sec. V-B, over two fields): 2 eps (2 eps) (n S_AB - S1_A S1_B) / n^2
- * with S_AB = sum q_A q_B, S1_A = sum q_A, S1_B = sum q_B exact integers,
- * finished in FP64 into the device double *d_result. S_AB comes from the
- * homomorphic sum: (q_A + q_B)^2 = q_A^2 + 2 q_A q_B + q_B^2, so
- * S_AB = (S2(A+B) - S2(A) - S2(B)) / 2 with A + B formed as by hoszp_add. The
- * streams must agree in n and eps_q and their qbounds may add up to at most
- * HOSZP_QLIM (device status MISMATCH / OVERFLOW otherwise, as for hoszp_add);
- * n = 0 -> ARG. The context keeps a scratch buffer of a_bytes + b_bytes + 320
- * bytes for A + B (allocated on first use and when it must grow). */
+ * variance of Sec. V-B, over two fields): 2 eps_A 2 eps_B (n S_AB - S1_A S1_B) / n^2
+ * with S_AB = sum q_A q_B, S1_A = sum q_A, S1_B = sum q_B exact integers from
+ * one pass over both streams, finished in FP64 into the device double
+ * *d_result. The streams must hold the same number of values n (device status
+ * MISMATCH otherwise); their error bounds may differ, since each side is scaled
+ * by its own 2 eps_q. n = 0 -> ARG. Needs no memory beyond the context's
+ * workspace. */
 int hoszp_cov(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
               double* d_result, hoszp_stream_t stream);
 

@@ -420,8 +420,8 @@ def std(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = Tru
 
 
 def cov(a, b, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):
-    """Population covariance of two streams with the same bound, from exact
-    integer sums (Sec. V-D)."""
+    """Population covariance of two streams of one length (their bounds may
+    differ), from exact integer sums in one pass (Sec. V-D)."""
     torch = _torch()
     a = _stream_tensor(a)
     b = _stream_tensor(b)

@@ -19,8 +19,6 @@ struct hoszp_ctx {
   size_t ws_bytes;
   uint64_t ws_tiles, ws_staging_words, ws_grid;
   Ws ws;
-  void* cov_mem;     // covariance scratch: 3 x 5 sum words, then the stream A + B
-  size_t cov_bytes;
 };
 
 namespace {
@@ -198,7 +196,6 @@ void hoszp_ctx_destroy(hoszp_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->ws_mem) cudaFree(ctx->ws_mem);
-  if (ctx->cov_mem) cudaFree(ctx->cov_mem);
   delete ctx;
 }
 
@@ -418,8 +415,7 @@ int hoszp_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, 
   return add_sub(ctx, d_a, a_bytes, d_b, b_bytes, d_out, cap, d_out_bytes, stream, true);
 }
 
-// Covariance as a composition of exact operators: the sums of A, B and of the
-// homomorphic sum A + B give S_AB = (S2(A+B) - S2(A) - S2(B)) / 2 exactly.
+// Covariance in one pass over both streams (k_cov).
 int hoszp_cov(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,
               double* d_result, hoszp_stream_t stream) {
   if (!ctx || !d_a || !d_b || !d_result || a_bytes < HOSZP_HEADER_BYTES ||
@@ -427,36 +423,11 @@ int hoszp_cov(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, 
     return HOSZP_ERR_ARG;
   if (!aligned16(d_a) || !aligned16(d_b) || !aligned8(d_result)) return HOSZP_ERR_ARG;
   DeviceGuard g(ctx->device);
-  // a block of A + B needs at most the words of A's and B's blocks
-  const size_t cap = a_bytes + b_bytes + 64;
-  const size_t need = 256 + cap;
-  if (ctx->cov_bytes < need) {
-    if (ctx->cov_mem) {
-      cudaDeviceSynchronize();
-      cudaFree(ctx->cov_mem);
-      ctx->cov_mem = nullptr;
-      ctx->cov_bytes = 0;
-    }
-    if (cudaMalloc(&ctx->cov_mem, need) != cudaSuccess) {
-      cudaGetLastError();
-      ctx->cov_mem = nullptr;
-      return HOSZP_ERR_CUDA;
-    }
-    ctx->cov_bytes = need;
-  }
-  unsigned long long* sums = (unsigned long long*)ctx->cov_mem;  // A: 0-4, B: 5-9, A+B: 10-14
-  uint64_t* sum_bytes = (uint64_t*)(sums + 15);
-  uint8_t* tmp = (uint8_t*)ctx->cov_mem + 256;
-  int rc = hoszp_sums(ctx, d_a, a_bytes, (uint64_t*)sums, stream);
+  const uint64_t ta = tiles_from_bytes(a_bytes), tb = tiles_from_bytes(b_bytes);
+  int rc = ensure_ws(ctx, ta > tb ? ta : tb, 16);
   if (rc) return rc;
-  rc = hoszp_sums(ctx, d_b, b_bytes, (uint64_t*)(sums + 5), stream);
-  if (rc) return rc;
-  rc = add_sub(ctx, d_a, a_bytes, d_b, b_bytes, tmp, cap, sum_bytes, stream, false);
-  if (rc) return rc;
-  rc = hoszp_sums(ctx, tmp, cap, (uint64_t*)(sums + 10), stream);
-  if (rc) return rc;
-  return cuda_rc(launch_cov_finish((cudaStream_t)stream, (const uint8_t*)d_a, a_bytes, sums,
-                                   sums + 5, sums + 10, d_result, ctx->ws.status));
+  return cuda_rc(launch_cov(lc_of(ctx, stream), (const uint8_t*)d_a, a_bytes, (const uint8_t*)d_b,
+                            b_bytes, d_result, ctx->ws));
 }
 
 static int moments(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,

@@ -432,42 +432,4 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
   return cudaGetLastError();
 }
 
-
-// ---------------------------------------------------------------- covariance finish
-// Covariance (Sec. V-D) from the exact sums of A, B and A + B (hoszp_sums
-// layout: S1 two's complement in words 0-1, S2 in words 2-3, n in word 4):
-// S_AB = sum q_A q_B = (S2(A+B) - S2(A) - S2(B)) / 2 exactly, since
-// (q_A + q_B)^2 = q_A^2 + 2 q_A q_B + q_B^2; then the FP64 finish.
-__global__ void k_cov_finish(const uint8_t* a, uint64_t a_bytes, const unsigned long long* sa,
-                             const unsigned long long* sb, const unsigned long long* sab,
-                             double* result, int* status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const Info h = parse_header(a, a_bytes);
-  auto s1 = [](const unsigned long long* w) {
-    return (__int128)(((unsigned __int128)w[1] << 64) | w[0]);
-  };
-  auto s2 = [](const unsigned long long* w) {
-    return (unsigned __int128)(((unsigned __int128)w[3] << 64) | w[2]);
-  };
-  double res = 0.0;
-  if (!h.ok) {
-    set_status(status, HOSZP_ERR_FORMAT);
-  } else if (sa[4] != h.n || sb[4] != h.n || sab[4] != h.n) {
-    set_status(status, HOSZP_ERR_MISMATCH);  // the sum stream was not produced
-  } else if (h.n == 0) {
-    set_status(status, HOSZP_ERR_ARG);
-  } else {
-    const __int128 cross = (__int128)(s2(sab) - s2(sa) - s2(sb)) / 2;  // even, exact
-    res = cov_finish(cross, s1(sa), s1(sb), h.n, h.eps_q, h.eps_q);
-  }
-  *result = res;
-}
-
-cudaError_t launch_cov_finish(cudaStream_t s, const uint8_t* a, uint64_t a_bytes,
-                              const unsigned long long* sa, const unsigned long long* sb,
-                              const unsigned long long* sab, double* result, int* status) {
-  k_cov_finish<<<1, 32, 0, s>>>(a, a_bytes, sa, sb, sab, result, status);
-  return cudaGetLastError();
-}
-
 }  // namespace hz

@@ -40,9 +40,6 @@ cudaError_t launch_decode_q(const Launch& lc, const uint8_t* c, uint64_t c_bytes
                            uint64_t n, Ws ws);
 cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* out,
                                uint64_t nb, Ws ws);
-cudaError_t launch_cov_finish(cudaStream_t s, const uint8_t* a, uint64_t a_bytes,
-                              const unsigned long long* sa, const unsigned long long* sb,
-                              const unsigned long long* sab, double* result, int* status);
 // ops.cu
 cudaError_t launch_negate(const Launch& lc, const uint8_t* c, uint64_t c_bytes, uint8_t* out,
                           uint64_t cap, uint64_t* out_bytes, Ws ws);
@@ -57,6 +54,8 @@ cudaError_t launch_hadamard(const Launch& lc, const uint8_t* a, uint64_t a_bytes
                             uint64_t cap, Ws ws);
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, bool subtract, Ws ws);
+cudaError_t launch_cov(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
+                       uint64_t b_bytes, double* result, Ws ws);
 
 // Persistent grid: SMs x resident CTAs per SM of `kernel` (capped at 8).
 template <typename K>

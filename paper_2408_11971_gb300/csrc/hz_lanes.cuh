@@ -247,5 +247,44 @@ HZL_HD HalfSums half_sums(const uint32_t t[32], int nval, bool zero0, const Shif
   return hs;
 }
 
+// The local prefixes p_i (i = 0 .. 31) of one half (steps 2 and 3), handed to
+// f(i, p_i) in position order (once unrolled, i is a compile-time constant in
+// each call). Positions past the block's end are not masked.
+template <int G, class F>
+HZL_HD void half_visit(const uint32_t t[32], bool zero0, const Shifts& K, F&& f) {
+  uint32_t X[4][4], Y[4][4];
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    bt4x4(t[8 * g], t[8 * g + 1], t[8 * g + 2], t[8 * g + 3], X[g]);
+    bt4x4(t[8 * g + 4], t[8 * g + 5], t[8 * g + 6], t[8 * g + 7], Y[g]);
+#pragma unroll
+    for (int k = 0; k < 4; k++) tr8x8(X[g][k], Y[g][k], K);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      uint32_t w[4];
+#pragma unroll
+      for (int g = 0; g < G; g++) w[g] = u ? Y[g][k] : X[g][k];
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        const int i = 8 * k + 4 * u + v;
+        int d = gather_delta<G>(w, v);
+        if (i == 0 && zero0) d = 0;
+        acc += (uint32_t)d;
+        f(i, (int)acc);
+      }
+    }
+  }
+}
+
+// The local prefixes of one half into p[0 .. 31].
+template <int G>
+HZL_HD void half_prefix(const uint32_t t[32], bool zero0, const Shifts& K, int p[32]) {
+  half_visit<G>(t, zero0, K, [&](int i, int v) { p[i] = v; });
+}
+
 }  // namespace lanes
 }  // namespace hz

@@ -1,7 +1,8 @@
 // hz_var.cuh — one warp's share of the exact sums S1 = sum q and S2 = sum q^2
 // (Sec. V-B) over one 64-block tile of a landed super-tile stage, decoded two
 // lanes per block with hz_lanes.cuh. Shared by the single-stream variance and
-// the batched reductions.
+// the batched reductions; the block-wise means and the covariance sums of two
+// streams (Sec. V-D) use the same decode.
 #pragma once
 #include "hz_lanes.cuh"
 #include "hz_super.cuh"
@@ -121,6 +122,112 @@ __device__ __forceinline__ void block_means_tile(const St& sg, const uint64_t* r
     const double mb = (len == L) ? (double)s1 * 0.015625 : (double)s1 / (double)len;
     if (hf == 0 && len > 0) out[tile * TILE + b] = mb * e2;
   }
+}
+
+// half_visit / half_prefix of hz_lanes.cuh for the warp's widest rate Rw.
+template <class F>
+__device__ __forceinline__ void half_visit_any(int Rw, const uint32_t t[32], bool zero0,
+                                               const lanes::Shifts& K, F&& f) {
+  switch ((Rw + 8) >> 3) {
+    case 1: lanes::half_visit<1>(t, zero0, K, f); break;
+    case 2: lanes::half_visit<2>(t, zero0, K, f); break;
+    case 3: lanes::half_visit<3>(t, zero0, K, f); break;
+    default: lanes::half_visit<4>(t, zero0, K, f); break;
+  }
+}
+__device__ __forceinline__ void half_prefix_any(int Rw, const uint32_t t[32], bool zero0,
+                                                const lanes::Shifts& K, int p[32]) {
+  switch ((Rw + 8) >> 3) {
+    case 1: lanes::half_prefix<1>(t, zero0, K, p); break;
+    case 2: lanes::half_prefix<2>(t, zero0, K, p); break;
+    case 3: lanes::half_prefix<3>(t, zero0, K, p); break;
+    default: lanes::half_prefix<4>(t, zero0, K, p); break;
+  }
+}
+
+// Covariance sums (Sec. V-D) over 16 blocks of tile `ti` of two landed stages
+// of streams of one length: blocks 16 quarter .. 16 quarter + 15, lane 2m + hf
+// holding half hf of block 16 quarter + m of both streams. With q = b + p on
+// each side (b the half's base, p its local prefix), a half adds
+//   sum q_A q_B = n b_A b_B + b_A sum p_B + b_B sum p_A + sum p_A p_B
+// to sab and its sums of q_A and q_B to s1a and s1b. qsmall: both headers
+// bound every |q| below 2^13. Every warp collective here runs on all 32 lanes
+// (the half bases are exchanged unconditionally, then selected).
+template <class St>
+__device__ __forceinline__ void cov_quarter(const St& sa, const St& sb, const uint64_t* ring,
+                                            int ti, const TileRates& tra, const TileRates& trb,
+                                            uint64_t tile, uint64_t ntiles, int lastlen,
+                                            int quarter, bool qsmall, const lanes::Shifts& K,
+                                            __int128& sab, long long& s1a, long long& s1b) {
+  const int lane = threadIdx.x & 31;
+  const int hf = lane & 1, m = lane >> 1;
+  const int nvt = tra.nvt;
+  if (16 * quarter >= nvt) return;  // warp-uniform: the whole quarter lies past the stream's end
+  const int b = 16 * quarter + m;
+  uint32_t ra, exa, rb, exb;
+  tile_block(tra, b, ra, exa);
+  tile_block(trb, b, rb, exb);
+  const int len = (b < nvt - 1) ? L : (b == nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+  const int nval = min(max(len - 32 * hf, 0), 32);
+  const long long OA = len ? sa.outlier[TILE * ti + b] : 0;
+  const long long OB = len ? sb.outlier[TILE * ti + b] : 0;
+  const uint32_t* sga = reinterpret_cast<const uint32_t*>(sa.sign + sa.sbase + sa.tnc[ti]);
+  const uint32_t* sgb = reinterpret_cast<const uint32_t*>(sb.sign + sb.sbase + sb.tnc[ti]);
+  const uint32_t* pla = reinterpret_cast<const uint32_t*>(ring + sa.pring + sa.pbase + sa.tr[ti]);
+  const uint32_t* plb = reinterpret_cast<const uint32_t*>(ring + sb.pring + sb.pbase + sb.tr[ti]);
+  const uint32_t swa = ra ? sga[2 * (exa >> 16) + hf] : 0u;
+  const uint32_t swb = rb ? sgb[2 * (exb >> 16) + hf] : 0u;
+  const int RwA = (int)__reduce_max_sync(0xffffffffu, ra);
+  const int RwB = (int)__reduce_max_sync(0xffffffffu, rb);
+  const bool fullblk = __all_sync(0xffffffffu, len == L);
+  int pA[32];
+  {
+    uint32_t t[32];
+    lanes::twos_planes_any(RwA, pla + 2 * (exa & 0xffffu) + hf, (int)ra, swa, t);
+    half_prefix_any(RwA, t, hf == 0, K, pA);
+  }
+  // narrow: every |p| < 2^14, so eight products p_A p_B add up inside 32 bits
+  const bool narrow = fullblk && (qsmall || (RwA <= 8 && RwB <= 8));
+  long long spa = 0, spb = 0;
+  __int128 pab = 0;
+  int lastB = 0;
+  {
+    uint32_t t[32];
+    lanes::twos_planes_any(RwB, plb + 2 * (exb & 0xffffu) + hf, (int)rb, swb, t);
+    if (narrow) {
+      int x = 0, y = 0, acc = 0;
+      long long s8 = 0;
+      half_visit_any(RwB, t, hf == 0, K, [&](int i, int pb) {
+        x += pA[i];
+        y += pb;
+        acc = (int)lanes::mad((uint32_t)pA[i], (uint32_t)pb, (uint32_t)acc);
+        if ((i & 7) == 7) {
+          s8 += acc;
+          acc = 0;
+        }
+        if (i == 31) lastB = pb;
+      });
+      spa = x;
+      spb = y;
+      pab = s8;
+    } else {
+      half_visit_any(RwB, t, hf == 0, K, [&](int i, int pb) {
+        const long long xa = (i < nval) ? pA[i] : 0, yb = (i < nval) ? pb : 0;
+        spa += xa;
+        spb += yb;
+        pab += (__int128)(xa * yb);
+        if (i == 31) lastB = pb;
+      });
+    }
+  }
+  // the first half's totals, exchanged by every lane; the second half adds them
+  const int totA = __shfl_xor_sync(0xffffffffu, pA[31], 1);
+  const int totB = __shfl_xor_sync(0xffffffffu, lastB, 1);
+  const long long bA = OA + (hf ? (long long)totA : 0ll);
+  const long long bB = OB + (hf ? (long long)totB : 0ll);
+  sab += (__int128)(nval * bA) * bB + (__int128)bA * spb + (__int128)bB * spa + pab;
+  s1a += (long long)nval * bA + spa;
+  s1b += (long long)nval * bB + spb;
 }
 
 }  // namespace hz

@@ -4,6 +4,7 @@
 //   element-wise addition through the decoded deltas (workflow 2).
 #include "hz_scalar.cuh"
 #include "hz_super.cuh"
+#include "hz_var.cuh"
 #include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
@@ -712,6 +713,159 @@ cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, con
     k_add<true><<<grid, ADD_THREADS, smem, lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws);
   else
     k_add<false><<<grid, ADD_THREADS, smem, lc.stream>>>(a, a_bytes, b, b_bytes, out, cap, ws);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- covariance
+// Population covariance of two streams of one length (Sec. V-D, done like the
+// variance of Sec. V-B over two fields) in one pass: exact sums
+// S_AB = sum q_A q_B, S1_A and S1_B, finished in FP64 by the last CTA. Each
+// side scales by its own 2 eps, so the error bounds may differ. The inputs come
+// through the addition's two-stream super-tile pipeline. A stage holds 16 jobs
+// (4 tiles x 4 quarters of 16 blocks); compute warp j takes jobs j and j + 8,
+// two lanes per block of both streams (cov_quarter, hz_var.cuh). Eight compute
+// warps and the loader leave each thread about 168 registers: a lane keeps its
+// half's 32 prefixes of A while it decodes B, which spills at the 96 registers
+// of the addition's 17 warps. No named barrier in the stage loop, so a warp
+// whose bounded wait gave up leaves it. Per-CTA partials: [bid] holds S1_A and
+// S1_B, [G + bid] S_AB.
+constexpr int COV_NCW = 8;
+constexpr int COV_JOBS = ADD_NT * 4;  // quarters of a stage
+constexpr int COV_THREADS = (COV_NCW + 1) * 32;
+static_assert(COV_JOBS % COV_NCW == 0, "every compute warp takes as many jobs");
+
+__global__ void __launch_bounds__(COV_THREADS, 1) k_cov(
+    const uint8_t* __restrict__ a, uint64_t a_bytes, const uint8_t* __restrict__ b,
+    uint64_t b_bytes, double* result, Ws ws) {
+  using St = SStageT<ADD_NT>;
+  extern __shared__ __align__(16) uint8_t dyn[];
+  St* stages = reinterpret_cast<St*>(dyn);  // [2][ADD_STAGES]: A's, then B's
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + 2 * ADD_STAGES);
+  __shared__ uint64_t full[ADD_STAGES], empty[ADD_STAGES];
+  __shared__ unsigned long long stage_st[ADD_STAGES];
+  __shared__ uint32_t s_ts[2 * ADD_TS];
+  __shared__ __int128 s_w[3][COV_THREADS / 32];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const Info ha = parse_header(a, a_bytes);
+  const Info hb = parse_header(b, b_bytes);
+  const unsigned long long epoch = launch_epoch(ws);
+  int bad = 0;
+  if (tid == 0) {
+    int ok = 0;
+    if (!ha.ok || !hb.ok) bad = HOSZP_ERR_FORMAT;
+    else if (ha.n != hb.n) bad = HOSZP_ERR_MISMATCH;
+    else ok = 1;
+    s_ok = ok;
+    for (int k = 0; k < ADD_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], COV_NCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  const uint64_t ntiles = ok ? ntiles_of(ha.nb) : 0;
+  const uint64_t nst = nsuper_of<ADD_NT>(ntiles);
+  const uint8_t* cs[2] = {a, b};
+  const Info hs[2] = {ha, hb};
+  const SRange rg = range_sums_n<ADD_NT, 2>(cs, hs, ntiles, nst, s_ts, ADD_TS, ws, epoch, bad);
+  __syncthreads();
+  __int128 sab = 0;
+  long long s1a = 0, s1b = 0;
+  if (w == COV_NCW) {
+    __shared__ uint32_t s_beg[ADD_STAGES];
+    super_loader_n<ADD_NT, 2, ADD_STAGES, ADD_RING, 1>(stages, ring, s_beg, full, empty, stage_st,
+                                                        cs, hs, rg, s_ts, ADD_TS, ws, epoch);
+  } else if (w < COV_NCW) {
+    const int lastlen = ok ? (int)(ha.n - (ha.nb - 1) * L) : 0;
+    const bool qsmall = ha.qbound < (1u << 13) && hb.qbound < (1u << 13);
+    const lanes::Shifts K = lanes::make_shifts(a_bytes != 0 ? 1u : 0u);
+    for (uint64_t k = 0;; k++) {
+      const int st = (int)(k % ADD_STAGES);
+      if (!mbar_wait_warp(&full[st], (uint32_t)((k / ADD_STAGES) & 1), ws.status)) break;
+      const unsigned long long s = stage_st[st];
+      if (s == ~0ull) break;
+      const St& sa = stages[st];
+      const St& sb = stages[ADD_STAGES + st];
+#pragma unroll 1
+      for (int jb = w; jb < COV_JOBS; jb += COV_NCW) {
+        const int grp = jb >> 2, quarter = jb & 3;
+        const uint64_t tile = (uint64_t)ADD_NT * s + grp;
+        const TileRates tra = tile_rates(sa, grp, tile, ha.nb);
+        const TileRates trb = tile_rates(sb, grp, tile, hb.nb);
+        cov_quarter(sa, sb, ring, grp, tra, trb, tile, ntiles, lastlen, quarter, qsmall, K, sab,
+                    s1a, s1b);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+  }
+  // CTA reduction -> two partials per CTA
+  sab = warp_sum_i128(sab);
+  const __int128 t1a = warp_sum_i128((__int128)s1a), t1b = warp_sum_i128((__int128)s1b);
+  if (lane == 0) {
+    s_w[0][w] = sab;
+    s_w[1][w] = t1a;
+    s_w[2][w] = t1b;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __int128 x = 0, y = 0, z = 0;
+    for (int k = 0; k < COV_THREADS / 32; k++) {
+      x += s_w[0][k];
+      y += s_w[1][k];
+      z += s_w[2][k];
+    }
+    Partial p1, p2;  // signed 128-bit values as two's-complement words
+    p1.s1_lo = (long long)(unsigned long long)y;
+    p1.s1_hi = (long long)(y >> 64);
+    p1.s2_lo = (unsigned long long)z;
+    p1.s2_hi = (unsigned long long)(z >> 64);
+    p2.s1_lo = (long long)(unsigned long long)x;
+    p2.s1_hi = (long long)(x >> 64);
+    p2.s2_lo = 0;
+    p2.s2_hi = 0;
+    ws.partials[blockIdx.x] = p1;
+    ws.partials[gridDim.x + blockIdx.x] = p2;
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && w == 0) {
+    __int128 ya = 0, zb = 0, xab = 0;
+    for (unsigned int u = lane; u < gridDim.x; u += 32) {
+      const Partial p1 = ws.partials[u], p2 = ws.partials[gridDim.x + u];
+      ya += (__int128)(((unsigned __int128)(unsigned long long)p1.s1_hi << 64) |
+                       (unsigned long long)p1.s1_lo);
+      zb += (__int128)(((unsigned __int128)p1.s2_hi << 64) | p1.s2_lo);
+      xab += (__int128)(((unsigned __int128)(unsigned long long)p2.s1_hi << 64) |
+                        (unsigned long long)p2.s1_lo);
+    }
+    ya = warp_sum_i128(ya);
+    zb = warp_sum_i128(zb);
+    xab = warp_sum_i128(xab);
+    const bool ok_a = range_totals_ok(ws, ha, 0, 2), ok_b = range_totals_ok(ws, hb, 1, 2);
+    if (tid == 0) {
+      double res = 0.0;
+      if (ok && !(ok_a && ok_b)) set_status(ws.status, HOSZP_ERR_FORMAT);
+      else if (ok && ha.n == 0) set_status(ws.status, HOSZP_ERR_ARG);
+      else if (ok) res = cov_finish(xab, ya, zb, ha.n, ha.eps_q, hb.eps_q);
+      *result = res;
+      launch_reset(ws);
+    }
+  }
+}
+
+cudaError_t launch_cov(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
+                       uint64_t b_bytes, double* result, Ws ws) {
+  const size_t smem = 2 * ADD_STAGES * sizeof(SStageT<ADD_NT>) + ADD_RING * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int grid = persistent_grid(k_cov, COV_THREADS, lc.grid, smem);
+  if ((uint64_t)2 * grid > ws.max_grid) return cudaErrorInvalidConfiguration;  // two partials per CTA
+  k_cov<<<grid, COV_THREADS, smem, lc.stream>>>(a, a_bytes, b, b_bytes, result, ws);
   return cudaGetLastError();
 }
 

@@ -1,9 +1,10 @@
-"""Scalar subtraction, standard deviation and block-wise means (Sec. V-A,
-V-B) on the CUDA path against the oracle, through the C ABI.
+"""Scalar subtraction, standard deviation, block-wise means, covariance,
+multiplication by the scalar itself and the Hadamard product (Sec. V-A, V-B,
+V-C, V-D) on the CUDA path against the oracle, through the C ABI.
 
 Bit-exact: produced streams and block-wise means (exact block sums, the same
-two FP64 operations). Within 1e-12 relative: standard deviation (exact
-integer sums, FP64 finish)."""
+two FP64 operations). Within 1e-12 relative: standard deviation and
+covariance (exact integer sums, FP64 finish)."""
 import numpy as np
 import pytest
 
@@ -138,19 +139,21 @@ def test_mixed_rates_every_width(hz):
 def test_cov_small_cases(hz, name):
     x = CASES[name]
     y = (x[::-1].copy() * np.float32(-0.75) + np.float32(0.125)).astype(np.float32)
-    c = hz.compress(dev(x), eb=0.05, dims=(x.size,))
-    d = hz.compress(dev(y), eb=0.05, dims=(y.size,))
-    oc, od = host(c), host(d)
-    assert np.array_equal(oc, O.compress(x, dims=(x.size,), eb=0.05))
-    assert np.array_equal(od, O.compress(y, dims=(y.size,), eb=0.05))
-    assert close(hz.cov(c, d), O.cov(oc, od))
-    assert close(hz.cov(d, c), O.cov(od, oc))
-    assert close(hz.cov(hz.negate(c), d), O.cov(O.negate(oc), od))
+    for eb_a, eb_b in ((0.05, 0.05), (0.05, 0.013)):  # equal and different bounds
+        c = hz.compress(dev(x), eb=eb_a, dims=(x.size,))
+        d = hz.compress(dev(y), eb=eb_b, dims=(y.size,))
+        oc, od = host(c), host(d)
+        assert np.array_equal(oc, O.compress(x, dims=(x.size,), eb=eb_a))
+        assert np.array_equal(od, O.compress(y, dims=(y.size,), eb=eb_b))
+        assert close(hz.cov(c, d), O.cov(oc, od))
+        assert close(hz.cov(d, c), O.cov(od, oc))
+        assert close(hz.cov(hz.negate(c), d), O.cov(O.negate(oc), od))
     assert hz.cov(c, c) == hz.var(c)  # S_AA = S2 exactly, then the same FP64 steps
 
 
-@pytest.mark.parametrize("shape", [(64, 48, 37), (449, 45, 23)])
+@pytest.mark.parametrize("shape", [(64, 48, 37), (449, 45, 23), (256, 256, 128)])
 def test_cov_grf_pairs(hz, shape):
+    # (256, 256, 128): 512 super-tiles, several per CTA range
     x = datagen.grf(shape, seed=21).reshape(-1)
     y = datagen.grf(shape, seed=22).reshape(-1)
     y = (0.6 * x + 0.8 * y).astype(np.float32)  # correlated
@@ -162,6 +165,8 @@ def test_cov_grf_pairs(hz, shape):
     assert close(hz.cov(c, d), O.cov(oc, od))
     m = hz.mul_scalar(d, 7.5)
     assert close(hz.cov(c, m), O.cov(oc, O.mul_scalar(od, 7.5)))
+    f = hz.compress(dev(y), eb=1e-3, mode="rel", dims=shape)  # another bound
+    assert close(hz.cov(c, f), O.cov(oc, host(f)))
 
 
 def test_cov_wide_rates_and_errors(hz):
@@ -175,9 +180,13 @@ def test_cov_wide_rates_and_errors(hz):
     om, od = host(m), host(d)
     assert close(hz.cov(m, d), O.cov(om, od))
     assert close(hz.cov(m, hz.negate(m)), O.cov(om, O.negate(om)))
-    with pytest.raises(hz.HoszpError) as ex:  # different bounds
-        hz.cov(c, hz.compress(dev(x), eb=1.0))
-    assert ex.value.name == "MISMATCH"
+    z = hz.add(m, m)  # the widest rates: deltas near 2^31
+    oz = host(z)
+    assert close(hz.cov(z, d), O.cov(oz, od))
+    assert close(hz.cov(m, z), O.cov(om, oz))
+    assert close(hz.cov(z, hz.negate(z)), O.cov(oz, O.negate(oz)))
+    g = hz.compress(dev(x), eb=1.0)  # another bound
+    assert close(hz.cov(c, g), O.cov(host(c), host(g)))
     with pytest.raises(hz.HoszpError) as ex:  # different lengths
         hz.cov(c, hz.compress(dev(np.ones(n + 1, np.float32)), eb=0.5))
     assert ex.value.name == "MISMATCH"

@@ -1,8 +1,9 @@
-"""The two-lanes-per-block decode of the variance (hz_lanes.cuh) against
-brute force on the host: the header is host-compilable, the device
-intrinsics running as its host definitions. Every rate 0..31, short last
-blocks, signs on zero magnitudes, ignored bits at position 0, both
-accumulation widths."""
+"""The two-lanes-per-block decode of the variance and the covariance
+(hz_lanes.cuh) against brute force on the host: the header is
+host-compilable, the device intrinsics running as its host definitions.
+Every rate 0..31, short last blocks, signs on zero magnitudes, ignored bits
+at position 0, both accumulation widths; the exact sums S1 and S2 of single
+blocks and sum q_A q_B, sum q_A, sum q_B of block pairs."""
 import os
 import shutil
 import subprocess
