@@ -199,7 +199,7 @@ def profile_op(op: str, shape):
     ca = hz.compress(xa, eb=REL, mode="rel", ctx=ctx)
     e = hz.header(ca)["eps_q"]
     cb = None
-    if op == "add":
+    if op in ("add", "cov"):
         cb = hz.compress(torch.from_numpy(B.reshape(-1)).cuda(), eb=e, ctx=ctx)
     del B
     if op not in ("compress", "decompress"):
@@ -222,6 +222,8 @@ def profile_op(op: str, shape):
             hz.mean(ca, ctx=ctx)
         elif op == "var":
             hz.var(ca, ctx=ctx)
+        elif op == "cov":
+            hz.cov(ca, cb, ctx=ctx)
     torch.cuda.synchronize()
     ctx.check(op)
     print(f"profile-op {op} done: stream {ca.numel()} bytes")
@@ -413,7 +415,7 @@ def main():
                     help="field shape (smaller cases are for profiling, not bench lines)")
     ap.add_argument("--profile-op", default=None,
                     choices=["compress", "decompress", "negate", "add_scalar", "mul_scalar", "add",
-                             "mean", "var"],
+                             "mean", "var", "cov"],
                     help="run only this operator 4 times (for ncu captures; prints no bench line)")
     args = ap.parse_args()
     global SHAPE
