@@ -16,7 +16,6 @@
 // per reduction, the pipeline depth and the CTAs per SM from timed runs on the
 // plan's own data.
 #include <algorithm>
-#include <mutex>
 #include <vector>
 
 #include "hz_moments.cuh"
@@ -516,10 +515,7 @@ cudaError_t launch_bsuper(int num_sms, cudaStream_t s, const BField* F, uint32_t
                           unsigned long long* acc, unsigned int* done, double* results,
                           int* status, float* const* outs = nullptr) {
   const size_t smem = BS_STAGES * sizeof(SStage) + BS_RING * sizeof(uint64_t);
-  static std::once_flag once;
-  std::call_once(once, [&]() {
-    cudaFuncSetAttribute(k_bsuper<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
+  smem_attr<k_bsuper<MODE>>(smem);
   k_bsuper<MODE><<<persistent_grid(k_bsuper<MODE>, BS_THREADS, num_sms, smem), BS_THREADS, smem,
                    s>>>(F, nf, total_tiles, pre, acc, done, results, status, outs);
   return cudaGetLastError();
@@ -531,11 +527,7 @@ cudaError_t launch_bmoments(int grid, cudaStream_t s, const BField* F, uint32_t 
                             unsigned long long* acc, unsigned int* done, double* results,
                             int* status) {
   const size_t smem = STAGES * sizeof(InStage) + 8192 * sizeof(uint64_t);
-  static std::once_flag once;
-  std::call_once(once, [&]() {
-    cudaFuncSetAttribute(k_bmoments<VAR, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-  });
+  smem_attr<k_bmoments<VAR, STAGES>>(smem);
   k_bmoments<VAR, STAGES><<<grid, CONSUMER_THREADS, smem, s>>>(F, nf, total_tiles, pre, acc,
                                                                done, results, status);
   return cudaGetLastError();

@@ -250,11 +250,7 @@ cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const 
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
                             uint64_t cap, Ws ws) {
   const size_t smem = CMP_STAGES * sizeof(InX);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  smem_attr<k_compress>(smem);
   k_compress<<<persistent_grid(k_compress, CMP_THREADS, lc.grid, smem), CMP_THREADS, smem,
                lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs,
                                   rel ? 1 : 0, out, cap, ws);

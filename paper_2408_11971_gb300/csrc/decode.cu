@@ -374,12 +374,7 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
                               uint64_t n, Ws ws) {
   // the kernel finds the rate prefix itself (range_sums): no pre-scan
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_decompress<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
+  smem_attr<k_decompress<0>>(smem);
   const int grid = persistent_grid(k_decompress<0>, MEAN_THREADS, lc.grid, smem);
   k_decompress<0><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
   return cudaGetLastError();
@@ -388,11 +383,7 @@ cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_byt
 cudaError_t launch_decode_q(const Launch& lc, const uint8_t* c, uint64_t c_bytes, int* q,
                            uint64_t n, Ws ws) {
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_decompress<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  smem_attr<k_decompress<2>>(smem);
   const int grid = persistent_grid(k_decompress<2>, MEAN_THREADS, lc.grid, smem);
   k_decompress<2><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, q, n, ws);
   return cudaGetLastError();
@@ -401,12 +392,7 @@ cudaError_t launch_decode_q(const Launch& lc, const uint8_t* c, uint64_t c_bytes
 cudaError_t launch_block_means(const Launch& lc, const uint8_t* c, uint64_t c_bytes, double* out,
                                uint64_t nb, Ws ws) {
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_decompress<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
+  smem_attr<k_decompress<1>>(smem);
   const int grid = persistent_grid(k_decompress<1>, MEAN_THREADS, lc.grid, smem);
   k_decompress<1><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, out, nb, ws);
   return cudaGetLastError();
@@ -416,12 +402,8 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                            bool variance, Ws ws, unsigned long long* sums, bool take_sqrt) {
   // both kernels find the rate prefix themselves (range_sums): no pre-scan
   const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_var, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  smem_attr<k_mean>(smem);
+  smem_attr<k_var>(smem);
   const int grid = (variance || sums) ? persistent_grid(k_var, MEAN_THREADS, lc.grid, smem)
                                       : persistent_grid(k_mean, MEAN_THREADS, lc.grid, smem);
   if (variance || sums)

@@ -1,6 +1,7 @@
 // hz_kernels.cuh — host-side launch wrappers implemented by the .cu files and
 // called by the C ABI (api.cu).
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -67,6 +68,28 @@ inline int persistent_grid(K kernel, int threads, int num_sms, size_t smem = 0) 
   }
   per = per < 1 ? 1 : (per > 8 ? 8 : per);
   return num_sms * per;
+}
+
+// Raises kernel Kern's dynamic shared-memory limit to smem on the current
+// device, once per device: function attributes belong to a device's context,
+// so a process that launches on several devices sets it on each. Thread-safe
+// (a race sets the same value twice). Devices 64 and above set it every time.
+template <auto Kern>
+inline void smem_attr(size_t smem) {
+  static std::atomic<unsigned long long> done{0};  // bit d: set on device d
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 64;
+  }
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  if (cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+      cudaSuccess) {
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+  } else {
+    cudaGetLastError();  // the launch then reports the error
+  }
 }
 
 }  // namespace hz

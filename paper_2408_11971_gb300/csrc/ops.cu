@@ -469,12 +469,7 @@ static cudaError_t launch_mul_mode(const Launch& lc, const uint8_t* c, uint64_t 
   cudaError_t e = launch_scan(lc, c, c_bytes, ws.pre[0], ws);
   if (e != cudaSuccess) return e;
   const size_t smem = MUL_STAGES * sizeof(InStage) + MUL_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mul_scalar<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
+  smem_attr<k_mul_scalar<MODE>>(smem);
   k_mul_scalar<MODE><<<persistent_grid(k_mul_scalar<MODE>, PRODUCER_THREADS, lc.grid, smem),
                        PRODUCER_THREADS, smem, lc.stream>>>(c, c_bytes, s, b, b_bytes, qb, out,
                                                             cap, e_bits, ws.pre[0], ws);
@@ -701,12 +696,8 @@ __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
 cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, uint8_t* out, uint64_t cap, bool subtract, Ws ws) {
   const size_t smem = 2 * ADD_STAGES * sizeof(SStageT<ADD_NT>) + ADD_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_add<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_add<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  smem_attr<k_add<false>>(smem);
+  smem_attr<k_add<true>>(smem);
   const int grid = subtract ? persistent_grid(k_add<true>, ADD_THREADS, lc.grid, smem)
                             : persistent_grid(k_add<false>, ADD_THREADS, lc.grid, smem);
   if (subtract)
@@ -858,11 +849,7 @@ __global__ void __launch_bounds__(COV_THREADS, 1) k_cov(
 cudaError_t launch_cov(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, double* result, Ws ws) {
   const size_t smem = 2 * ADD_STAGES * sizeof(SStageT<ADD_NT>) + ADD_RING * sizeof(uint64_t);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  smem_attr<k_cov>(smem);
   const int grid = persistent_grid(k_cov, COV_THREADS, lc.grid, smem);
   if ((uint64_t)2 * grid > ws.max_grid) return cudaErrorInvalidConfiguration;  // two partials per CTA
   k_cov<<<grid, COV_THREADS, smem, lc.stream>>>(a, a_bytes, b, b_bytes, result, ws);
