@@ -712,23 +712,23 @@ cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, con
 // variance of Sec. V-B over two fields) in one pass: exact sums
 // S_AB = sum q_A q_B, S1_A and S1_B, finished in FP64 by the last CTA. Each
 // side scales by its own 2 eps, so the error bounds may differ. The inputs come
-// through the addition's two-stream super-tile pipeline. A stage holds 16 jobs
-// (4 tiles x 4 quarters of 16 blocks); compute warp j takes jobs j and j + 8,
-// two lanes per block of both streams (cov_quarter, hz_var.cuh). Eight compute
-// warps and the loader leave each thread about 168 registers: a lane keeps its
-// half's 32 prefixes of A while it decodes B, which spills at the 96 registers
-// of the addition's 17 warps. No named barrier in the stage loop, so a warp
-// whose bounded wait gave up leaves it. Per-CTA partials: [bid] holds S1_A and
-// S1_B, [G + bid] S_AB.
-constexpr int COV_NCW = 8;
-constexpr int COV_JOBS = ADD_NT * 4;  // quarters of a stage
+// through the addition's two-stream super-tile pipeline, with three tiles per
+// stage: 12 jobs (3 tiles x 4 quarters of 16 blocks), one per compute warp,
+// two lanes per block of both streams (cov_quarter, hz_var.cuh). Twelve
+// compute warps and the loader leave 128 registers per thread (a lane keeps its
+// half's 32 prefixes of A while it decodes B). No named barrier in the stage
+// loop, so a warp whose bounded wait gave up leaves it. Per-CTA partials:
+// [bid] holds S1_A and S1_B, [G + bid] S_AB.
+constexpr int COV_NT = 3;
+constexpr int COV_NCW = 12;
+constexpr int COV_JOBS = COV_NT * 4;  // quarters of a stage
 constexpr int COV_THREADS = (COV_NCW + 1) * 32;
 static_assert(COV_JOBS % COV_NCW == 0, "every compute warp takes as many jobs");
 
 __global__ void __launch_bounds__(COV_THREADS, 1) k_cov(
     const uint8_t* __restrict__ a, uint64_t a_bytes, const uint8_t* __restrict__ b,
     uint64_t b_bytes, double* result, Ws ws) {
-  using St = SStageT<ADD_NT>;
+  using St = SStageT<COV_NT>;
   extern __shared__ __align__(16) uint8_t dyn[];
   St* stages = reinterpret_cast<St*>(dyn);  // [2][ADD_STAGES]: A's, then B's
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + 2 * ADD_STAGES);
@@ -757,16 +757,16 @@ __global__ void __launch_bounds__(COV_THREADS, 1) k_cov(
   __syncthreads();
   const bool ok = s_ok != 0;
   const uint64_t ntiles = ok ? ntiles_of(ha.nb) : 0;
-  const uint64_t nst = nsuper_of<ADD_NT>(ntiles);
+  const uint64_t nst = nsuper_of<COV_NT>(ntiles);
   const uint8_t* cs[2] = {a, b};
   const Info hs[2] = {ha, hb};
-  const SRange rg = range_sums_n<ADD_NT, 2>(cs, hs, ntiles, nst, s_ts, ADD_TS, ws, epoch, bad);
+  const SRange rg = range_sums_n<COV_NT, 2>(cs, hs, ntiles, nst, s_ts, ADD_TS, ws, epoch, bad);
   __syncthreads();
   __int128 sab = 0;
   long long s1a = 0, s1b = 0;
   if (w == COV_NCW) {
     __shared__ uint32_t s_beg[ADD_STAGES];
-    super_loader_n<ADD_NT, 2, ADD_STAGES, ADD_RING, 1>(stages, ring, s_beg, full, empty, stage_st,
+    super_loader_n<COV_NT, 2, ADD_STAGES, ADD_RING, 1>(stages, ring, s_beg, full, empty, stage_st,
                                                         cs, hs, rg, s_ts, ADD_TS, ws, epoch);
   } else if (w < COV_NCW) {
     const int lastlen = ok ? (int)(ha.n - (ha.nb - 1) * L) : 0;
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(COV_THREADS, 1) k_cov(
 #pragma unroll 1
       for (int jb = w; jb < COV_JOBS; jb += COV_NCW) {
         const int grp = jb >> 2, quarter = jb & 3;
-        const uint64_t tile = (uint64_t)ADD_NT * s + grp;
+        const uint64_t tile = (uint64_t)COV_NT * s + grp;
         const TileRates tra = tile_rates(sa, grp, tile, ha.nb);
         const TileRates trb = tile_rates(sb, grp, tile, hb.nb);
         cov_quarter(sa, sb, ring, grp, tra, trb, tile, ntiles, lastlen, quarter, qsmall, K, sab,
@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(COV_THREADS, 1) k_cov(
 
 cudaError_t launch_cov(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, double* result, Ws ws) {
-  const size_t smem = 2 * ADD_STAGES * sizeof(SStageT<ADD_NT>) + ADD_RING * sizeof(uint64_t);
+  const size_t smem = 2 * ADD_STAGES * sizeof(SStageT<COV_NT>) + ADD_RING * sizeof(uint64_t);
   smem_attr<k_cov>(smem);
   const int grid = persistent_grid(k_cov, COV_THREADS, lc.grid, smem);
   if ((uint64_t)2 * grid > ws.max_grid) return cudaErrorInvalidConfiguration;  // two partials per CTA
