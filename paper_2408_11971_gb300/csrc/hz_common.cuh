@@ -93,9 +93,6 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
-  return *reinterpret_cast<const volatile unsigned int*>(p);
-}
 
 // ---------------------------------------------------------------- workspace
 // Per-tile look-back descriptor: flag = (epoch << 2) | state, state 1 = the
@@ -493,47 +490,5 @@ __device__ __forceinline__ int octet_excl_scan(int v, int j) {
   return x - v;
 }
 #endif  // __CUDACC__
-
-// ---------------------------------------------------------------- tile-level block scan
-// For the 64 blocks of a tile: counts of non-constant blocks and rate sums,
-// their exclusive prefixes per block, and the tile aggregate. Called by the
-// whole CTA; rate_of_block supplied in shared memory s_rate[64].
-struct TileScan {
-  unsigned int nc_excl[TILE];
-  unsigned int r_excl[TILE];
-  unsigned int agg_nc, agg_r;
-};
-
-#ifdef __CUDACC__
-__device__ __forceinline__ void tile_scan(const uint8_t* s_rate, TileScan* ts) {
-  // warps 0 and 1 scan 32 blocks each, then combine
-  const int tid = threadIdx.x;
-  if (tid < 64) {
-    int lane = tid & 31;
-    unsigned int r = s_rate[tid];
-    unsigned int nc = r > 0 ? 1u : 0u;
-    unsigned int pr = r, pnc = nc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned int yr = __shfl_up_sync(0xffffffffu, pr, o);
-      unsigned int ync = __shfl_up_sync(0xffffffffu, pnc, o);
-      if (lane >= o) { pr += yr; pnc += ync; }
-    }
-    ts->nc_excl[tid] = pnc - nc;
-    ts->r_excl[tid] = pr - r;
-  }
-  __syncthreads();
-  if (tid >= 32 && tid < 64) {
-    ts->nc_excl[tid] += ts->nc_excl[31] + (s_rate[31] > 0 ? 1u : 0u);
-    ts->r_excl[tid] += ts->r_excl[31] + s_rate[31];
-  }
-  __syncthreads();
-  if (tid == 0) {
-    ts->agg_nc = ts->nc_excl[63] + (s_rate[63] > 0 ? 1u : 0u);
-    ts->agg_r = ts->r_excl[63] + s_rate[63];
-  }
-  __syncthreads();
-}
-#endif
 
 }  // namespace hz
