@@ -221,12 +221,45 @@ int orc_quantize_scalar(double s, float eps_q, int64_t* q) {
   return rc == ORC_ERR_NONFINITE ? ORC_ERR_ARG : rc;
 }
 
-/* Reverse quantization (proof of Theorem 1, step 2): x' = 2 eps_q * q, rounded
- * to float32 as float(q) * (2 eps_q) -- one conversion, one float multiply. */
+/* Reverse quantization (proof of Theorem 1, step 2): x' = 2 eps_q * q, the real
+ * product rounded ONCE to the nearest float32 (ties to even). Streams made by
+ * the operators hold |q| up to 2^30-1, where float(q) itself would already
+ * round; so the product is formed exactly as an integer P = q * M (2 eps_q =
+ * M 2^E, M < 2^53) and P is rounded to 24 significant bits by integer shifts.
+ * The scaling by 2^E is then exact: 2 eps_q >= 2^-148, so with M odd E >= -148
+ * and every P 2^E is a multiple of 2^-148, which float32 holds while P has at
+ * most 24 significant bits (the subnormal clamp below is kept for clarity and
+ * never shortens the grid); a product beyond FLT_MAX rounds to infinity. */
 float orc_dequantize(int64_t q, float eps_q) {
-  float two_e = 2.0f * eps_q; /* exact */
-  float qf = (float)q;
-  return qf * two_e;
+  if (q == 0) return 0.0f;
+  int64_t M;
+  int E;
+  split_double(2.0 * (double)eps_q, &M, &E); /* 2 eps_q = M 2^E exactly */
+  while ((M & 1) == 0) { /* odd M: fewer bits to carry */
+    M >>= 1;
+    E += 1;
+  }
+  const int neg = q < 0;
+  u128 P = (u128)(neg ? -(i128)q : (i128)q) * (u128)M; /* exact, < 2^54 */
+  int bits = 0;
+  for (u128 t = P; t; t >>= 1) bits++;
+  /* the float32 grid at the product's binade: 24 significant bits, but never
+   * finer than 2^-149 (subnormals) */
+  int keep_lsb = bits - 24;                           /* exponent of the grid step in P units */
+  if (E + keep_lsb < -149) keep_lsb = -149 - E;       /* subnormal grid */
+  if (keep_lsb > 0) {
+    u128 rem = P & (((u128)1 << keep_lsb) - 1);
+    u128 half = (u128)1 << (keep_lsb - 1);
+    P >>= keep_lsb;
+    if (rem > half || (rem == half && (P & 1))) P += 1; /* nearest, ties to even */
+    E += keep_lsb;
+  }
+  /* P <= 2^24 now (2^24 after a carry), so (double)P is exact and so is the
+   * scaling; the final conversion to float is exact unless the value lies
+   * beyond FLT_MAX, where it gives infinity */
+  double v = ldexp((double)P, E);
+  float f = (float)v;
+  return neg ? -f : f;
 }
 
 /* Scalar multiplication requantization (Sec. V-A example): q' = floor(2e*q*rho + 1/2),

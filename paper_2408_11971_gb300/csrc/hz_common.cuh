@@ -427,14 +427,27 @@ __device__ __forceinline__ void quantize8(const float v[8], const Quant& Q, int 
   }
 }
 
-// x' = float(q) * 2e (reverse quantization). For |q| < 2^22 the conversion is
-// done with the magic-number trick (FP32 pipe), otherwise with I2F.
+// x' = 2e * q rounded once to float32 (reverse quantization, proof of
+// Theorem 1). For |q| < 2^22 the conversion of q is exact (magic-number trick
+// on the FP32 pipe) and the one float multiply is the only rounding.
 __device__ __forceinline__ float dequant_small(int q, float e2) {
   float qf = __fsub_rn(__int_as_float(q + 0x4B400000), 12582912.0f);
   return __fmul_rn(qf, e2);
 }
+// Any |q| < 2^31 (operator outputs reach 2^30 - 1, where float(q) would
+// already round). With 2e = M 2^E (M its integer significand, < 2^24), the
+// product P = q M is exact in 64 bits (< 2^55), the int64 -> float conversion
+// rounds it once to nearest-even, and the scaling by 2^E is exact: for q != 0
+// and a normal 2e, |P| >= 2^23 and E >= -149 keep the result normal; for a
+// subnormal 2e (E = -149) a P below 2^24 converts exactly and its multiple of
+// 2^-149 is representable. A product beyond FLT_MAX becomes infinity.
 __device__ __forceinline__ float dequant_any(int q, float e2) {
-  return __fmul_rn(__int2float_rn(q), e2);
+  const uint32_t b = __float_as_uint(e2);
+  const int ex = (int)((b >> 23) & 0xffu);
+  const long long M = (long long)(ex ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu));
+  const int E = ex ? ex - 150 : -149;  // in [-149, 104]
+  const float p2 = E >= -126 ? __int_as_float((E + 127) << 23) : __int_as_float(1 << (E + 149));
+  return __fmul_rn(__ll2float_rn((long long)q * M), p2);
 }
 
 // ---------------------------------------------------------------- octet codec

@@ -155,18 +155,54 @@ def test_quantize_range_limit():
     assert ex.value.name == "RANGE"
 
 
+def nearest_f32(exact: Fraction) -> np.float32:
+    """The float32 nearest to a rational, ties to the even significand; found by
+    comparing exact distances of the float32 neighbours of a first guess (the
+    guess may be one step off after its double rounding)."""
+    guess = np.float32(float(exact))
+    cands = [guess]
+    for _ in range(2):
+        cands += [np.nextafter(cands[-1], np.float32(-np.inf))]
+    up = guess
+    for _ in range(2):
+        up = np.nextafter(up, np.float32(np.inf))
+        cands.append(up)
+    cands = [c for c in cands if np.isfinite(c)]
+    dist = [abs(Fraction(float(c)) - exact) for c in cands]
+    best = min(dist)
+    tied = [c for c, d in zip(cands, dist) if d == best]
+    return min(tied, key=lambda c: int(np.array(c).view(np.uint32)) & 1)
+
+
 def test_dequantize_is_correctly_rounded():
+    """Reverse quantization (proof of Theorem 1): 2e*q rounded once to float32,
+    over the whole stream range |q| <= 2^30 - 1 that operator outputs reach."""
     rng = np.random.default_rng(9)
-    for _ in range(200):
+    cases = []
+    for _ in range(600):
         e = np.float32(10.0 ** rng.uniform(-8, 3))
-        q = int(rng.integers(-(1 << 23), 1 << 23))
+        top = int(rng.choice([1 << 23, 1 << 25, (1 << 30) - 1]))
+        cases.append((int(rng.integers(-top, top + 1)), e))
+    # ties at |q| >= 2^24: 2e a power of two and q odd above 2^24, so the
+    # product needs 25 significant bits and lies halfway between two floats
+    for q in (16777217, 16777219, -16777217, -16777219, (1 << 30) - 1, -((1 << 30) - 1),
+              (1 << 25) + 2, (1 << 25) + 6, 33554435):
+        cases.append((q, np.float32(0.5)))
+        cases.append((q, np.float32(2.0 ** -20)))
+    # e whose significand is odd and wide (no power of two), large q
+    for q in ((1 << 30) - 1, (1 << 29) + 12345, -(1 << 28) - 7):
+        cases.append((q, np.float32(0.1)))
+        cases.append((q, np.float32(1e-7)))
+    for q, e in cases:
         exact = Fraction(q) * 2 * Fraction(float(e))
         got = O.dequantize(q, e)
-        # nearest float32 to the exact product (|q| < 2^24: conversion exact)
-        cand = np.float32(float(exact))
-        lo, hi = np.nextafter(cand, np.float32(-np.inf)), np.nextafter(cand, np.float32(np.inf))
-        best = min([cand, lo, hi], key=lambda f: abs(Fraction(float(f)) - exact))
-        assert got == best
+        want = nearest_f32(exact)
+        assert got == want and np.signbit(got) == np.signbit(want), (q, float(e), got, want)
+    # the double rounding of float(q) * 2e is what this must not do: it differs
+    # on some of these cases, so the pin does tell the two apart
+    twice = sum(np.float32(np.float32(q) * np.float32(2 * e)) != nearest_f32(
+        Fraction(q) * 2 * Fraction(float(e))) for q, e in cases)
+    assert twice > 0
 
 
 # ---------------------------------------------------------------- codec
