@@ -244,15 +244,20 @@ int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums
  * latency-critical loop that cannot afford the device synchronization a
  * cudaMalloc implies -- and that therefore cannot create a hoszp_ctx. The
  * paper has no counterpart; the result is the same as hoszp_mean's.
- * Scratch: one file-scope device array of about 1.4 MB per device, kept for as
- * long as the library is loaded; it bounds the stream to at most 2^28 values
- * (larger streams: status HOSZP_ERR_CAPACITY). The first call on a device looks
- * up the array's device address with that device current; make that first
- * call before capturing any stream. Every call shares the array, so calls
- * that overlap on the GPU (e.g. on two streams at once) race and must not.
+ * Scratch: one file-scope device array of about 256 KB per device (per-CTA
+ * records only), kept for as long as the library is loaded. Streams of more
+ * than 2^28 values are refused (a policy limit of this entry point, not of the
+ * kernel): status HOSZP_ERR_CAPACITY, and *d_result is set to NaN. The array's
+ * device address is looked up with the caller's device current on every call
+ * (so it stays right after a cudaDeviceReset and in a non-primary context); the
+ * first call on a device also loads the library's kernels there, so make it
+ * before capturing any stream. Every call shares the array, so calls that
+ * overlap on the GPU (e.g. on two streams at once) race and must not.
  * d_c: stream (16-byte aligned), d_result: device double, d_status: device int
  * that receives the call's device-side status (HOSZP_OK or an error code).
- * Host-checkable argument errors are returned immediately. */
+ * Host-checkable argument errors are returned immediately; a device with more
+ * than 512 SMs (more CTAs than the array holds records for) gets
+ * HOSZP_ERR_CAPACITY. */
 int hoszp_mean_noalloc(const void* d_c, size_t c_bytes, double* d_result, int* d_status,
                        hoszp_stream_t stream);
 

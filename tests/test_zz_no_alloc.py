@@ -63,10 +63,33 @@ def test_mean_noalloc_rejects_streams_beyond_its_scratch(lib):
     x = torch.zeros(n, dtype=torch.float32, device="cuda")
     c = hz.compress(x, eb=0.1)
     del x
-    rc, _, st = call_noalloc(f, c)
+    rc, got, st = call_noalloc(f, c)
     assert rc == 0 and hz.STATUS[st] == "CAPACITY"
+    assert np.isnan(got)  # a refused stream's result is NaN, never a stale or partial mean
     # and a valid call afterwards still works
     y = torch.from_numpy(datagen.sines_1d(100_000, seed=9)).cuda()
     cy = hz.compress(y, eb=1e-3, mode="rel")
     rc, got, st = call_noalloc(f, cy)
     assert rc == 0 and st == 0 and abs(got - hz.mean(cy)) <= REL_TOL * abs(hz.mean(cy))
+
+
+def test_mean_noalloc_allocates_no_device_memory(lib):
+    """After a first call (which loads the kernels), further calls leave the
+    device's free memory unchanged: the scratch is the static array."""
+    hz, f = lib
+    x = torch.from_numpy(datagen.sines_1d(2_000_000, seed=21)).cuda()
+    c = hz.compress(x, eb=1e-4, mode="rel")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (ctypes.c_void_p(c.data_ptr()), c.numel(), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(st.data_ptr()), stream)
+    assert f(*args) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(20):
+        assert f(*args) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert int(st.item()) == 0 and abs(float(out.item()) - hz.mean(c)) <= REL_TOL * abs(hz.mean(c))
