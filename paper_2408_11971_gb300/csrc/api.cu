@@ -329,7 +329,8 @@ static int mul_scalar_any(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, doubl
   if (o < a + c_bytes && a < o + cap) return HOSZP_ERR_ARG;  // no aliasing
   DeviceGuard g(ctx->device);
   const uint64_t tiles = tiles_from_bytes(c_bytes);
-  // slot words: (1 + e) per non-constant input block + the input's plane words,
+  // slot words: one sign word per non-constant input block (sign slots), then
+  // e + the input's rate words per non-constant input block (plane slots),
   // where e bounds the growth of a block's rate: |2e rho| <= 2|s| when rho != 0
   // (|q' - q'_prev| <= |s| |delta| + 1 for the exact variant too); no rate exceeds 31
   const uint32_t e_bits =
@@ -340,7 +341,7 @@ static int mul_scalar_any(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, doubl
   Launch lc = lc_of(ctx, stream);
   rc = cuda_rc(launch_mul_scalar(lc, a, c_bytes, s, exact, e_bits, o, cap, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_MUL, e_bits, ctx->ws));
+  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_SPLIT, e_bits, ctx->ws));
 }
 
 int hoszp_mul_scalar(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double s, void* d_out,

@@ -286,5 +286,54 @@ HZL_HD void half_prefix(const uint32_t t[32], bool zero0, const Shifts& K, int p
   half_visit<G>(t, zero0, K, [&](int i, int v) { p[i] = v; });
 }
 
+// ---------------------------------------------------------------- encode
+// The inverse transposes, for operators that produce a stream from values
+// held two lanes per block: the two's-complement planes z[0 .. 8G-1] of the
+// half's 32 deltas d[0 .. 31] (bit i of z[p] = bit p of d_i). Per group g of
+// 8 planes: byte g of each delta, four to a word (byte permutes); an 8x8 bit
+// transpose per octet of positions turns its 8 bytes into the octet's byte of
+// each of the 8 planes; two 4x4 byte transposes assemble each plane's word
+// from the four octets.
+template <int G>
+HZL_HD void half_planes(const int d[32], uint32_t z[32], const Shifts& K) {
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    const uint32_t sel = (uint32_t)g | ((4u + (uint32_t)g) << 4);  // byte g of a, of b
+    uint32_t lo[4], hi[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int* o = d + 8 * u;
+      lo[u] = prmt(prmt((uint32_t)o[0], (uint32_t)o[1], sel), prmt((uint32_t)o[2], (uint32_t)o[3], sel),
+                   0x5410u);
+      hi[u] = prmt(prmt((uint32_t)o[4], (uint32_t)o[5], sel), prmt((uint32_t)o[6], (uint32_t)o[7], sel),
+                   0x5410u);
+      tr8x8(lo[u], hi[u], K);  // byte t: bit 8g + t of the octet's 8 deltas
+    }
+    bt4x4(lo[0], lo[1], lo[2], lo[3], z + 8 * g);
+    bt4x4(hi[0], hi[1], hi[2], hi[3], z + 8 * g + 4);
+  }
+}
+
+// Two's-complement planes z[0 .. 8G-1] (values below 2^(8G-1) in magnitude,
+// so plane 8G-1 is the sign) to the stream's sign-magnitude form: returns the
+// sign half-word; z[p] becomes magnitude plane p for p < 8G - 1, with
+// |d| = (d xor -s) + s as a bit-sliced carry chain. *nz gets bit p set when
+// magnitude plane p is not zero.
+template <int G>
+HZL_HD uint32_t half_sign_magnitude(uint32_t z[32], uint32_t* nz) {
+  constexpr int W = 8 * G - 1;
+  const uint32_t s = z[W];
+  uint32_t c = s, m = 0;
+#pragma unroll
+  for (int p = 0; p < W; p++) {
+    const uint32_t t = z[p] ^ s;
+    z[p] = t ^ c;
+    c &= t;
+    m |= (z[p] != 0u ? 1u : 0u) << p;
+  }
+  *nz = m;
+  return s;
+}
+
 }  // namespace lanes
 }  // namespace hz

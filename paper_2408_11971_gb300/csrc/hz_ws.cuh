@@ -298,7 +298,12 @@ __device__ __forceinline__ void produce_tile(uint8_t (*srate)[TILE], uint64_t kt
 // Rule EXPLICIT: the producer wrote each tile's slot offset into pre0[2t].
 // Rule FULL: 32 words per block (a sign word and 31 planes), for products of
 // two fields, whose rates the inputs' rates do not bound.
-enum SlotRule { SLOT_COMPRESS = 0, SLOT_ADD = 1, SLOT_MUL = 2, SLOT_EXPLICIT = 3, SLOT_FULL = 4 };
+// Rule SPLIT: a tile's sign words and plane words sit in two separate slots,
+// whose word offsets the producer wrote into pre0[2t] (signs) and pre0[2t+1]
+// (planes); a producer that finds its tile's sign count only at the tile's end
+// can then write both kinds as it goes.
+enum SlotRule { SLOT_COMPRESS = 0, SLOT_ADD = 1, SLOT_MUL = 2, SLOT_EXPLICIT = 3, SLOT_FULL = 4,
+                SLOT_SPLIT = 5 };
 
 __device__ __forceinline__ uint64_t slot_offset(int rule, uint64_t t,
                                                 const unsigned long long* pre0,
@@ -308,6 +313,38 @@ __device__ __forceinline__ uint64_t slot_offset(int rule, uint64_t t,
   if (rule == SLOT_ADD) return pre0[2 * t] + pre0[2 * t + 1] + pre1[2 * t] + pre1[2 * t + 1];
   if (rule == SLOT_EXPLICIT) return pre0[2 * t];
   return pre0[2 * t] * (1ull + e) + pre0[2 * t + 1];
+}
+
+// ---------------------------------------------------------------- producer header and qbound
+__device__ __forceinline__ void write_template(const Info& h, uint32_t qbound_fixed,
+                                               const Ws& ws) {
+  hoszp_header* H = ws.hdr;
+  H->magic = HOSZP_MAGIC;
+  H->version = HOSZP_VERSION;
+  H->dtype = 0;
+  H->ndims = (uint8_t)h.ndims;
+  H->dims[0] = h.dims[0];
+  H->dims[1] = h.dims[1];
+  H->dims[2] = h.dims[2];
+  H->eps_q = h.eps_q;
+  H->n = h.n;
+  H->eps = h.eps;
+  H->nnc = 0;
+  H->R = 0;
+  H->qbound = qbound_fixed;
+  H->block = HOSZP_BLOCK;
+}
+
+__device__ __forceinline__ void reduce_qmax(uint32_t qmax, const Ws& ws) {
+  __shared__ uint32_t s_q[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+  if ((threadIdx.x & 31) == 0) s_q[threadIdx.x >> 5] = qmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) qmax = max(qmax, s_q[w]);
+    atomicMax(&ws.totals[2], (unsigned long long)qmax);
+  }
 }
 
 }  // namespace hz

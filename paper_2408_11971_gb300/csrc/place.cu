@@ -31,20 +31,30 @@ __global__ void __launch_bounds__(512) k_place(uint8_t* __restrict__ out, uint64
          t += nwarps) {
       const unsigned long long a = ws.agg[t];
       const uint64_t nc = a >> 32, r = a & 0xffffffffull;
-      const uint64_t so = slot_offset(rule, t, ws.pre[0], ws.pre[1], e_bits);
+      uint64_t so, po;  // word offsets of the tile's sign words and plane words
+      if (rule == SLOT_SPLIT) {
+        so = ws.pre[0][2 * t];
+        po = ws.pre[0][2 * t + 1];
+      } else {
+        so = slot_offset(rule, t, ws.pre[0], ws.pre[1], e_bits);
+        po = so + nc;
+      }
       const uint64_t NC = ws.opre[2 * t], RR = ws.opre[2 * t + 1];
-      if (so + nc + r > ws.staging_words || NC + nc > nnc || RR + r > R) {
+      if (so + nc > ws.staging_words || po + r > ws.staging_words || NC + nc > nnc ||
+          RR + r > R) {
         bad = HOSZP_ERR_CAPACITY;
         continue;
       }
-      const uint64_t* src = ws.staging + so;
+      const uint64_t* ssrc = ws.staging + so;
+      const uint64_t* psrc = ws.staging + po - nc;  // word i >= nc of the tile at psrc[i]
       const uint64_t words = nc + r;
       constexpr int U = 8;
       for (uint64_t i0 = lane; i0 < words; i0 += 32 * U) {
         uint64_t v[U];
 #pragma unroll
         for (int u = 0; u < U; u++)
-          if (i0 + 32 * u < words) v[u] = __ldcs(src + i0 + 32 * u);
+          if (i0 + 32 * u < words)
+            v[u] = __ldcs((i0 + 32 * u < nc ? ssrc : psrc) + i0 + 32 * u);
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const uint64_t i = i0 + 32 * u;

@@ -166,6 +166,40 @@ static long cov_pairs() {
   return fails;
 }
 
+
+// Encode of one half (half_planes + half_sign_magnitude) against brute force:
+// magnitude planes and sign bits of 32 random deltas below 2^B in magnitude.
+template <int G>
+static bool encode_ok(const int d[32], int B) {
+  uint32_t z[32] = {0};
+  half_planes<G>(d, z, make_shifts(1u));
+  uint32_t nz = 0;
+  const uint32_t s = half_sign_magnitude<G>(z, &nz);
+  uint32_t want_nz = 0;
+  for (int i = 0; i < 32; i++) {
+    if (((s >> i) & 1u) != (d[i] < 0 ? 1u : 0u)) return false;
+  }
+  for (int p = 0; p < 8 * G - 1; p++) {
+    uint32_t w = 0;
+    for (int i = 0; i < 32; i++) {
+      const uint32_t a = (uint32_t)(d[i] < 0 ? -(long long)d[i] : d[i]);
+      w |= ((a >> p) & 1u) << i;
+    }
+    if (w != z[p]) return false;
+    if (w) want_nz |= 1u << p;
+  }
+  (void)B;
+  return nz == want_nz;
+}
+static bool encode_any(int G, const int d[32], int B) {
+  switch (G) {
+    case 1: return encode_ok<1>(d, B);
+    case 2: return encode_ok<2>(d, B);
+    case 3: return encode_ok<3>(d, B);
+    default: return encode_ok<4>(d, B);
+  }
+}
+
 int main() {
   // the 8x8 bit transpose is a transpose
   for (int it = 0; it < 2000; it++) {
@@ -181,6 +215,22 @@ int main() {
           return 1;
         }
       }
+  }
+  // encode of a half: every magnitude width 0..31, with the group count the
+  // kernels use (8 G >= B + 1: the top plane is the sign)
+  for (int it = 0; it < 20000; it++) {
+    const int B = (int)(rnd() % 32);
+    const int G = (B + 8) / 8;
+    int d[32];
+    for (int i = 0; i < 32; i++) {
+      long long m = B ? (long long)(rnd() & ((1ull << B) - 1)) : 0;
+      if (rnd() % 7 == 0) m = B ? (long long)((1ull << B) - 1) : 0;
+      d[i] = (int)((rnd() & 1) ? -m : m);
+    }
+    if (!encode_any(G, d, B)) {
+      printf("encode differs at B=%d\n", B);
+      return 1;
+    }
   }
   const long long QL = (1ll << 30) - 1;
   long fails = 0;

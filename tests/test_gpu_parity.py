@@ -250,3 +250,24 @@ def test_sums_words_and_sharded_finish(hz, config1):
     p = [hz.compress(dev(x[:cut]), eb=eq), hz.compress(dev(x[cut:]), eb=eq)]
     t = sharded.from_words(hz.sums(p[0])) + sharded.from_words(hz.sums(p[1]))
     assert (t.s1, t.s2, t.n) == (s1, s2, n)
+
+
+@pytest.mark.parametrize("eb,mode", [(0.1, "abs"), (1e-3, "rel"), (1e-5, "rel")])
+def test_mul_scalar_every_requantization_width(hz, eb, mode):
+    """Scalars from below the bin width to 1e5: the 32-bit, 64-bit and 128-bit
+    requantizations (picked from the header's bound of |q| and the scalar's
+    bin), rates growing by up to 17 bits, a tail of 43 values."""
+    x = datagen.grf((47_147,), seed=5)
+    c = hz.compress(dev(x), eb=eb, mode=mode)
+    oc = O.compress(x, eb=eb, mode=mode)
+    assert np.array_equal(host(c), oc)
+    for s in (3.14, -2.5, 0.3, 1e-7, 123.456, -7.5e3, 1e5):
+        for gpu_op, orc_op in ((hz.mul_scalar, O.mul_scalar),
+                               (hz.mul_scalar_exact, O.mul_scalar_exact)):
+            try:
+                want = orc_op(oc, s)
+            except O.OracleError as ex:
+                with pytest.raises(RuntimeError, match=ex.name):
+                    gpu_op(c, s)
+                continue
+            assert np.array_equal(host(gpu_op(c, s)), want), (s, orc_op.__name__)
