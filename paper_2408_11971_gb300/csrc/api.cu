@@ -262,7 +262,7 @@ int hoszp_compress(hoszp_ctx* ctx, const float* d_x, uint64_t n, const uint32_t 
   rc = cuda_rc(launch_compress(lc, d_x, n, d3, (uint32_t)ndims, eq, eb,
                                eb_mode == HOSZP_EB_REL, (uint8_t*)d_out, cap, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, (uint8_t*)d_out, cap, d_out_bytes, SLOT_COMPRESS, 0, ctx->ws));
+  return cuda_rc(launch_place(lc, (uint8_t*)d_out, cap, d_out_bytes, SLOT_SPLIT, 0, ctx->ws));
 }
 
 int hoszp_decompress(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, float* d_x, uint64_t n,

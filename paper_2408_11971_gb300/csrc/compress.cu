@@ -3,6 +3,7 @@
 // blockwise fixed-length bit-plane encoding, stream layout of Fig. 3).
 #include <cfloat>
 
+#include "hz_produce.cuh"
 #include "hz_ws.cuh"
 #include "hz_kernels.cuh"
 
@@ -102,47 +103,42 @@ cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double re
 }
 
 // ---------------------------------------------------------------- compression
-// Pipeline per CTA: the next tiles' 16 KB of input are bulk-copied into a
-// shared-memory ring while the current tile is quantized and encoded into an
-// output stage; a tile's place in the stream (look-back over the tiles before
-// it) is resolved one tile later, so the look-back latency overlaps compute.
-constexpr int CMP_STAGES = 4;
-constexpr int CMP_THREADS = (NCW + 1) * 32;  // compute warps + one issuer warp
-
-struct InX {
-  float v[TILE_VALUES];
-};
-
-__device__ __forceinline__ void issue_x(InX* s, uint64_t* bar, const float* x, uint64_t n,
-                                        uint64_t t) {
-  const uint64_t first = (uint64_t)TILE_VALUES * t;
-  const uint64_t cnt = umin64(TILE_VALUES, n - first);
-  const unsigned bytes = (unsigned)((cnt * 4) & ~15ull);
-  fence_proxy_async();
-  mbar_expect_tx(bar, bytes);
-  if (bytes) bulk_g2s(s->v, x + first, bytes, bar);
-}
-
-__global__ void __launch_bounds__(CMP_THREADS, 2) k_compress(
+// Two lanes per block (hz_lanes.cuh, hz_produce.cuh): lane 2m + h of a warp
+// holds positions 32h .. 32h + 31 of block m of the warp's 16-block step, all
+// in registers, from the float loads to the stored bit-planes:
+//   32 floats -> q (Eq. 3, exact) -> delta (Eq. 4; the second half's first
+//   delta takes the first half's last q) -> two's-complement planes ->
+//   sign word half and magnitude planes (Fig. 3).
+// A warp takes whole 64-block tiles from a launch-wide ticket and walks each in
+// four steps, keeping the tile's running count of sign and plane words, so it
+// writes every block's words at once: signs to the tile's sign slot (64 words
+// per tile), planes to its plane slot (64 x 24 words per tile: |q| <= 2^23 - 2
+// keeps every rate at or below 24). Rates and outliers go straight to the
+// stream; the produced-tile scan and the placement kernel finish it.
+constexpr int CMP_WARPS = 16;
+constexpr int CMP_THREADS = CMP_WARPS * 32;
+constexpr uint32_t CMP_PLANE_SLOT = TILE * 24;  // plane words per tile slot
+__global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
     const float* __restrict__ x, uint64_t n, const uint32_t dims0, const uint32_t dims1,
     const uint32_t dims2, const uint32_t ndims, float eps_q_abs, double eps_abs, int rel,
     uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  InX* ins = reinterpret_cast<InX*>(dyn);
-  __shared__ uint64_t full[CMP_STAGES], empty[CMP_STAGES];
-  __shared__ unsigned long long stage_tile[CMP_STAGES];
-  __shared__ uint8_t srate[2][TILE];
-  __shared__ unsigned int s_qmax[CMP_THREADS / 32];
-  const int tid = threadIdx.x, w = tid >> 5, g = tid >> 3, j = tid & 7;
-
+  __shared__ unsigned int s_qmax[CMP_WARPS];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int hf = lane & 1, m = lane >> 1;
   const float e = rel ? *ws.eps_q : eps_q_abs;
   const uint64_t nb = nblocks(n);
-  const uint64_t ntiles = (e >= FLT_MIN) ? ntiles_of(nb) : 0;  // range pass failed: no work
+  uint64_t ntiles = (e >= FLT_MIN) ? ntiles_of(nb) : 0;  // range pass failed: no work
+  int bad = 0;
+  // slots: 64 sign words per tile, then 64 x 24 plane words per tile
+  if (ntiles + 1 > ws.max_tiles ||
+      (uint64_t)(TILE + CMP_PLANE_SLOT) * ntiles > ws.staging_words) {
+    bad = HOSZP_ERR_CAPACITY;
+    ntiles = 0;
+  }
   Quant Q;
   Q.e = e;
   Q.e2 = 2.0f * e;
   Q.r = (e >= FLT_MIN) ? __double2float_rn(1.0 / (double)Q.e2) : 0.0f;
-
   if (tid == 0 && blockIdx.x == 0) {  // header template for the placement kernel
     hoszp_header* H = ws.hdr;
     H->magic = HOSZP_MAGIC;
@@ -160,100 +156,110 @@ __global__ void __launch_bounds__(CMP_THREADS, 2) k_compress(
     H->qbound = 0;
     H->block = HOSZP_BLOCK;
   }
-  ring_init<CMP_STAGES>(full, empty);
-  const OctetSel S = octet_sel(j);
-  uint32_t qmax = 0;
-  int bad = 0;
-  if (w == LOADER_WARP) {
-    const uint64_t G = gridDim.x;
-    issuer_warp<CMP_STAGES>(
-        stage_tile, full, empty, ntiles, ws.status,
-        [&](uint32_t k) { return (unsigned long long)(blockIdx.x + (uint64_t)k * G); },
-        [&](int sk, unsigned long long t) {
-          if ((tid & 31) == 0) issue_x(&ins[sk], &full[sk], x, n, t);
-        });
-  } else {
-    RingPos rp{0, 0u};
-    for (uint64_t k = 0;; k++) {
-      const int s = rp.s;
-      mbar_wait(&full[s], rp.par, ws.status);
-      const unsigned long long tile = stage_tile[s];
-      if (tile >= ntiles) break;
-      const InX& in = ins[s];
-      const uint64_t b = tile * TILE + g;
-      const uint64_t first = (uint64_t)TILE_VALUES * tile;
-      const uint64_t copied = umin64(TILE_VALUES, n - first) & ~3ull;
-      const int o0 = 64 * g + 8 * j;  // offset in the tile
-      const uint64_t i0 = first + o0;
-      float v[8];
-      if ((uint64_t)o0 + 8 <= copied) {
-        const float4 a = *reinterpret_cast<const float4*>(&in.v[o0]);
-        const float4 c = *reinterpret_cast<const float4*>(&in.v[o0 + 4]);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
-      } else {
+  const lanes::Shifts K = lanes::make_shifts(n != 0 ? 1u : 0u);
+  int qhi = 0, qlo = 0;  // extremes of q (zeros included: max |q| is unchanged)
+  uint64_t* const pslots = ws.staging + (uint64_t)TILE * ntiles;
+  for (;;) {
+    unsigned int t32 = 0;
+    if (lane == 0) t32 = atomicAdd(&ws.sync->ticket, 1u);
+    const uint64_t tile = __shfl_sync(0xffffffffu, t32, 0);
+    if (tile >= ntiles) break;
+    const int nvt = (int)umin64(TILE, nb - tile * TILE);
+    const uint64_t so = (uint64_t)TILE * tile, po = (uint64_t)CMP_PLANE_SLOT * tile;
+    uint32_t* sdst = reinterpret_cast<uint32_t*>(ws.staging + so);
+    uint32_t* pdst = reinterpret_cast<uint32_t*>(pslots + po);
+    uint32_t run = 0;  // (sign words << 16 | plane words) of the tile so far
+    int tbad = 0;
+    const int steps = (nvt + 15) >> 4;
+    for (int it = 0; it < steps; it++) {
+      const int b = 16 * it + m;
+      const bool valid = b < nvt;
+      const uint64_t bi = tile * TILE + b;
+      const uint64_t i0 = bi * L + 32 * hf;  // the half's first value
+      const int nval = (valid && i0 < n) ? (int)umin64(32, n - i0) : 0;
+      const bool fullblk = __all_sync(0xffffffffu, nval == 32);
+      int q[32];
+      {
+        float f[32];
+        if (fullblk) {
+          const float4* x4 = reinterpret_cast<const float4*>(x + i0);
 #pragma unroll
-        for (int t = 0; t < 8; t++) {
-          const uint64_t o = (uint64_t)o0 + t;
-          v[t] = (o < copied) ? in.v[o] : ((i0 + t < n) ? __ldg(x + i0 + t) : 0.0f);
+          for (int k = 0; k < 8; k++) {
+            const float4 a = __ldg(x4 + k);
+            f[4 * k] = a.x;
+            f[4 * k + 1] = a.y;
+            f[4 * k + 2] = a.z;
+            f[4 * k + 3] = a.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; i++) f[i] = (i < nval) ? __ldg(x + i0 + i) : 0.0f;
         }
-      }
-      __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
-      rp.next<CMP_STAGES>();
-      int q[8];
-      quantize8(v, Q, q, bad);
-      const bool past_end = i0 + 8 > n;  // only in the stream's last block
-      if (past_end) {
 #pragma unroll
-        for (int t = 0; t < 8; t++)
-          if (i0 + t >= n) q[t] = 0;
+        for (int k = 0; k < 4; k++) quantize8(f + 8 * k, Q, q + 8 * k, bad);
       }
 #pragma unroll
-      for (int t = 0; t < 8; t++) qmax = max(qmax, (uint32_t)abs(q[t]));
-      // Eq. 4 inside the block: delta_i = q_i - q_{i-1}, delta_0 := 0 (outlier)
-      const int prev = __shfl_up_sync(0xffffffffu, q[7], 1, 8);
-      int d[8];
-#pragma unroll
-      for (int t = 0; t < 8; t++) d[t] = (t == 0) ? ((j == 0) ? 0 : q[0] - prev) : q[t] - q[t - 1];
-      if (past_end) {
-#pragma unroll
-        for (int t = 0; t < 8; t++)
-          if (i0 + t >= n) d[t] = 0;
+      for (int i = 0; i < 32; i += 2) {
+        qhi = __vimax3_s32(qhi, q[i], q[i + 1]);
+        qlo = __vimin3_s32(qlo, q[i], q[i + 1]);
       }
-      uint32_t mag[8];
-      uint32_t sb = 0;
+      // Eq. 4 inside the block: delta_i = q_i - q_(i-1), delta_0 := 0 (outlier)
+      const int last0 = __shfl_xor_sync(0xffffffffu, q[31], 1);
+      const int o_new = q[0];
 #pragma unroll
-      for (int t = 0; t < 8; t++) {
-        mag[t] = (uint32_t)abs(d[t]);
-        sb |= (d[t] < 0 ? 1u : 0u) << t;
+      for (int i = 31; i > 0; i--) q[i] -= q[i - 1];
+      q[0] = hf ? q[0] - last0 : 0;
+      if (!fullblk) {
+#pragma unroll
+        for (int i = 0; i < 32; i++)
+          if (i >= nval) q[i] = 0;
       }
-      const int rate = octet_rate(mag);
-      produce_tile(srate, k, tile, nb, mag, sb, rate, q[0], b < nb, g, j, out, ws.staging,
-                   slot_offset(SLOT_COMPRESS, tile, nullptr, nullptr, 0), ws.staging_words,
-                   ws.agg, S, bad);
+      // plane groups for the warp's widest delta (its sign takes one more bit)
+      int dhi = 0, dlo = 0;
+#pragma unroll
+      for (int i = 0; i < 32; i += 2) {
+        dhi = __vimax3_s32(dhi, q[i], q[i + 1]);
+        dlo = __vimin3_s32(dlo, q[i], q[i + 1]);
+      }
+      const uint32_t dm = __reduce_or_sync(0xffffffffu, (uint32_t)max(dhi, -dlo));
+      const int Ge = min(4, (40 - __clz(dm)) >> 3);  // (bit length + 8) / 8
+      // a quantizer error anywhere in the warp: its values are not stored
+      int sbad = __any_sync(0xffffffffu, bad != 0) ? HOSZP_ERR_RANGE : tbad;
+      const int rate = encode_store_any(Ge, q, K, valid, sdst, pdst, TILE, CMP_PLANE_SLOT, run,
+                                        sbad);
+      if (sbad == HOSZP_ERR_CAPACITY) tbad = sbad;
+      if (valid && hf == 0) {
+        out[HOSZP_HEADER_BYTES + bi] = (uint8_t)rate;
+        reinterpret_cast<int*>(out + off_outlier(nb))[bi] = o_new;
+      }
+    }
+    if (tbad) bad = tbad;
+    if (lane == 0) {
+      ws.agg[tile] = ((unsigned long long)(run >> 16) << 32) | (run & 0xffffu);
+      ws.pre[0][2 * tile] = so;
+      ws.pre[0][2 * tile + 1] = (uint64_t)TILE * ntiles + po;
     }
   }
   // epilogue: max |q| for the header's qbound, first error, launch bookkeeping
+  uint32_t qmax = max((uint32_t)qhi, (uint32_t)(-(long long)qlo));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
-  if ((tid & 31) == 0) s_qmax[tid >> 5] = qmax;
+  if (lane == 0) s_qmax[w] = qmax;
   __syncthreads();
   if (tid == 0) {
-    for (int k = 1; k < CMP_THREADS / 32; k++) qmax = max(qmax, s_qmax[k]);
+    for (int k = 1; k < CMP_WARPS; k++) qmax = max(qmax, s_qmax[k]);
     atomicMax(&ws.totals[2], (unsigned long long)qmax);
   }
   if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const uint32_t dims[3],
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
                             uint64_t cap, Ws ws) {
-  const size_t smem = CMP_STAGES * sizeof(InX);
-  smem_attr<k_compress>(smem);
-  k_compress<<<persistent_grid(k_compress, CMP_THREADS, lc.grid, smem), CMP_THREADS, smem,
-               lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims, eps_q_abs, eps_abs,
-                                  rel ? 1 : 0, out, cap, ws);
+  const int grid = persistent_grid(k_compress, CMP_THREADS, lc.grid);
+  k_compress<<<grid, CMP_THREADS, 0, lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims,
+                                                  eps_q_abs, eps_abs, rel ? 1 : 0, out, cap, ws);
   return cudaGetLastError();
 }
 
