@@ -238,6 +238,18 @@ int hoszp_cov(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, 
 int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums,
                hoszp_stream_t stream);
 
+/* Mean and population variance of a field from exact sums combined over its
+ * shards (Sec. V-B: mean = (S1 / n) 2 eps_q, variance = (2 eps_q)^2
+ * (n S2 - S1^2) / n^2 over the integers): d_sums (device, 5 words, the layout
+ * hoszp_sums writes) holds the word-wise 128-bit sums of the shards' S1 and S2
+ * and the total n; eps_q is the shards' common bound (the header's eps_q
+ * bits). Writes *d_mean and/or *d_var (device doubles; either may be NULL, not
+ * both) with the same FP64 steps as hoszp_mean and hoszp_var, so the result
+ * equals those of the whole field on one device bit for bit. n == 0 sets the
+ * context's status to HOSZP_ERR_ARG (results 0). Asynchronous on stream. */
+int hoszp_finish_sums(hoszp_ctx* ctx, const uint64_t* d_sums, float eps_q, double* d_mean,
+                      double* d_var, hoszp_stream_t stream);
+
 /* Mean of a stream without allocating: for callers that may not allocate
  * device memory when they call -- e.g. code whose device memory is owned by a
  * host framework's pool that forbids driver allocations while it runs, or a

@@ -73,6 +73,7 @@ def _load():
     lib.orc_add_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
     lib.orc_mul_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
     lib.orc_add.argtypes = [P, SZ, P, SZ, P, SZ, P]
+    lib.orc_concat.argtypes = [ctypes.c_uint32, P, P, P, I, P, SZ, P]
     lib.orc_sub.argtypes = [P, SZ, P, SZ, P, SZ, P]
     lib.orc_sums.argtypes = [P, SZ, P, P, P, P, P, P]
     lib.orc_sub_scalar.argtypes = [P, SZ, ctypes.c_double, P, SZ, P]
@@ -90,7 +91,7 @@ def _load():
     for f in (lib.orc_compress, lib.orc_decompress, lib.orc_decode_q, lib.orc_negate,
               lib.orc_add_scalar, lib.orc_mul_scalar, lib.orc_add, lib.orc_sums,
               lib.orc_header, lib.orc_eps_q, lib.orc_quantize, lib.orc_quantize_scalar,
-              lib.orc_mul_requant):
+              lib.orc_mul_requant, lib.orc_concat):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -228,6 +229,23 @@ def add(a, b) -> np.ndarray:
     nbytes = np.zeros(1, np.uint64)
     _check(_load().orc_add(_ptr(a), a.size, _ptr(b), b.size, _ptr(out), cap, _ptr(nbytes)),
            "add")
+    return out[: int(nbytes[0])].copy()
+
+
+def concat(streams, dims) -> np.ndarray:
+    """Streams of consecutive shards of one field (same bound; every shard but
+    the last of whole blocks) joined into the field's stream of shape dims."""
+    ss = [_stream(c) for c in streams]
+    k = len(ss)
+    ptrs = (ctypes.c_void_p * k)(*[c.ctypes.data for c in ss])
+    sizes = (ctypes.c_size_t * k)(*[c.size for c in ss])
+    d = (ctypes.c_uint32 * 3)(*(list(dims) + [0, 0, 0])[:3])
+    n = int(np.prod(dims))
+    cap = bound(n)
+    out = np.zeros(cap, np.uint8)
+    nbytes = np.zeros(1, np.uint64)
+    _check(_load().orc_concat(k, ptrs, sizes, d, len(dims), _ptr(out), cap, _ptr(nbytes)),
+           "concat")
     return out[: int(nbytes[0])].copy()
 
 

@@ -793,6 +793,51 @@ int orc_cov_sums(const uint8_t* a, size_t a_bytes, const uint8_t* b, size_t b_by
 }
 
 /* Header fields, for tests. */
+/* Streams of consecutive shards of one field joined into the field's stream
+ * (Sec. VI-B5: the nodes' compressed data gathered at a root). The plain
+ * definition: decode every shard to its integers, join them in order, and
+ * encode the whole field. Shards must share eps_q and eps bits (MISMATCH),
+ * and every shard but the last must hold whole blocks (MISMATCH); dims give
+ * the field's shape (their product must be the total n, else ARG). The header's
+ * qbound is the largest of the shards'. */
+int orc_concat(uint32_t k, const uint8_t* const* streams, const size_t* bytes,
+               const uint32_t* dims, int ndims, uint8_t* out, size_t cap, uint64_t* out_bytes) {
+  if (k == 0 || ndims < 1 || ndims > 3) return ORC_ERR_ARG;
+  orc_hdr h0, hk;
+  uint64_t n = 0;
+  uint32_t qb = 0;
+  for (uint32_t s = 0; s < k; s++) {
+    int rc = read_header(streams[s], bytes[s], &hk);
+    if (rc) return rc;
+    if (s == 0) h0 = hk;
+    if (float_to_bits(hk.eps_q) != float_to_bits(h0.eps_q) ||
+        double_to_bits(hk.eps) != double_to_bits(h0.eps))
+      return ORC_ERR_MISMATCH;
+    if (s + 1 < k && hk.n % ORC_L != 0) return ORC_ERR_MISMATCH;
+    n += hk.n;
+    if (hk.qbound > qb) qb = hk.qbound;
+  }
+  uint64_t prod = 1;
+  for (int d = 0; d < ndims; d++) prod *= dims[d];
+  if (prod != n) return ORC_ERR_ARG;
+  int64_t* q = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  if (!q) return ORC_ERR_ARG;
+  uint64_t at = 0;
+  for (uint32_t s = 0; s < k; s++) {
+    read_header(streams[s], bytes[s], &hk);
+    decode_q(streams[s], bytes[s], &hk, q + at);
+    at += hk.n;
+  }
+  orc_hdr h = h0;
+  h.n = n;
+  h.ndims = (uint32_t)ndims;
+  for (int d = 0; d < 3; d++) h.dims[d] = d < ndims ? dims[d] : 0;
+  h.qbound = qb;
+  int rc = encode_q(q, &h, out, cap, out_bytes);
+  free(q);
+  return rc;
+}
+
 int orc_header(const uint8_t* c, size_t bytes, uint64_t* n, uint64_t* nnc, uint64_t* R,
                uint32_t* qbound, float* eps_q, uint64_t* size) {
   orc_hdr h;

@@ -81,6 +81,7 @@ def load_library():
             "hoszp_hadamard": (I, [P, P, SZ, P, SZ, P, U64, P, SZ, P, P]),
             "hoszp_mean": (I, [P, P, SZ, P, P]),
             "hoszp_sums": (I, [P, P, SZ, P, P]),
+            "hoszp_finish_sums": (I, [P, P, ctypes.c_float, P, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
             "hoszp_std": (I, [P, P, SZ, P, P]),
             "hoszp_cov": (I, [P, P, SZ, P, SZ, P, P]),
@@ -402,6 +403,23 @@ def sums(c, stream=None, ctx=None):
                                      _stream_ptr(stream)), "sums")
     ctx.check("sums")
     return [int(v) & ((1 << 64) - 1) for v in w.cpu().tolist()]
+
+
+def finish_sums(words, eps_q, device=0, stream=None, ctx=None):
+    """(mean, population variance) of a field from the five words of its exact
+    sums combined over shards (hoszp_finish_sums: the kernels' FP64 finish)."""
+    torch = _torch()
+    w = torch.tensor([int(v) - (1 << 64) if int(v) >> 63 else int(v) for v in words],
+                     dtype=torch.int64, device=torch.device("cuda", device))
+    if ctx is None:
+        ctx = _ctx(None, w)
+    out = torch.zeros(2, dtype=torch.float64, device=w.device)
+    _check(load_library().hoszp_finish_sums(ctx.handle, _dev_ptr(w), ctypes.c_float(eps_q),
+                                            _dev_ptr(out), _dev_ptr(out) + 8,
+                                            _stream_ptr(stream)), "finish_sums")
+    ctx.check("finish_sums")
+    m, v = out.cpu().tolist()
+    return m, v
 
 
 def mean(c, out=None, stream=None, ctx=None, sync: bool = True, check: bool = True):

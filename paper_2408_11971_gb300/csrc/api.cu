@@ -469,6 +469,20 @@ int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums
                                 ctx->ws, reinterpret_cast<unsigned long long*>(d_sums)));
 }
 
+int hoszp_finish_sums(hoszp_ctx* ctx, const uint64_t* d_sums, float eps_q, double* d_mean,
+                      double* d_var, hoszp_stream_t stream) {
+  if (!ctx || !d_sums || (!d_mean && !d_var)) return HOSZP_ERR_ARG;
+  if (!aligned8(d_sums) || (d_mean && !aligned8(d_mean)) || (d_var && !aligned8(d_var)))
+    return HOSZP_ERR_ARG;
+  if (!(eps_q > 0.0f) || !std::isfinite(eps_q)) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = ensure_ws(ctx, 1, 16);
+  if (rc) return rc;
+  return cuda_rc(launch_finish_sums(lc_of(ctx, stream),
+                                    reinterpret_cast<const unsigned long long*>(d_sums), eps_q,
+                                    d_mean, d_var, ctx->ws));
+}
+
 int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
                hoszp_stream_t stream) {
   return moments(ctx, d_c, c_bytes, d_result, stream, false);

@@ -414,4 +414,30 @@ cudaError_t launch_moments(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- finish of combined sums
+// Mean and variance of a field from exact sums added over its shards (five
+// words as hoszp_sums writes them: S1 low/high, S2 low/high, n), with the same
+// FP64 steps as the single-stream kernels, so a sharded field gives the same
+// doubles as the whole field on one device.
+__global__ void k_finish_sums(const unsigned long long* sums, float eps_q, double* mean,
+                              double* var, Ws ws) {
+  const __int128 S1 = (__int128)(((unsigned __int128)sums[1] << 64) | sums[0]);
+  const U128 S2 = {sums[2], sums[3]};
+  const uint64_t n = sums[4];
+  if (n == 0 || !(eps_q >= FLT_MIN) || !(eps_q <= FLT_MAX)) {
+    set_status(ws.status, HOSZP_ERR_ARG);
+    if (mean) *mean = 0.0;
+    if (var) *var = 0.0;
+    return;
+  }
+  if (mean) *mean = moment_finish(S1, S2, n, eps_q, false);
+  if (var) *var = moment_finish(S1, S2, n, eps_q, true);
+}
+
+cudaError_t launch_finish_sums(const Launch& lc, const unsigned long long* sums, float eps_q,
+                               double* mean, double* var, Ws ws) {
+  k_finish_sums<<<1, 1, 0, lc.stream>>>(sums, eps_q, mean, var, ws);
+  return cudaGetLastError();
+}
+
 }  // namespace hz

@@ -58,6 +58,9 @@ cudaError_t launch_add(const Launch& lc, const uint8_t* a, uint64_t a_bytes, con
 cudaError_t launch_cov(const Launch& lc, const uint8_t* a, uint64_t a_bytes, const uint8_t* b,
                        uint64_t b_bytes, double* result, Ws ws);
 
+cudaError_t launch_finish_sums(const Launch& lc, const unsigned long long* sums, float eps_q,
+                               double* mean, double* var, Ws ws);
+
 // Persistent grid: SMs x resident CTAs per SM of `kernel` (capped at 8).
 template <typename K>
 inline int persistent_grid(K kernel, int threads, int num_sms, size_t smem = 0) {

@@ -16,9 +16,10 @@ Each rank holds a stream of whole blocks of the field, compressed with the same
 absolute bound (the same eps_q bits). The library returns each shard's exact
 integer sums (hoszp_sums: S1 = sum q, S2 = sum q^2, n; Sec. V-B); the ranks add
 them with one all-reduce of 32-bit limbs held in int64 -- exact and independent
-of the order of addition -- and every rank finishes mean and variance with the
-same FP64 steps as the single-stream kernels, so a sharded field gives the same
-double as the whole field on one device.
+of the order of addition -- and every rank finishes mean and variance on its
+device with the library's hoszp_finish_sums, the same FP64 steps as the
+single-stream kernels, so a sharded field gives the same double as the whole
+field on one device.
 """
 from __future__ import annotations
 
@@ -74,30 +75,21 @@ def allreduce(s: Sums, group=None) -> Sums:
     return _from_limbs(t.cpu().tolist())
 
 
-def _u64_double(v: int) -> float:
-    return float(v & MASK64)
+def to_words(s: Sums):
+    """The five words of hoszp_sums for combined sums (S1 as a 128-bit two's
+    complement integer, S2 as 128-bit unsigned, n)."""
+    s1 = s.s1 & ((1 << 128) - 1)
+    return [s1 & MASK64, s1 >> 64, s.s2 & MASK64, (s.s2 >> 64) & MASK64, s.n]
 
 
-def finish(s: Sums, eps_q: float):
-    """(mean, population variance) with the kernels' FP64 steps: the mean from
-    |S1| as hi * 2^64 + lo, the variance from the exact 256-bit numerator
-    n S2 - S1^2 converted word by word from the top."""
+def finish(s: Sums, eps_q: float, device: int = 0, ctx=None):
+    """(mean, population variance) of combined sums, finished on the device by
+    the library (hoszp_finish_sums) with the single-stream kernels' FP64 steps."""
     if s.n == 0:
         raise ValueError("empty field")
-    import struct
+    from . import _binding as B
 
-    e = struct.unpack("<f", struct.pack("<f", eps_q))[0]
-    e2 = 2.0 * e
-    a = -s.s1 if s.s1 < 0 else s.s1
-    md = _u64_double(a >> 64) * 18446744073709551616.0 + _u64_double(a)
-    mean = ((-md if s.s1 < 0 else md) / float(s.n)) * e2
-    D = s.n * s.s2 - s.s1 * s.s1
-    d = _u64_double(D >> 192)
-    for k in (2, 1, 0):
-        d = d * 18446744073709551616.0 + _u64_double(D >> (64 * k))
-    dn = float(s.n)
-    var = (d / (dn * dn)) * (e2 * e2)
-    return mean, var
+    return B.finish_sums(to_words(s), eps_q, device=device, ctx=ctx)
 
 
 def mean_var(c_local, eps_q: float, group=None, ctx=None):
@@ -106,7 +98,7 @@ def mean_var(c_local, eps_q: float, group=None, ctx=None):
     from . import _binding as B
 
     s = from_words(B.sums(c_local, ctx=ctx))
-    return finish(allreduce(s, group), eps_q)
+    return finish(allreduce(s, group), eps_q, device=c_local.device.index or 0, ctx=ctx)
 
 
 def _send_stream(t, dst, group=None):

@@ -234,9 +234,9 @@ def test_repeated_calls_are_deterministic(hz, config1):
 
 
 def test_sums_words_and_sharded_finish(hz, config1):
-    """hoszp_sums gives the oracle's exact sums; finishing them on the host
-    (the multi-rank path) gives the kernels' mean and variance bit for bit, and
-    two shards of whole blocks add up to the whole field."""
+    """hoszp_sums gives the oracle's exact sums; finishing them with
+    hoszp_finish_sums (the multi-rank path) gives the kernels' mean and variance
+    bit for bit, also for the sums of two shards of whole blocks."""
     from paper_2408_11971_gb300 import sharded
 
     x, c, oc = config1
@@ -250,6 +250,10 @@ def test_sums_words_and_sharded_finish(hz, config1):
     p = [hz.compress(dev(x[:cut]), eb=eq), hz.compress(dev(x[cut:]), eb=eq)]
     t = sharded.from_words(hz.sums(p[0])) + sharded.from_words(hz.sums(p[1]))
     assert (t.s1, t.s2, t.n) == (s1, s2, n)
+    assert sharded.finish(t, eq) == (hz.mean(c), hz.var(c))
+    # the finish's own edge: no values
+    with pytest.raises(RuntimeError, match="ARG"):
+        hz.finish_sums([0, 0, 0, 0, 0], eq)
 
 
 @pytest.mark.parametrize("eb,mode", [(0.1, "abs"), (1e-3, "rel"), (1e-5, "rel")])

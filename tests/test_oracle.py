@@ -589,3 +589,37 @@ def test_hadamard(pair):
     with pytest.raises(O.OracleError) as ex:
         O.hadamard(big, big)
     assert ex.value.name == "OVERFLOW"
+
+
+# ---------------------------------------------------------------- shard streams joined
+def test_concat_of_shards_is_the_whole_field_stream():
+    """Sec. VI-B5 (the nodes' streams gathered at a root): the streams of
+    consecutive shards of whole blocks, compressed with one bound, join into
+    exactly the stream of the whole field; the last shard may be ragged."""
+    x = datagen.sines_1d(64 * 700 + 37, seed=8)
+    eps = 1e-3 * float(x.max() - x.min())
+    whole = O.compress(x, eb=eps)
+    for cuts in ([0, 64 * 300, x.size], [0, 64, 64 * 2, 64 * 650, x.size], [0, x.size]):
+        parts = [O.compress(np.ascontiguousarray(x[a:b]), eb=eps) for a, b in zip(cuts, cuts[1:])]
+        assert np.array_equal(O.concat(parts, (x.size,)), whole)
+    # a 3-D field split along its slowest axis keeps its shape in the header
+    g = datagen.grf((8, 16, 32), seed=2)
+    e = 1e-3 * float(g.max() - g.min())
+    parts = [O.compress(np.ascontiguousarray(g[:5]).reshape(-1), eb=e),
+             O.compress(np.ascontiguousarray(g[5:]).reshape(-1), eb=e)]
+    assert np.array_equal(O.concat(parts, (8, 16, 32)), O.compress(g, eb=e))
+
+
+def test_concat_refuses_what_is_not_one_field():
+    x = datagen.sines_1d(64 * 20, seed=9)
+    a = O.compress(x[:64 * 10], eb=0.01)
+    b = O.compress(x[64 * 10:], eb=0.01)
+    with pytest.raises(O.OracleError) as ex:  # different bounds
+        O.concat([a, O.compress(x[64 * 10:], eb=0.02)], (x.size,))
+    assert ex.value.name == "MISMATCH"
+    with pytest.raises(O.OracleError) as ex:  # a shard before the last is ragged
+        O.concat([O.compress(x[:100], eb=0.01), O.compress(x[100:], eb=0.01)], (x.size,))
+    assert ex.value.name == "MISMATCH"
+    with pytest.raises(O.OracleError) as ex:  # the shape disagrees with the values
+        O.concat([a, b], (x.size + 1,))
+    assert ex.value.name == "ARG"
