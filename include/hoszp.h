@@ -250,6 +250,38 @@ int hoszp_sums(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, uint64_t* d_sums
 int hoszp_finish_sums(hoszp_ctx* ctx, const uint64_t* d_sums, float eps_q, double* d_mean,
                       double* d_var, hoszp_stream_t stream);
 
+/* The streams of consecutive shards of one field joined into the field's
+ * stream (Sec. VI-B5: the nodes' compressed data gathered at a root). Blocks
+ * are independent (Sec. IV-A), so the result is the stream the compressor
+ * gives for the whole field: the shards' rate, outlier, sign and plane
+ * sections laid end to end (Fig. 3) under one header with the total n, the
+ * given shape (ndims 1..3, dims[0..ndims-1], product == total n), the shards'
+ * summed nnc and R and the largest qbound. Nothing is decoded.
+ * d_streams, stream_bytes: host arrays of nstreams >= 1 device pointers
+ * (16-byte aligned, not overlapping d_out) and sizes, in the field's order.
+ * Every shard must carry the same eps_q and eps bits, and every shard but the
+ * last a whole number of blocks (n a multiple of 64). Device-side errors go to
+ * the context's status: FORMAT (a bad header), MISMATCH (bounds differ, or a
+ * ragged shard before the last), ARG (the shape's product is not the total n),
+ * CAPACITY (cap too small); *d_out_bytes is then 0. Uses the context's
+ * workspace for the shard table; asynchronous on stream (the host arrays may
+ * be released when the call returns). */
+int hoszp_concat(hoszp_ctx* ctx, uint32_t nstreams, const void* const* d_streams,
+                 const size_t* stream_bytes, const uint32_t dims[3], int ndims, void* d_out,
+                 size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream);
+
+/* Failure-detection self-test (the paper has no counterpart): runs one of the
+ * library's bounded device waits on a flag that nothing sets, so the caller
+ * can check that the wait gives up. which = 0: the decoupled look-back's poll
+ * loop, waiting for a predecessor tile that never publishes, limited to
+ * `limit` polls of about 256 ns (1 .. 2^22); which = 1: the copy rings'
+ * mbarrier wait on a stage that never lands, limited to `limit` ns
+ * (1 .. 10^9). The kernel sets HOSZP_ERR_TIMEOUT in the context's status word
+ * (read and cleared by hoszp_get_status) and returns; the context stays
+ * usable. Nothing faults, traps or spins without a limit. Asynchronous on
+ * stream; ARG for another `which` or a limit outside its range. */
+int hoszp_selftest_wait(hoszp_ctx* ctx, int which, uint64_t limit, hoszp_stream_t stream);
+
 /* Mean of a stream without allocating: for callers that may not allocate
  * device memory when they call -- e.g. code whose device memory is owned by a
  * host framework's pool that forbids driver allocations while it runs, or a

@@ -82,6 +82,8 @@ def load_library():
             "hoszp_mean": (I, [P, P, SZ, P, P]),
             "hoszp_sums": (I, [P, P, SZ, P, P]),
             "hoszp_finish_sums": (I, [P, P, ctypes.c_float, P, P, P]),
+            "hoszp_concat": (I, [P, ctypes.c_uint32, P, P, P, I, P, SZ, P, P]),
+            "hoszp_selftest_wait": (I, [P, I, U64, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
             "hoszp_std": (I, [P, P, SZ, P, P]),
             "hoszp_cov": (I, [P, P, SZ, P, SZ, P, P]),
@@ -341,6 +343,33 @@ def _bivariate(fn, what, a, b, out, out_bytes, stream, ctx, sync, check):
     return _finish(ctx, out, out_bytes, sync, check, what)
 
 
+def concat(streams, dims, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
+           check: bool = True):
+    """The streams of consecutive shards of one field (every shard but the last of
+    whole blocks, one bound) joined into the field's stream of shape dims
+    (hoszp_concat; Sec. VI-B5)."""
+    torch = _torch()
+    ss = [_stream_tensor(c) for c in streams]
+    if not ss:
+        raise ValueError("no streams")
+    ctx = _ctx(ctx, ss[0])
+    n = 1
+    for d in dims:
+        n *= int(d)
+    if out is None:
+        out = torch.empty(compress_bound(n), dtype=torch.uint8, device=ss[0].device)
+    if out_bytes is None:
+        out_bytes = torch.zeros(1, dtype=torch.int64, device=ss[0].device)
+    k = len(ss)
+    ptrs = (ctypes.c_void_p * k)(*[_dev_ptr(c) for c in ss])
+    sizes = (ctypes.c_size_t * k)(*[c.numel() for c in ss])
+    d3 = (ctypes.c_uint32 * 3)(*(list(dims) + [0, 0, 0])[:3])
+    rc = load_library().hoszp_concat(ctx.handle, k, ptrs, sizes, d3, len(dims), _dev_ptr(out),
+                                     out.numel(), _dev_ptr(out_bytes), _stream_ptr(stream))
+    _check(rc, "concat")
+    return _finish(ctx, out, out_bytes, sync, check, "concat")
+
+
 def add(a, b, out=None, out_bytes=None, stream=None, ctx=None, sync: bool = True,
         check: bool = True):
     """Element-wise addition of two streams (Sec. V-C)."""
@@ -415,7 +444,7 @@ def finish_sums(words, eps_q, device=0, stream=None, ctx=None):
         ctx = _ctx(None, w)
     out = torch.zeros(2, dtype=torch.float64, device=w.device)
     _check(load_library().hoszp_finish_sums(ctx.handle, _dev_ptr(w), ctypes.c_float(eps_q),
-                                            _dev_ptr(out), _dev_ptr(out) + 8,
+                                            _dev_ptr(out), ctypes.c_void_p(out.data_ptr() + 8),
                                             _stream_ptr(stream)), "finish_sums")
     ctx.check("finish_sums")
     m, v = out.cpu().tolist()

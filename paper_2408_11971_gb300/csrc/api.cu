@@ -483,6 +483,39 @@ int hoszp_finish_sums(hoszp_ctx* ctx, const uint64_t* d_sums, float eps_q, doubl
                                     d_mean, d_var, ctx->ws));
 }
 
+int hoszp_concat(hoszp_ctx* ctx, uint32_t nstreams, const void* const* d_streams,
+                 const size_t* stream_bytes, const uint32_t dims[3], int ndims, void* d_out,
+                 size_t cap, uint64_t* d_out_bytes, hoszp_stream_t stream) {
+  if (!ctx || nstreams == 0 || !d_streams || !stream_bytes || !dims || !d_out || !d_out_bytes)
+    return HOSZP_ERR_ARG;
+  if (ndims < 1 || ndims > 3 || !aligned16(d_out) || !aligned8(d_out_bytes)) return HOSZP_ERR_ARG;
+  for (uint32_t s = 0; s < nstreams; s++) {
+    if (!d_streams[s] || !aligned16(d_streams[s]) || stream_bytes[s] < HOSZP_HEADER_BYTES)
+      return HOSZP_ERR_ARG;
+    const uint8_t* c = (const uint8_t*)d_streams[s];
+    const uint8_t* o = (const uint8_t*)d_out;
+    if (o < c + stream_bytes[s] && c < o + cap) return HOSZP_ERR_ARG;  // no aliasing
+  }
+  uint32_t d3[3] = {0, 0, 0};
+  for (int d = 0; d < ndims; d++) d3[d] = dims[d];
+  DeviceGuard g(ctx->device);
+  int rc = ensure_ws(ctx, 1, concat_table_words(nstreams) + 16);
+  if (rc) return rc;
+  return cuda_rc(launch_concat(lc_of(ctx, stream), nstreams, d_streams, stream_bytes, d3,
+                               (uint32_t)ndims, (uint8_t*)d_out, cap, d_out_bytes, ctx->ws));
+}
+
+int hoszp_selftest_wait(hoszp_ctx* ctx, int which, uint64_t limit, hoszp_stream_t stream) {
+  if (!ctx || (which != 0 && which != 1) || limit == 0) return HOSZP_ERR_ARG;
+  // at most about a second either way: 2^22 polls of ~256 ns, or 10^9 ns
+  if ((which == 0 && limit > (1ull << 22)) || (which == 1 && limit > 1000000000ull))
+    return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = ensure_ws(ctx, 2, 16);
+  if (rc) return rc;
+  return cuda_rc(launch_wait_selftest(lc_of(ctx, stream), which, (long long)limit, ctx->ws));
+}
+
 int hoszp_mean(hoszp_ctx* ctx, const void* d_c, size_t c_bytes, double* d_result,
                hoszp_stream_t stream) {
   return moments(ctx, d_c, c_bytes, d_result, stream, false);

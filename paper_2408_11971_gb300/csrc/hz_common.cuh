@@ -196,7 +196,8 @@ __device__ __forceinline__ void publish(Desc* d, int64_t tile, unsigned long lon
 // chain. All 32 lanes of the calling warp must take part. Spins are bounded;
 // on timeout the status word gets HOSZP_ERR_TIMEOUT and a zero prefix is used.
 __device__ __forceinline__ void lookback(Desc* d, int64_t tile, unsigned long long epoch, int* st,
-                                         unsigned long long& pnc, unsigned long long& pr) {
+                                         unsigned long long& pnc, unsigned long long& pr,
+                                         long long spin_limit = SPIN_LIMIT) {
   const int lane = threadIdx.x & 31;
   unsigned long long acc_nc = 0, acc_r = 0;
   int64_t base = tile - 1;
@@ -210,7 +211,7 @@ __device__ __forceinline__ void lookback(Desc* d, int64_t tile, unsigned long lo
         unsigned long long f = ld_acquire(&d[j].flag);
         state = ((f >> 2) == epoch) ? (int)(f & 3) : 0;
         if (state != 0) break;
-        if (++spins > SPIN_LIMIT) {
+        if (++spins > spin_limit) {
           set_status(st, HOSZP_ERR_TIMEOUT);
           state = 2;
           break;

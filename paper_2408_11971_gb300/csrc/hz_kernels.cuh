@@ -61,6 +61,13 @@ cudaError_t launch_cov(const Launch& lc, const uint8_t* a, uint64_t a_bytes, con
 cudaError_t launch_finish_sums(const Launch& lc, const unsigned long long* sums, float eps_q,
                                double* mean, double* var, Ws ws);
 
+uint64_t concat_table_words(uint32_t k);
+cudaError_t launch_concat(const Launch& lc, uint32_t k, const void* const* streams,
+                          const size_t* bytes, const uint32_t dims[3], uint32_t ndims,
+                          uint8_t* out, uint64_t cap, uint64_t* out_bytes, Ws ws);
+
+cudaError_t launch_wait_selftest(const Launch& lc, int which, long long limit, Ws ws);
+
 // Persistent grid: SMs x resident CTAs per SM of `kernel` (capped at 8).
 template <typename K>
 inline int persistent_grid(K kernel, int threads, int num_sms, size_t smem = 0) {

@@ -43,12 +43,13 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // Returns false when the wait gave up (status TIMEOUT set): callers then stop
 // their loops, so a stalled pipeline costs about a second, not a second per
 // remaining stage.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* st) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* st,
+                                          unsigned long long timeout_ns = MBAR_TIMEOUT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   for (unsigned spins = 1;; spins++) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((spins & 255u) == 0 && globaltimer_ns() - t0 > MBAR_TIMEOUT_NS) {
+    if ((spins & 255u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
       set_status(st, HOSZP_ERR_TIMEOUT);
       return false;
     }

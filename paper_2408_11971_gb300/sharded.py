@@ -10,6 +10,10 @@ stream is ever decompressed and the root receives the stream of the sum. The
 result does not depend on the tree: q-sums are exact and the encoding of a
 q-field is unique.
 
+Stream of a field whose shards live on the ranks: `gather_stream` assembles
+the shards' streams into the field's stream on rank 0 (the sections laid end
+to end under one header; nothing is decoded).
+
 Mean and variance of one field whose compressed shards live on the ranks:
 
 Each rank holds a stream of whole blocks of the field, compressed with the same
@@ -146,3 +150,40 @@ def reduce_sum(c_local, group=None, add=None):
             cur = add(cur, other)
         step *= 2
     return cur
+
+
+def gather_stream(c_local, dims, group=None, concat=None):
+    """The stream of a field whose consecutive shards (whole blocks each but the
+    last; one bound) the ranks hold in rank order, assembled on rank 0 (Sec.
+    VI-B5: the nodes' compressed data gathered at a root). One all-gather of
+    the shards' byte counts gives each rank its byte offset in the gathered
+    bytes (an exclusive scan, returned with the result); the shards then travel
+    to rank 0, which joins their sections under one header with `concat`
+    (default: the library's hoszp_concat on the tensors' device). Returns
+    (stream or None, offsets) -- the stream on rank 0, None elsewhere."""
+    import torch
+    import torch.distributed as dist
+
+    if concat is None:
+        from . import _binding as B
+
+        concat = B.concat
+    rank = dist.get_rank(group)
+    world = dist.get_world_size(group)
+    dev = c_local.device
+    mine = torch.tensor([c_local.numel()], dtype=torch.int64, device=dev)
+    sizes = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(sizes, mine, group=group)
+    sizes = [int(t.item()) for t in sizes]
+    offsets = [0]
+    for s in sizes[:-1]:
+        offsets.append(offsets[-1] + s)
+    if rank != 0:
+        dist.send(c_local.contiguous(), 0, group=group)
+        return None, offsets
+    parts = [c_local]
+    for r in range(1, world):
+        t = torch.empty(sizes[r], dtype=torch.uint8, device=dev)
+        dist.recv(t, r, group=group)
+        parts.append(t)
+    return concat(parts, dims), offsets

@@ -63,6 +63,9 @@ def test_compress_bound_and_host_checks(lib):
     assert L.hoszp_cov(None, None, 0, None, 0, None, None) == -1
     assert L.hoszp_hadamard(None, None, 0, None, 0, None, 0, None, 0, None, None) == -1
     assert L.hoszp_batch_decompress(None, None, None) == -1
+    assert L.hoszp_finish_sums(None, None, ctypes.c_float(1.0), None, None, None) == -1
+    assert L.hoszp_concat(None, 0, None, None, None, 1, None, 0, None, None) == -1
+    assert L.hoszp_selftest_wait(None, 0, 1, None) == -1
 
 
 def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):

@@ -275,3 +275,34 @@ def test_mul_scalar_every_requantization_width(hz, eb, mode):
                     gpu_op(c, s)
                 continue
             assert np.array_equal(host(gpu_op(c, s)), want), (s, orc_op.__name__)
+
+
+def test_concat_shards_into_the_field_stream(hz):
+    """hoszp_concat joins the GPU streams of consecutive shards into the stream
+    of the whole field, byte for byte the oracle's (Sec. VI-B5), for 1-D and
+    3-D shapes, shards of one block, a ragged last shard and a single shard;
+    and refuses what is not one field."""
+    g = datagen.grf((20, 48, 63), seed=12)  # 60480 values: 945 blocks
+    x = g.reshape(-1)
+    eps = float(O.header(O.compress(x, eb=1e-4, mode="rel"))["eps_q"])
+    whole = O.compress(g, eb=eps)
+    for cuts in ([0, 64 * 400, x.size], [0, 64, 128, 64 * 900, x.size], [0, x.size],
+                 [0, 64 * 100, 64 * 200, 64 * 300, 64 * 940, x.size]):
+        parts = [hz.compress(dev(x[a:b]), eb=eps) for a, b in zip(cuts, cuts[1:])]
+        assert np.array_equal(host(hz.concat(parts, g.shape)), whole), cuts
+    a = hz.compress(dev(x[:64 * 10]), eb=eps)
+    with pytest.raises(RuntimeError, match="MISMATCH"):  # another bound
+        hz.concat([a, hz.compress(dev(x[64 * 10:]), eb=2 * eps)], (x.size,))
+    with pytest.raises(RuntimeError, match="MISMATCH"):  # a ragged shard before the last
+        hz.concat([hz.compress(dev(x[:100]), eb=eps), hz.compress(dev(x[100:]), eb=eps)],
+                  (x.size,))
+    with pytest.raises(RuntimeError, match="ARG"):  # the shape disagrees with the values
+        hz.concat([a, hz.compress(dev(x[64 * 10:]), eb=eps)], (x.size + 1,))
+    bad = a.clone()
+    bad[0] ^= 1  # magic
+    with pytest.raises(RuntimeError, match="FORMAT"):
+        hz.concat([bad, a], (64 * 20,))
+    b = hz.compress(dev(x[64 * 10:]), eb=eps)
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(RuntimeError, match="CAPACITY"):
+        hz.concat([a, b], (x.size,), out=small)

@@ -143,3 +143,61 @@ def test_reduce_sum_binomial_tree(world):
     assert got[0] == chain.tobytes()
     qsum = sum(O.decode_q(c).astype(np.int64) for c in cs)
     assert np.array_equal(O.decode_q(np.frombuffer(got[0], np.uint8)), qsum)
+
+
+def _gather_rank(rank, world, port, q):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import datagen
+    import oracle as O
+    from paper_2408_11971_gb300 import sharded
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g = datagen.grf((12, 40, 63), seed=7)  # 30240 values: 472 blocks and a ragged one
+    x = g.reshape(-1)
+    eps = 1e-3 * float(x.max() - x.min())
+    cuts = [0, 64 * 101, 64 * 300, 64 * 400][:world] + [x.size]  # whole blocks but the last
+    c = torch.from_numpy(O.compress(np.ascontiguousarray(x[cuts[rank]:cuts[rank + 1]]), eb=eps))
+
+    def concat(parts, dims):  # the oracle's join stands in for hoszp_concat here
+        return torch.from_numpy(O.concat([p.numpy() for p in parts], dims))
+
+    out, offsets = sharded.gather_stream(c, g.shape, concat=concat)
+    q.put((rank, None if out is None else out.numpy().tobytes(), offsets, c.numel()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_gather_stream_assembles_the_whole_field(world):
+    """Shards of one field compressed on the ranks are assembled on rank 0 into
+    the stream of the whole field, byte for byte the oracle's compression of it
+    (Sec. VI-B5); every rank gets the exclusive scan of the shard sizes."""
+    import multiprocessing as mp
+
+    import datagen
+    import oracle as O
+
+    O.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    ps = [ctx.Process(target=_gather_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    got = {r: (s, off, nb) for r, s, off, nb in (q.get(timeout=60) for _ in ps)}
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(got[r][0] is None for r in range(1, world))
+    g = datagen.grf((12, 40, 63), seed=7)
+    eps = 1e-3 * float(g.max() - g.min())
+    assert got[0][0] == O.compress(g, eb=eps).tobytes()
+    sizes = [got[r][2] for r in range(world)]
+    want = [sum(sizes[:r]) for r in range(world)]
+    assert all(got[r][1] == want for r in range(world))
