@@ -26,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -167,6 +168,55 @@ def run_oracle(a, b, steps: int, warmup: int):
         oracle_step(O, a, b)
     ts = [oracle_step(O, a, b) for _ in range(steps)]
     return sum(ts) / len(ts)
+
+
+def host_cpu():
+    """Core count and CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or platform.machine()
+
+
+def run_omp_baseline(a, b, reps: int = 3):
+    """The oracle's arithmetic with an OpenMP loop over blocks (the paper's CPU
+    design) on every host core: median seconds of `reps` steps after one warm-up."""
+    import oracle as O
+    from oracle import omp
+
+    omp.build()
+    oracle_step(omp_ops(O, omp), a, b)
+    ts = sorted(oracle_step(omp_ops(O, omp), a, b) for _ in range(reps))
+    return ts[len(ts) // 2], omp.threads()
+
+
+def omp_ops(O, omp):
+    """The OpenMP baseline behind the oracle's call names (header from the oracle)."""
+    class _Ops:
+        compress = staticmethod(omp.compress)
+        header = staticmethod(O.header)
+        negate = staticmethod(omp.negate)
+        add_scalar = staticmethod(omp.add_scalar)
+        mul_scalar = staticmethod(omp.mul_scalar)
+        add = staticmethod(omp.add)
+        mean = staticmethod(omp.mean)
+        var = staticmethod(omp.var)
+        decompress = staticmethod(omp.decompress)
+    return _Ops
 
 
 def sample_fields(A: np.ndarray, B: np.ndarray, n: int):
@@ -794,9 +844,18 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         a, b = sample_fields(A, B, args.oracle_sample)
         sec = run_oracle(a, b, 1, 0)
+        cores, model = host_cpu()
         cpu = {"value": 40.0 * a.size / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {a.size} values of fields A and B, one step of all rows",
-               "seconds": sec}
+               "seconds": sec, "host": {"nproc": cores, "cpu_model": model}}
+        try:
+            osec, threads = run_omp_baseline(a, b)
+            cpu["all_cores"] = {
+                "value": 40.0 * a.size / osec / 1e9, "unit": "GB/s", "cores": threads,
+                "kind": "oracle arithmetic + OpenMP loop over blocks (the paper's CPU design)",
+                "sample": "the same sample, median of 3 steps", "seconds": osec}
+        except (OSError, subprocess.CalledProcessError) as ex:  # no OpenMP toolchain
+            cpu["all_cores"] = {"unavailable": f"OpenMP build failed: {ex}"}
 
     value = world * 40.0 * n / ms_step / 1e6
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,

@@ -473,8 +473,13 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
             octet_deltas(br, kmax, j, S, d);
             octet_values(br, d, j, q);
             float v[8];
+            if (small) {  // uniform over the stream: no per-value select
 #pragma unroll
-            for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+              for (int t = 0; t < 8; t++) v[t] = dequant_small(q[t], e2);
+            } else {
+#pragma unroll
+              for (int t = 0; t < 8; t++) v[t] = dequant_any(q[t], e2);
+            }
             const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
             if (br.len == L) {
               float4* o = reinterpret_cast<float4*>(x + i0);

@@ -343,8 +343,13 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
             continue;
           }
           float v[8];
+          if (small) {  // uniform over the stream: no per-value select
 #pragma unroll
-          for (int t = 0; t < 8; t++) v[t] = small ? dequant_small(q[t], e2) : dequant_any(q[t], e2);
+            for (int t = 0; t < 8; t++) v[t] = dequant_small(q[t], e2);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 8; t++) v[t] = dequant_any(q[t], e2);
+          }
           if (br.len == L) {
             float4* o = reinterpret_cast<float4*>(x + i0);
             __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
