@@ -330,6 +330,41 @@ int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_st
                        const size_t* stream_bytes, hoszp_batch** out);
 void hoszp_batch_destroy(hoszp_batch* b);
 int hoszp_batch_info(const hoszp_batch* b, uint32_t* nfields, uint64_t* total_tiles);
+/* Batched producing operators: every field of a plan gets its own output
+ * stream, from one persistent launch over the plan's global tile space (a
+ * warp per 64-block tile, the field found per tile), one scan of all tiles'
+ * word counts and one placement launch -- no launch per field. Each field's
+ * result is byte for byte what the single-stream operator gives for it.
+ * d_outs: device array of nfields device pointers (16-byte aligned), d_caps:
+ * device array of their capacities in bytes, d_out_bytes: device array that
+ * receives each field's stream size (0 for a field that failed). Errors go to
+ * the plan's status (hoszp_batch_get_status). The first call may grow the
+ * plan's context workspace (a device allocation) to the batch's slots; later
+ * calls with the same or a smaller need allocate nothing, synchronize nothing
+ * and can be captured in a CUDA graph. Calls on one plan must not overlap.
+ * hoszp_batch_mul_scalar: every field times s (Sec. V-A), each with its own
+ *   bound's bin of s; RANGE when a field's bin of s is out of range.
+ * hoszp_batch_add: field by field A_f + B_f, or A_f - B_f when subtract != 0
+ *   (Sec. V-C); plan b must hold the same number of fields with the same n
+ *   and eps_q bits field by field (MISMATCH), the sums' bounds must stay
+ *   within 2^30 - 1 (OVERFLOW); errors go to plan a's status. */
+int hoszp_batch_mul_scalar(hoszp_batch* b, double s, void* const* d_outs, const uint64_t* d_caps,
+                           uint64_t* d_out_bytes, hoszp_stream_t stream);
+int hoszp_batch_add(hoszp_batch* a, hoszp_batch* b, int subtract, void* const* d_outs,
+                    const uint64_t* d_caps, uint64_t* d_out_bytes, hoszp_stream_t stream);
+/* Compression of many float fields in one launch over all their tiles (Sec.
+ * IV-A per field), with a range pass over every field's values first for
+ * relative bounds (eb_mode HOSZP_EB_REL: eps_f = eb[f] (max - min) of field f).
+ * d_x, d_outs: host arrays of nfields device pointers (fields 4-byte aligned,
+ * outputs 16-byte aligned); n, eb, caps: host arrays (n[f] in 1 .. 2^32 - 1);
+ * d_out_bytes: device array of nfields sizes. Each field is compressed as a
+ * 1-D field of n[f] values, byte for byte the stream hoszp_compress gives with
+ * dims = {n[f]}. Device errors go to the context's status. Uses the context's
+ * workspace for slots and tables (grown on the first call); asynchronous on
+ * stream, the host arrays may be released when the call returns. */
+int hoszp_batch_compress(hoszp_ctx* ctx, uint32_t nfields, const float* const* d_x,
+                         const uint64_t* n, const double* eb, int eb_mode, void* const* d_outs,
+                         const size_t* caps, uint64_t* d_out_bytes, hoszp_stream_t stream);
 /* Synchronizes the plan's device, returns its status word and clears it. */
 int hoszp_batch_get_status(hoszp_batch* b, int* status);
 

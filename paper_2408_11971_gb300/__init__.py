@@ -41,6 +41,7 @@ from ._binding import (  # noqa: F401
     sums,
     finish_sums,
     concat,
+    batch_compress,
     header,
     fop_axpb,
     fop_add,
@@ -51,5 +52,5 @@ __all__ = [
     "HoszpError", "Context", "Batch", "Server", "STATUS", "lib_path", "load_library",
     "default_context", "compress_bound", "compress", "decompress", "negate", "add_scalar",
     "sub_scalar", "mul_scalar", "mul_scalar_exact", "add", "sub", "hadamard", "mean", "var",
-    "std", "cov", "block_means", "sums", "finish_sums", "concat", "header", "fop_axpb", "fop_add", "fop_moments",
+    "std", "cov", "block_means", "sums", "finish_sums", "concat", "batch_compress", "header", "fop_axpb", "fop_add", "fop_moments",
 ]

@@ -84,6 +84,9 @@ def load_library():
             "hoszp_finish_sums": (I, [P, P, ctypes.c_float, P, P, P]),
             "hoszp_concat": (I, [P, ctypes.c_uint32, P, P, P, I, P, SZ, P, P]),
             "hoszp_selftest_wait": (I, [P, I, U64, P]),
+            "hoszp_batch_mul_scalar": (I, [P, D, P, P, P, P]),
+            "hoszp_batch_add": (I, [P, P, I, P, P, P, P]),
+            "hoszp_batch_compress": (I, [P, ctypes.c_uint32, P, P, P, I, P, P, P, P]),
             "hoszp_var": (I, [P, P, SZ, P, P]),
             "hoszp_std": (I, [P, P, SZ, P, P]),
             "hoszp_cov": (I, [P, P, SZ, P, SZ, P, P]),
@@ -632,6 +635,45 @@ class Batch:
         _check(self._lib.hoszp_batch_add_scalar(self.handle, float(s), _stream_ptr(stream)),
                "batch_add_scalar")
 
+    def _outputs(self, outs, bound_n):
+        torch = _torch()
+        if outs is None:
+            outs = [torch.empty(bound_n(c), dtype=torch.uint8, device=self.device)
+                    for c in self._streams]
+        ptrs = torch.tensor([o.data_ptr() for o in outs], dtype=torch.int64, device=self.device)
+        caps = torch.tensor([o.numel() for o in outs], dtype=torch.int64, device=self.device)
+        sizes = torch.zeros(len(outs), dtype=torch.int64, device=self.device)
+        return outs, ptrs, caps, sizes
+
+    def _produced(self, what, outs, ptrs, caps, sizes, sync, check):
+        self._keep = (ptrs, caps)  # kept alive until the next call (the launches read them)
+        if not sync:
+            return outs, sizes
+        _torch().cuda.synchronize(self.device)
+        if check:
+            self.check(what)
+        return [o[: int(k)] for o, k in zip(outs, sizes.cpu().tolist())]
+
+    def mul_scalar(self, s: float, outs=None, stream=None, sync: bool = True,
+                   check: bool = True):
+        """Every field times s (Sec. V-A), one launch over all fields (+ one
+        scan and one placement launch): a list of output streams."""
+        outs, ptrs, caps, sizes = self._outputs(outs, lambda c: compress_bound(header(c)["n"]))
+        _check(self._lib.hoszp_batch_mul_scalar(self.handle, float(s), _dev_ptr(ptrs),
+                                                _dev_ptr(caps), _dev_ptr(sizes),
+                                                _stream_ptr(stream)), "batch_mul_scalar")
+        return self._produced("batch_mul_scalar", outs, ptrs, caps, sizes, sync, check)
+
+    def add(self, other: "Batch", subtract: bool = False, outs=None, stream=None,
+            sync: bool = True, check: bool = True):
+        """Field by field A_f + B_f (or A_f - B_f; Sec. V-C) of this plan and
+        another with the same fields' shapes and bounds, one launch."""
+        outs, ptrs, caps, sizes = self._outputs(outs, lambda c: compress_bound(header(c)["n"]))
+        _check(self._lib.hoszp_batch_add(self.handle, other.handle, 1 if subtract else 0,
+                                         _dev_ptr(ptrs), _dev_ptr(caps), _dev_ptr(sizes),
+                                         _stream_ptr(stream)), "batch_add")
+        return self._produced("batch_add", outs, ptrs, caps, sizes, sync, check)
+
     def tune(self, stream=None):
         """Pick each reduction's launch shape from timed runs; returns the picks."""
         torch = _torch()
@@ -647,6 +689,40 @@ class Batch:
                                             ctypes.byref(cps)), "batch_config")
         return {"stages": st.value, "ctas_per_sm": cps.value}
 
+
+
+def batch_compress(xs, eb, mode: str = "rel", outs=None, stream=None, ctx=None,
+                   sync: bool = True, check: bool = True):
+    """Many float32 fields (1-D CUDA tensors) compressed in one launch over all
+    their tiles (+ a range pass for relative bounds, one scan and one placement
+    launch); eb: one bound per field (or one for all). Returns the streams."""
+    torch = _torch()
+    xs = [x.contiguous() for x in xs]
+    if not xs:
+        raise ValueError("no fields")
+    dev = xs[0].device
+    ctx = _ctx(ctx, xs[0])
+    k = len(xs)
+    ebs = list(eb) if hasattr(eb, "__len__") else [float(eb)] * k
+    if outs is None:
+        outs = [torch.empty(compress_bound(x.numel()), dtype=torch.uint8, device=dev) for x in xs]
+    sizes = torch.zeros(k, dtype=torch.int64, device=dev)
+    P = ctypes.c_void_p
+    xp = (P * k)(*[x.data_ptr() for x in xs])
+    ns = (ctypes.c_uint64 * k)(*[x.numel() for x in xs])
+    es = (ctypes.c_double * k)(*[float(e) for e in ebs])
+    op = (P * k)(*[o.data_ptr() for o in outs])
+    cp = (ctypes.c_size_t * k)(*[o.numel() for o in outs])
+    rc = load_library().hoszp_batch_compress(ctx.handle, k, xp, ns, es,
+                                             1 if mode == "rel" else 0, op, cp, _dev_ptr(sizes),
+                                             _stream_ptr(stream))
+    _check(rc, "batch_compress")
+    if not sync:
+        return outs, sizes
+    torch.cuda.synchronize(dev)
+    if check:
+        ctx.check("batch_compress")
+    return [o[: int(n)] for o, n in zip(outs, sizes.cpu().tolist())]
 
 
 class _DevBuf:

@@ -542,6 +542,23 @@ int ctx_prepare(hoszp_ctx* ctx, uint64_t tiles, Ws* ws, int* device, int* num_sm
   return HOSZP_OK;
 }
 
+// The compressor's bound for an absolute eps (batched compression, bproduce.cu).
+float eps_q_host(double eps) { return eps_q_of(eps); }
+
+// Batched producing operators (bproduce.cu): the workspace grown to a tile
+// count and a number of staging words.
+int ctx_prepare_staging(hoszp_ctx* ctx, uint64_t tiles, uint64_t staging_words, Ws* ws,
+                        int* device, int* num_sms) {
+  if (!ctx) return HOSZP_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  const int rc = ensure_ws(ctx, tiles, staging_words);
+  if (rc) return rc;
+  *ws = ctx->ws;
+  *device = ctx->device;
+  *num_sms = ctx->num_sms;
+  return HOSZP_OK;
+}
+
 // Serving (serve.cu): the context's device status word, its workspace size,
 // and a cap on the SMs its persistent grids spread over (0 restores all).
 int* ctx_status_word(hoszp_ctx* ctx) { return ctx ? ctx->ws.status : nullptr; }

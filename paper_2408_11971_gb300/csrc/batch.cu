@@ -23,26 +23,15 @@
 #include "hz_super.cuh"
 #include "hz_var.cuh"
 #include "hz_kernels.cuh"
+#include "batch_plan.cuh"
 
 namespace hz {
 int ctx_prepare(hoszp_ctx* ctx, uint64_t tiles, Ws* ws, int* device, int* num_sms);  // api.cu
+int* ctx_status_word(hoszp_ctx* ctx);                                                   // api.cu
 }  // namespace hz
 
 namespace hz {
 namespace {
-
-// One field of a plan (device table).
-struct BField {
-  const uint8_t* c;
-  uint8_t* cw;       // same stream, writable (in-place operators)
-  Info h;
-  uint64_t tile0;    // first tile in the global tile space
-  uint64_t ntiles;
-  uint64_t pre0;     // first word of the field's (nc, r) prefixes in pre[]
-  uint64_t ch0[2];   // first 16-byte chunk of the field's metadata region: [0] negate, [1] add
-  uint64_t nch[2];
-  long long rho;     // scalar addition: this field's quantized scalar (0: field skipped)
-};
 
 // ---------------------------------------------------------------- plan parsing
 __global__ void k_bparse(const uint8_t* const* ptrs, const uint64_t* bytes, uint32_t nf,
@@ -64,16 +53,6 @@ __global__ void k_bparse(const uint8_t* const* ptrs, const uint64_t* bytes, uint
 }
 
 // ---------------------------------------------------------------- field walk
-// Index of the field holding global tile t (fields have >= 1 tile; tile0 grows).
-__device__ __forceinline__ uint32_t field_of_tile(const BField* F, uint32_t nf, uint64_t t) {
-  uint32_t lo = 0, hi = nf;  // answer in [lo, hi)
-  while (hi - lo > 1) {
-    const uint32_t mid = lo + (hi - lo) / 2;
-    if (F[mid].tile0 <= t) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
 __device__ __forceinline__ uint32_t field_of_chunk(const BField* F, uint32_t nf, int op,
                                                    uint64_t ch) {
   uint32_t lo = 0, hi = nf;
@@ -617,48 +596,10 @@ __global__ void __launch_bounds__(512) k_bmeta(const BField* __restrict__ F, uin
   }
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-inline int rc_of(cudaError_t e) {
-  if (e == cudaSuccess) return HOSZP_OK;
-  cudaGetLastError();
-  return HOSZP_ERR_CUDA;
-}
-
 }  // namespace
 }  // namespace hz
 
 using namespace hz;
-
-// Autotuned launch shape of one reduction: pipeline depth (variant) and CTAs per SM.
-struct BatchCfg {
-  int variant;  // 0: tile pipeline, 8 stages; 1: tile pipeline, 4 stages; 2: super-tile pipeline
-  int cps;      // CTAs per SM (1 or 2; the super-tile pipeline takes one)
-};
-
-struct hoszp_batch {
-  hoszp_ctx* ctx;
-  int device, num_sms;
-  uint32_t nf;
-  uint64_t total_tiles, total_ch[2];
-  void* mem;
-  BField* d_fields;
-  unsigned long long* d_pre;
-  unsigned long long* d_acc;
-  unsigned int* d_done;
-  int* status;  // the plan's own status word (first device error of its operators)
-  BatchCfg cfg[2];  // mean, variance
-};
 
 namespace {
 
@@ -755,7 +696,10 @@ int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_st
   const size_t pbytes = (pre_words * 8 + 255) / 256 * 256;
   const size_t abytes = (nfields * 32 + 255) / 256 * 256;
   const size_t dbytes = (nfields * 4 + 255) / 256 * 256;
-  if (cudaMalloc(&b->mem, fbytes + pbytes + abytes + dbytes + 256) != cudaSuccess) {
+  const size_t xbytes = ((nfields + 1) * 16 + 255) / 256 * 256;  // fpre
+  const size_t obytes = (nfields * sizeof(BOut) + 255) / 256 * 256;
+  if (cudaMalloc(&b->mem, fbytes + pbytes + abytes + dbytes + 256 + xbytes + obytes) !=
+      cudaSuccess) {
     delete b;
     return rc_of(cudaErrorMemoryAllocation);
   }
@@ -765,7 +709,20 @@ int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_st
   b->d_acc = (unsigned long long*)(m + fbytes + pbytes);
   b->d_done = (unsigned int*)(m + fbytes + pbytes + abytes);
   b->status = (int*)(m + fbytes + pbytes + abytes + dbytes);
+  b->d_fpre = (unsigned long long*)(m + fbytes + pbytes + abytes + dbytes + 256);
+  b->d_out = (BOut*)(m + fbytes + pbytes + abytes + dbytes + 256 + xbytes);
   cudaMemcpy(b->d_fields, F.data(), nfields * sizeof(BField), cudaMemcpyHostToDevice);
+  {
+    std::vector<unsigned long long> fp(2 * (nfields + 1), 0ull);
+    for (uint32_t f = 0; f < nfields; f++) {
+      fp[2 * (f + 1)] = fp[2 * f] + F[f].h.nnc;
+      fp[2 * (f + 1) + 1] = fp[2 * f + 1] + F[f].h.R;
+    }
+    cudaMemcpy(b->d_fpre, fp.data(), fp.size() * 8, cudaMemcpyHostToDevice);
+    b->total_nnc = fp[2 * nfields];
+    b->total_R = fp[2 * nfields + 1];
+    cudaMemset(b->d_out, 0, obytes);
+  }
   cudaMemset(b->d_acc, 0, abytes + dbytes + 256);
   // each stream's rate pre-scan, once
   rc = ctx_prepare(ctx, max_tiles + 1, &ws, &device, &sms);
@@ -807,15 +764,20 @@ void hoszp_batch_destroy(hoszp_batch* b) {
 int hoszp_batch_get_status(hoszp_batch* b, int* status) {
   if (!b || !status) return HOSZP_ERR_ARG;
   DeviceGuard guard(b->device);
-  int v = 0;
+  int v = 0, vc = 0;
+  // the plan's own word, then the context's (the word scan of the producing
+  // operators reports there)
+  int* cst = ctx_status_word(b->ctx);
   if (cudaDeviceSynchronize() != cudaSuccess ||
       cudaMemcpy(&v, b->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemset(b->status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(b->status, 0, sizeof(int)) != cudaSuccess ||
+      (cst && (cudaMemcpy(&vc, cst, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+               cudaMemset(cst, 0, sizeof(int)) != cudaSuccess))) {
     cudaGetLastError();
     *status = HOSZP_ERR_CUDA;
     return HOSZP_ERR_CUDA;
   }
-  *status = v;
+  *status = v ? v : vc;
   return HOSZP_OK;
 }
 

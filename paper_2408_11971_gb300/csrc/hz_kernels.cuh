@@ -29,7 +29,7 @@ cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t*
 cudaError_t launch_scan(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                         unsigned long long* pre, Ws ws);
 // scan.cu: prefixes of the produced tiles' aggregates (launched by launch_place)
-cudaError_t launch_scan_agg(const Launch& lc, Ws ws);
+cudaError_t launch_scan_agg(const Launch& lc, Ws ws, uint64_t ntiles_given = 0);
 // decode.cu
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
                               uint64_t n, Ws ws);

@@ -23,9 +23,7 @@
 // and the placement kernel then move the words to their final places.
 #include <climits>
 
-#include "hz_lanes.cuh"
-#include "hz_mul.cuh"
-#include "hz_produce.cuh"
+#include "hz_mullanes.cuh"
 #include "hz_scalar.cuh"
 #include "hz_super.cuh"
 #include "hz_kernels.cuh"
@@ -42,37 +40,6 @@ constexpr int ML_NCW = ML_GW * ML_GROUPS;
 constexpr int ML_THREADS = (ML_NCW + 1) * 32;  // + loader warp
 constexpr int ML_STAGES = 6;
 constexpr uint32_t ML_RING = 22528;  // plane-ring words (176 KB)
-
-// Local prefixes of a half for the warp's widest input rate Rw.
-__device__ __forceinline__ void half_prefix_any(int Rw, const uint32_t t[32], bool zero0,
-                                                const lanes::Shifts& K, int p[32]) {
-  const int G = (Rw + 8) >> 3;
-  if (G == 1) lanes::half_prefix<1>(t, zero0, K, p);
-  else if (G == 2) lanes::half_prefix<2>(t, zero0, K, p);
-  else if (G == 3) lanes::half_prefix<3>(t, zero0, K, p);
-  else lanes::half_prefix<4>(t, zero0, K, p);
-}
-
-// Orders the work on v[0 .. 7] before the work on v[8 .. 15]: an empty asm
-// that takes the first eight as inputs and gives the next eight as outputs,
-// so the compiler cannot start the next chunk's 64- or 128-bit products early
-// (which would keep wide temporaries of all 32 values live at once).
-__device__ __forceinline__ void chunk_fence(int* v) {
-  asm volatile(""
-               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
-                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
-                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
-}
-
-// Bits of the largest |delta'| a warp can produce from input deltas below
-// 2^Rw: |q'_i - q'_(i-1)| < |k| |delta| + 1, so |delta'| <= ceil(|k| (2^Rw - 1))
-// (k = 2e rho, or s for the exact variant; kabs carries a relative margin).
-__device__ __forceinline__ int delta_bits(double kabs, int Rw) {
-  const double b = ceil(kabs * (double)((1u << Rw) - 1u));
-  if (!(b < 2147483648.0)) return 31;
-  const uint32_t v = (uint32_t)b;
-  return 32 - __clz(v);
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(ML_THREADS, 1) k_mul_lanes(
@@ -163,98 +130,12 @@ __global__ void __launch_bounds__(ML_THREADS, 1) k_mul_lanes(
       if (so + lim_nc > sign_cap || po + lim_r > ws.staging_words) tbad = HOSZP_ERR_CAPACITY;
       uint32_t* sdst = reinterpret_cast<uint32_t*>(ws.staging + so);
       uint32_t* pdst = reinterpret_cast<uint32_t*>(ws.staging + po);
-      uint32_t run = 0;  // output (sign words << 16 | plane words) of the tile so far
-      const int steps = (tr.nvt + 15) >> 4;  // warp-uniform
-      for (int it = 0; it < steps; it++) {
-        const int b = 16 * it + m;
-        uint32_t r, ex;
-        tile_block(tr, b, r, ex);
-        const int len =
-            (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
-        const int nval = min(max(len - 32 * hf, 0), 32);
-        const int O = len ? sg.outlier[TILE * ti + b] : 0;
-        const uint32_t sw = r ? sgn[2 * (ex >> 16) + hf] : 0u;
-        const int Rw = (int)__reduce_max_sync(0xffffffffu, r);
-        const bool fullblk = __all_sync(0xffffffffu, len == L);
-        int v[32];
-        {
-          uint32_t t[32];
-          lanes::twos_planes_any(Rw, pls + 2 * (ex & 0xffffu) + hf, (int)r, sw, t);
-          half_prefix_any(Rw, t, hf == 0, K, v);
-        }
-        // the second half's base: O plus the first half's delta total (every
-        // lane takes part in the exchange, then selects)
-        const int tot0 = __shfl_xor_sync(0xffffffffu, v[31], 1);
-        const int base = O + (hf ? tot0 : 0);
-        if (fullblk) {
-#pragma unroll
-          for (int i = 0; i < 32; i++) v[i] += base;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; i++) v[i] = (i < nval) ? v[i] + base : 0;
-        }
-        // requantization (the plan is uniform over the launch)
-        if (vp->f32) {
-          MulPlan mp;
-          mp.rho32 = vp->rho32;
-          mp.M32 = vp->M32;
-          mp.sh2 = vp->sh2;
-          mp.half = vp->half;
-#pragma unroll
-          for (int c8 = 0; c8 < 32; c8 += 8) {
-#pragma unroll
-            for (int i = c8; i < c8 + 8; i++) v[i] = mul_requant_f32(v[i], mp);
-            if (c8 < 24) chunk_fence(v + c8);
-          }
-        } else if (vp->fast) {
-          MulPlan mp;
-          mp.P = vp->P;
-          mp.sh = vp->sh;
-#pragma unroll
-          for (int c8 = 0; c8 < 32; c8 += 8) {
-#pragma unroll
-            for (int i = c8; i < c8 + 8; i++) v[i] = mul_requant_fast(v[i], mp, ovf);
-            if (c8 < 24) chunk_fence(v + c8);
-          }
-        } else {  // 128-bit products (rare): one value at a time, rotating the half
-          MulPlan mp;
-          mp.rho = vp->rho;
-          mp.M = vp->M;
-          mp.E = vp->E;
-#pragma unroll 1
-          for (int i = 0; i < 32; i++) {
-            const int x = mul_requant(v[0], mp, ovf);
-#pragma unroll
-            for (int j = 0; j < 31; j++) v[j] = v[j + 1];
-            v[31] = x;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          vmax = __vimax3_s32(vmax, v[i], v[i + 1]);
-          vmin = __vimin3_s32(vmin, v[i], v[i + 1]);
-        }
-        // Lorenzo on q' (Eq. 4): the second half's first delta takes the first
-        // half's last value
-        const int last0 = __shfl_xor_sync(0xffffffffu, v[31], 1);
-        const int o_new = v[0];
-#pragma unroll
-        for (int i = 31; i > 0; i--) v[i] -= v[i - 1];
-        v[0] = hf ? v[0] - last0 : 0;
-        if (!fullblk) {
-#pragma unroll
-          for (int i = 0; i < 32; i++)
-            if (i >= nval) v[i] = 0;
-        }
-        const bool valid = b < tr.nvt;
-        const int Ge = s_ge[Rw];
-        const int rate = encode_store_any(Ge, v, K, valid, sdst, pdst, lim_nc, lim_r, run, tbad);
-        if (valid && hf == 0) {
-          const uint64_t bi = tile * TILE + b;
-          out[HOSZP_HEADER_BYTES + bi] = (uint8_t)rate;
-          reinterpret_cast<int*>(out + off_outlier(h.nb))[bi] = o_new;
-        }
-      }
+      const int lastlen_t = (tile + 1 == ntiles) ? lastlen : L;
+      const uint32_t run =
+          mul_lanes_tile(tr, sgn, pls, &sg.outlier[TILE * ti], lastlen_t, vp, s_ge, K, sdst, pdst,
+                         lim_nc, lim_r, out + HOSZP_HEADER_BYTES + tile * TILE,
+                         reinterpret_cast<int*>(out + off_outlier(h.nb)) + tile * TILE, vmax, vmin,
+                         ovf, tbad);
       if (tbad) bad = tbad;
       if (lane == 0 && tile < ntiles) {
         ws.agg[tile] = ((unsigned long long)(run >> 16) << 32) | (run & 0xffffu);

@@ -132,13 +132,14 @@ constexpr int SA_THREADS = 256;
 constexpr int SA_PER_THREAD = 16;
 constexpr int SA_SUPER = SA_THREADS * SA_PER_THREAD;  // tiles per CTA step
 
-__global__ void __launch_bounds__(SA_THREADS) k_scan_agg(Ws ws) {
+__global__ void __launch_bounds__(SA_THREADS) k_scan_agg(Ws ws, uint64_t ntiles_given) {
   __shared__ unsigned long long s_w[SA_THREADS / 32];
   __shared__ unsigned long long s_pre[2];
   __shared__ unsigned int s_tile;
   __shared__ unsigned long long s_epoch;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  uint64_t ntiles = ntiles_of(nblocks(ws.hdr->n));
+  // the produced stream's tiles, or (batched producers) the global tile space
+  uint64_t ntiles = ntiles_given ? ntiles_given : ntiles_of(nblocks(ws.hdr->n));
   int bad = 0;
   if (ntiles + 1 > ws.max_tiles) {
     bad = HOSZP_ERR_CAPACITY;
@@ -207,8 +208,9 @@ __global__ void __launch_bounds__(SA_THREADS) k_scan_agg(Ws ws) {
   if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
-cudaError_t launch_scan_agg(const Launch& lc, Ws ws) {
-  k_scan_agg<<<persistent_grid(k_scan_agg, SA_THREADS, lc.grid), SA_THREADS, 0, lc.stream>>>(ws);
+cudaError_t launch_scan_agg(const Launch& lc, Ws ws, uint64_t ntiles_given) {
+  k_scan_agg<<<persistent_grid(k_scan_agg, SA_THREADS, lc.grid), SA_THREADS, 0, lc.stream>>>(
+      ws, ntiles_given);
   return cudaGetLastError();
 }
 
