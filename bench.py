@@ -353,95 +353,147 @@ def serving_bench(hz, xa, xb, eps_q, nfields: int, budget: int, rates, per_rate:
 
 
 # ---------------------------------------------------------------- batched
-def batched_bench(hz, xa, xb, nfields: int, seed: int = 3, reps: int = 5):
-    """One snapshot of `nfields` uneven fields (sizes log-uniform in 1e4..1e7
-    values, relative bounds log-uniform in 1e-5..1e-2; each a slice of field A
-    or B at a seeded offset), compressed and kept resident. Times the batched
-    mean and variance (one launch each over every field) against the same
-    reductions called field by field, and checks that both give the same
-    doubles."""
+def batched_pools(device, seed: int = 3):
+    """The batched workload's value pools: a 1-D sines signal with constant runs,
+    a 2-D and a 3-D Gaussian random field, about 1e7 values each (the kinds of
+    datagen.field_set_batched); every field is a seeded slice of its kind's pool."""
     import torch
 
-    rng = np.random.default_rng(seed)
-    n_all = xa.numel()
-    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e7), nfields)).astype(np.int64)
-    rels = np.exp(rng.uniform(np.log(1e-5), np.log(1e-2), nfields))
-    cap = hz.compress_bound(int(sizes.max()))
-    buf = torch.empty(cap, dtype=torch.uint8, device=xa.device)
-    size = torch.zeros(1, dtype=torch.int64, device=xa.device)
-    streams = []
-    for i in range(nfields):
-        base = xa if i % 2 == 0 else xb
-        n = int(sizes[i])
-        off = int(rng.integers(0, (n_all - n) // 4)) * 4
-        hz.compress(base[off:off + n], eb=float(rels[i]), mode="rel", out=buf, out_bytes=size,
-                    sync=False)
-        streams.append(buf[: int(size.item())].clone())
-    del buf
-    b = hz.Batch(streams)
-    cbytes = sum(c.numel() for c in streams)
-    orig = 4 * int(sizes.sum())
-    out = {"fields": nfields, "values": int(sizes.sum()), "compressed_gb": cbytes / 1e9}
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    res = torch.empty(nfields, dtype=torch.float64, device=xa.device)
-    per = torch.empty(nfields, dtype=torch.float64, device=xa.device)
-    for name, bfn, sfn in (("mean", b.mean, hz.mean), ("var", b.var, hz.var)):
-        bfn(out=res, sync=False)
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record()
-        for _ in range(reps):
-            bfn(out=res, sync=False)
-        e1.record()
-        torch.cuda.synchronize()
-        bms = e0.elapsed_time(e1) / reps
-        for i, c in enumerate(streams):  # warm the per-field path
-            sfn(c, out=per[i:i + 1], sync=False)
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record()
-        for i, c in enumerate(streams):
-            sfn(c, out=per[i:i + 1], sync=False)
-        e1.record()
-        torch.cuda.synchronize()
-        fms = e0.elapsed_time(e1)
-        b.check(name)
-        out[name] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
-                     "batched_orig_gbs": orig / bms / 1e6,
-                     "batched_frac_of_measured_hbm": cbytes / bms / 1e6 / measured_peak()[0],
-                     "identical_to_per_field": bool(torch.equal(res, per))}
-    # decompression of every field in one launch against field-by-field calls
-    offs = np.concatenate([[0], np.cumsum((sizes.astype(np.int64) + 3) // 4 * 4)])
-    big = torch.empty(int(offs[-1]), dtype=torch.float32, device=xa.device)
-    outs = [big[int(offs[i]):int(offs[i]) + int(sizes[i])] for i in range(nfields)]
-    b.decompress(outs, sync=False)
+    import datagen
+
+    pools = {1: datagen.sines_1d(10_000_000, seed=seed, const_frac=0.1),
+             2: datagen.grf((3163, 3163), seed=seed + 1).reshape(-1),
+             3: datagen.grf((216, 216, 216), seed=seed + 2).reshape(-1)}
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in pools.items()}
+
+
+def _timed(fn, reps):
+    import torch
+
+    fn()
     torch.cuda.synchronize()
-    e0, e1 = ev(), ev()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        b.decompress(outs, sync=False)
+        fn()
     e1.record()
     torch.cuda.synchronize()
-    bms = e0.elapsed_time(e1) / reps
-    b.check("decompress")
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_bench(hz, device, nfields: int, seed: int = 3, reps: int = 3):
+    """One snapshot of `nfields` uneven fields: sizes log-uniform in 1e4..1e7
+    values, relative bounds log-uniform in 1e-5..1e-2 and a 1-D/2-D/3-D kind per
+    field (datagen.field_set_batched), each field a seeded slice of its kind's
+    pool, compressed and kept resident. Every batched operator (one launch over
+    all fields, plus a scan and a placement for the producing ones) is timed
+    against the same operator called field by field, and the results of both
+    are compared."""
+    import torch
+
+    import datagen
+
+    specs, _ = datagen.field_set_batched(nfields, seed=seed)
+    pools = batched_pools(device, seed)
+    rng = np.random.default_rng(seed + 7)
+    xs, xbs, rels = [], [], []
+    for n, rel, kind in specs:
+        pool = pools[kind]
+        o1 = int(rng.integers(0, (pool.numel() - n) // 4 + 1)) * 4  # 16-byte aligned slices
+        o2 = int(rng.integers(0, (pool.numel() - n) // 4 + 1)) * 4
+        xs.append(pool[o1:o1 + n])
+        xbs.append(pool[o2:o2 + n])
+        rels.append(rel)
+    sizes = np.array([n for n, _, _ in specs], np.int64)
+    orig = 4 * int(sizes.sum())
+    out = {"fields": nfields, "values": int(sizes.sum()),
+           "recipe": "datagen.field_set_batched sizes, bounds and kinds; values are seeded "
+                     "slices of a 1e7-value pool per kind"}
+    # resident streams: A at its relative bound, B at A's absolute bound (for A + B)
+    ca = hz.batch_compress(xs, rels, mode="rel")
+    eqs = [float(hz.header(c)["eps_q"]) for c in ca]
+    cb = hz.batch_compress(xbs, eqs, mode="abs")
+    cbytes = sum(c.numel() for c in ca)
+    out["compressed_gb"] = cbytes / 1e9
+    peak = measured_peak()[0]
+    bA, bB = hz.Batch(ca), hz.Batch(cb)
+    res = torch.empty(nfields, dtype=torch.float64, device=device)
+    per = torch.empty(nfields, dtype=torch.float64, device=device)
+    for name, bfn, sfn in (("mean", bA.mean, hz.mean), ("var", bA.var, hz.var)):
+        bms = _timed(lambda: bfn(out=res, sync=False), reps)
+
+        def fields():
+            for i, c in enumerate(ca):
+                sfn(c, out=per[i:i + 1], sync=False)
+        fms = _timed(fields, 1)
+        bA.check(name)
+        out[name] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
+                     "batched_orig_gbs": orig / bms / 1e6,
+                     "batched_frac_of_measured_hbm": cbytes / bms / 1e6 / peak,
+                     "identical_to_per_field": bool(torch.equal(res, per))}
+    # decompression into one float arena
+    offs = np.concatenate([[0], np.cumsum((sizes + 3) // 4 * 4)])
+    big = torch.empty(int(offs[-1]), dtype=torch.float32, device=device)
+    douts = [big[int(offs[i]):int(offs[i]) + int(sizes[i])] for i in range(nfields)]
+    bms = _timed(lambda: bA.decompress(douts, sync=False), reps)
+    bA.check("decompress")
     first = big.clone()
-    for i, c in enumerate(streams):  # warm the per-field path
-        hz.decompress(c, out=outs[i], check=False)
-    torch.cuda.synchronize()
-    e0, e1 = ev(), ev()
-    e0.record()
-    for i, c in enumerate(streams):
-        hz.decompress(c, out=outs[i], check=False)
-    e1.record()
-    torch.cuda.synchronize()
-    fms = e0.elapsed_time(e1)
+
+    def dfields():
+        for i, c in enumerate(ca):
+            hz.decompress(c, out=douts[i], check=False)
+    fms = _timed(dfields, 1)
     out["decompress"] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
                          "batched_orig_gbs": orig / bms / 1e6,
-                         "batched_frac_of_measured_hbm": (cbytes + orig) / bms / 1e6 / measured_peak()[0],
+                         "batched_frac_of_measured_hbm": (cbytes + orig) / bms / 1e6 / peak,
                          "identical_to_per_field": bool(torch.equal(first, big))}
-    del big, first, outs
-    b.close()
-    del streams
+    del big, first, douts
+    # producing operators: outputs in one arena per arm, compared byte for byte
+    bounds = [hz.compress_bound(int(n)) for n in sizes]
+    boffs = np.concatenate([[0], np.cumsum([(b + 255) // 256 * 256 for b in bounds])])
+
+    def arena():
+        buf = torch.empty(int(boffs[-1]), dtype=torch.uint8, device=device)
+        return buf, [buf[int(boffs[i]):int(boffs[i]) + bounds[i]] for i in range(nfields)]
+
+    a1, o1 = arena()
+    a2, o2 = arena()
+    sz1 = torch.zeros(nfields, dtype=torch.int64, device=device)
+    cases = (
+        ("mul_scalar", lambda: bA.mul_scalar(SCALAR_MUL, outs=o1, sync=False),
+         lambda i: hz.mul_scalar(ca[i], SCALAR_MUL, out=o2[i], out_bytes=sz1[i:i + 1],
+                                 sync=False), cbytes),
+        ("add", lambda: bA.add(bB, outs=o1, sync=False),
+         lambda i: hz.add(ca[i], cb[i], out=o2[i], out_bytes=sz1[i:i + 1], sync=False),
+         cbytes + sum(c.numel() for c in cb)),
+        ("compress", lambda: hz.batch_compress(xs, rels, mode="rel", outs=o1, sync=False),
+         lambda i: hz.compress(xs[i], eb=rels[i], mode="rel", out=o2[i],
+                               out_bytes=sz1[i:i + 1], sync=False), orig),
+    )
+    for name, bfn, sfn, in_bytes in cases:
+        holder = {}
+
+        def run_b():
+            holder["r"] = bfn()
+        bms = _timed(run_b, reps)
+        sizes_b = holder["r"][1]
+
+        def run_f():
+            for i in range(nfields):
+                sfn(i)
+        fms = _timed(run_f, 1)
+        same = bool(torch.equal(sizes_b, sz1))
+        if same:
+            nb = sizes_b.cpu().tolist()
+            same = all(torch.equal(o1[i][:nb[i]], o2[i][:nb[i]]) for i in range(nfields))
+        out_bytes = int(sizes_b.sum().item())
+        out[name] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
+                     "batched_orig_gbs": orig / bms / 1e6,
+                     "batched_frac_of_measured_hbm": (in_bytes + out_bytes) / bms / 1e6 / peak,
+                     "identical_to_per_field": same}
+    bA.close()
+    bB.close()
+    del a1, a2, o1, o2, ca, cb, pools, xs, xbs
     torch.cuda.empty_cache()
     return out
 
@@ -831,7 +883,7 @@ def main():
 
     batched = None
     if world == 1 and not args.no_batched:
-        batched = batched_bench(hz, xa, xb, args.batch_fields)
+        batched = batched_bench(hz, xa.device, args.batch_fields)
 
     serving = None
     if world == 1 and not args.no_serving:
