@@ -306,3 +306,26 @@ def test_concat_shards_into_the_field_stream(hz):
     small = torch.empty(256, dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError, match="CAPACITY"):
         hz.concat([a, b], (x.size,), out=small)
+
+
+@pytest.mark.parametrize("kind", ["sines", "grf", "mask", "const"])
+def test_compress_output_sizes(hz, kind):
+    """Compression into the library's bound and into a buffer of exactly the
+    stream's size gives the oracle's bytes (constant runs, no constant block,
+    land mask, a constant field); one 16-byte unit less is CAPACITY."""
+    if kind == "sines":
+        x = datagen.sines_1d(300_017, seed=17)  # about 20 % constant runs
+    elif kind == "grf":
+        x = datagen.grf((24, 48, 50), seed=18).reshape(-1)  # no constant block
+    elif kind == "mask":
+        x = datagen.lat_bands_2d(180, 360, seed=19).reshape(-1)
+    else:
+        x = np.full(70_001, np.float32(2.5), np.float32)
+    want = O.compress(x, eb=1e-4, mode="rel")
+    assert np.array_equal(host(hz.compress(dev(x), eb=1e-4, mode="rel")), want)
+    exact = torch.empty(want.size, dtype=torch.uint8, device="cuda")
+    got = hz.compress(dev(x), eb=1e-4, mode="rel", out=exact)
+    assert np.array_equal(host(got), want)
+    small = torch.empty(want.size - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(RuntimeError, match="CAPACITY"):
+        hz.compress(dev(x), eb=1e-4, mode="rel", out=small)
