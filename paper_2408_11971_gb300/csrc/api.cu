@@ -397,13 +397,15 @@ static int add_sub(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* 
   if ((o < a + a_bytes && a < o + cap) || (o < b + b_bytes && b < o + cap)) return HOSZP_ERR_ARG;
   DeviceGuard g(ctx->device);
   const uint64_t ta = tiles_from_bytes(a_bytes), tb = tiles_from_bytes(b_bytes);
-  // slot words: the two inputs' sign and plane words
-  int rc = ensure_ws(ctx, ta > tb ? ta : tb, (a_bytes + b_bytes) / 8 + 64);
+  // slot words: sign slots for A's plus B's sign words, then plane slots for
+  // their sign and plane words (a non-constant block takes >= 21 stream bytes)
+  const uint64_t nnc_bound = a_bytes / 21 + b_bytes / 21 + 2;
+  int rc = ensure_ws(ctx, ta > tb ? ta : tb, 2 * nnc_bound + (a_bytes + b_bytes) / 8 + 64);
   if (rc) return rc;
   Launch lc = lc_of(ctx, stream);
   rc = cuda_rc(launch_add(lc, a, a_bytes, b, b_bytes, o, cap, subtract, ctx->ws));
   if (rc) return rc;
-  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_EXPLICIT, 0, ctx->ws));
+  return cuda_rc(launch_place(lc, o, cap, d_out_bytes, SLOT_SPLIT, 0, ctx->ws));
 }
 
 int hoszp_add(hoszp_ctx* ctx, const void* d_a, size_t a_bytes, const void* d_b, size_t b_bytes,

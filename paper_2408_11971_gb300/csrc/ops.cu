@@ -340,22 +340,22 @@ cudaError_t launch_hadamard(const Launch& lc, const uint8_t* a, uint64_t a_bytes
 //
 // Inputs come through the two-stream super-tile pipeline of hz_super.cuh
 // (4 tiles of A and of B per stage, one loader warp, in-kernel rate prefixes of
-// both streams, no pre-scan launch). CTA: four groups of 4 compute warps;
-// group i takes tile i of every stage (thread = one 32-position half of one of
-// the tile's 64 blocks). Each tile's words go to its workspace slot, whose
-// offset (the words of A and B before the tile) is written for placement.
+// both streams, no pre-scan launch). Four groups of 4 compute warps take the
+// stages in turn; warp i of a group takes tile i of its stage and walks it 16
+// blocks at a time (lane 2m + h: half h of block m), keeping a running count
+// of the tile's output sign and plane words, so it writes every block's words
+// at once -- no barrier inside the loop. Sign words go to the tile's sign slot
+// and plane words to its plane slot (the SPLIT rule), at upper bounds known from
+// the inputs' prefixes: a block of the sum has a sign word only where A or B
+// has one, and at most max(rate_A, rate_B) + 1 planes.
 constexpr int ADD_NT = 4;        // tiles per stage
-constexpr int ADD_STAGES = 3;
-constexpr uint32_t ADD_RING = 16384;  // plane-ring words (128 KB), A's and B's words of a stage
-constexpr int ADD_TS = 4096;     // tile sums kept per stream
-constexpr int ADD_GW = 4;        // warps per group (one tile)
-constexpr int ADD_GROUPS = ADD_NT;
+constexpr int ADD_STAGES = 8;
+constexpr uint32_t ADD_RING = 18432;  // plane-ring words (144 KB), A's and B's words of stages
+constexpr int ADD_TS = 2048;     // tile sums kept per stream
+constexpr int ADD_GW = ADD_NT;   // warps per group (one per tile)
+constexpr int ADD_GROUPS = 4;
 constexpr int ADD_NCW = ADD_GROUPS * ADD_GW;
 constexpr int ADD_THREADS = (ADD_NCW + 1) * 32;  // + loader warp
-
-__device__ __forceinline__ void add_bar(int grp) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(ADD_GW * 32) : "memory");
-}
 
 template <bool SUB>
 __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
@@ -368,9 +368,8 @@ __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
   __shared__ uint64_t full[ADD_STAGES], empty[ADD_STAGES];
   __shared__ unsigned long long stage_st[ADD_STAGES];
   __shared__ uint32_t s_ts[2 * ADD_TS];
-  __shared__ uint8_t srate[ADD_GROUPS][2][TILE];
   __shared__ int s_ok;
-  const int tid = threadIdx.x, w = tid >> 5;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const Info ha = parse_header(a, a_bytes);
   const Info hb = parse_header(b, b_bytes);
   const unsigned long long epoch = launch_epoch(ws);
@@ -382,7 +381,7 @@ __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
       bad = HOSZP_ERR_MISMATCH;
     else if ((long long)ha.qbound + (long long)hb.qbound > HOSZP_QLIM)
       bad = HOSZP_ERR_OVERFLOW;
-    else if (cap < off_sign(ha.nb))
+    else if (cap < off_sign(ha.nb) || ntiles_of(ha.nb) + 1 > ws.max_tiles)
       bad = HOSZP_ERR_CAPACITY;
     else
       ok = 1;
@@ -393,7 +392,7 @@ __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
     }
     for (int k = 0; k < ADD_STAGES; k++) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], ADD_NCW);
+      mbar_init(&empty[k], ADD_GW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -407,115 +406,136 @@ __global__ void __launch_bounds__(ADD_THREADS, 1) k_add(
   __syncthreads();
   if (w == ADD_NCW) {
     __shared__ uint32_t s_beg[ADD_STAGES];
-    super_loader_n<ADD_NT, 2, ADD_STAGES, ADD_RING, 1>(stages, ring, s_beg, full, empty, stage_st,
-                                                        cs, hs, rg, s_ts, ADD_TS, ws, epoch);
+    super_loader_n<ADD_NT, 2, ADD_STAGES, ADD_RING, ADD_GROUPS>(
+        stages, ring, s_beg, full, empty, stage_st, cs, hs, rg, s_ts, ADD_TS, ws, epoch);
   } else if (w < ADD_NCW) {
-    const int grp = tid / (ADD_GW * 32), lt = tid % (ADD_GW * 32);
-    const int g = lt >> 1, hf = lt & 1;  // block of the tile, half (positions 32hf..32hf+31)
+    const int grp = w / ADD_GW, ti = w % ADD_GW;
+    const int hf = lane & 1, m = lane >> 1;
+    // the header values the loop needs, in registers (the stream tables above
+    // are passed by address and may live in local memory)
+    const uint64_t nb = ha.nb;
+    // sign slots first (at most A's plus B's sign words), plane slots after
+    const uint64_t sign_cap = umin64(ha.nnc + hb.nnc, ws.staging_words);
     for (uint64_t k = 0;; k++) {
-      const int st = (int)(k % ADD_STAGES);
-      mbar_wait(&full[st], (uint32_t)((k / ADD_STAGES) & 1), ws.status);  // add_bar below: no early exit
+      const uint64_t u = k * ADD_GROUPS + grp;  // stage use taken by this group
+      const int st = (int)(u % ADD_STAGES);
+      if (!mbar_wait_warp(&full[st], (uint32_t)((u / ADD_STAGES) & 1), ws.status)) break;
       const unsigned long long s = stage_st[st];
       if (s == ~0ull) break;
       const St& sa = stages[st];
       const St& sb = stages[ADD_STAGES + st];
-      const uint64_t tile = (uint64_t)ADD_NT * s + grp;
-      const TileRates tra = tile_rates(sa, grp, tile, ha.nb);
-      const TileRates trb = tile_rates(sb, grp, tile, hb.nb);
-      uint32_t ra, exa, rb, exb;
-      tile_block(tra, g, ra, exa);
-      tile_block(trb, g, rb, exb);
-      const uint32_t* pa = reinterpret_cast<const uint32_t*>(ring + sa.pring + sa.pbase +
-                                                             sa.tr[grp] + (exa & 0xffffu)) + hf;
-      const uint32_t* pb = reinterpret_cast<const uint32_t*>(ring + sb.pring + sb.pbase +
-                                                             sb.tr[grp] + (exb & 0xffffu)) + hf;
-      const uint32_t siga =
-          ra ? reinterpret_cast<const uint32_t*>(sa.sign + sa.sbase + sa.tnc[grp] + (exa >> 16))[hf]
-             : 0u;
-      uint32_t sigb =
-          rb ? reinterpret_cast<const uint32_t*>(sb.sign + sb.sbase + sb.tnc[grp] + (exb >> 16))[hf]
-             : 0u;
-      if (SUB) sigb = ~sigb;
-      const int oa = sa.outlier[TILE * grp + g], ob = sb.outlier[TILE * grp + g];
-      // slot of this tile: the words of A and B before it
-      const uint64_t so = sa.bnc + sa.tnc[grp] + sa.br + sa.tr[grp] + sb.bnc + sb.tnc[grp] + sb.br +
-                          sb.tr[grp];
+      const uint64_t tile = (uint64_t)ADD_NT * s + ti;
+      const TileRates tra = tile_rates(sa, ti, tile, nb);
+      const TileRates trb = tile_rates(sb, ti, tile, nb);
       const int nvt = tra.nvt;
-      const int m = max((int)ra, (int)rb);
-      // planes 0 .. P of the two's-complement sum, P = the warp's largest m + 1
-      // (|delta_A + delta_B| < 2^(m+1), so plane m+1 and above are the sign;
-      // a thread whose own m is smaller just sign-extends further). Fully
-      // unrolled over P so the planes live in registers and every load of the
-      // block is issued at once.
-      const int P = (int)__reduce_max_sync(0xffffffffu, (unsigned)(m > 0 ? m + 1 : 0));
-      uint32_t z[MAX_RATE + 2];
-      uint32_t sgn = 0u, nzp = 0u;
-      if (P > 0) {
-        uint32_t ca = siga, cb = sigb, cz = 0u;
+      const uint32_t* sgA = reinterpret_cast<const uint32_t*>(sa.sign + sa.sbase + sa.tnc[ti]);
+      const uint32_t* plA =
+          reinterpret_cast<const uint32_t*>(ring + sa.pring + sa.pbase + sa.tr[ti]);
+      const uint32_t* sgB = reinterpret_cast<const uint32_t*>(sb.sign + sb.sbase + sb.tnc[ti]);
+      const uint32_t* plB =
+          reinterpret_cast<const uint32_t*>(ring + sb.pring + sb.pbase + sb.tr[ti]);
+      // slots of the tile: upper bounds of the sum's words before it
+      const uint64_t ancA = sa.bnc + sa.tnc[ti], arA = sa.br + sa.tr[ti];
+      const uint64_t ancB = sb.bnc + sb.tnc[ti], arB = sb.br + sb.tr[ti];
+      const uint64_t so = ancA + ancB, po = sign_cap + ancA + ancB + arA + arB;
+      const uint32_t tA = __shfl_sync(0xffffffffu, tra.e1 + (tra.r1 ? 0x10000u : 0u) + tra.r1, 31);
+      const uint32_t tB = __shfl_sync(0xffffffffu, trb.e1 + (trb.r1 ? 0x10000u : 0u) + trb.r1, 31);
+      const uint32_t lim_nc = (tA >> 16) + (tB >> 16);
+      const uint32_t lim_r = lim_nc + (tA & 0xffffu) + (tB & 0xffffu);
+      int tbad = 0;
+      if (so + lim_nc > sign_cap || po + lim_r > ws.staging_words) tbad = HOSZP_ERR_CAPACITY;
+      uint32_t* sdst = reinterpret_cast<uint32_t*>(ws.staging + so);
+      uint32_t* pdst = reinterpret_cast<uint32_t*>(ws.staging + po);
+      uint32_t run = 0;  // output (sign words << 16 | plane words) of the tile so far
+      const int steps = (nvt + 15) >> 4;  // warp-uniform
+      for (int it = 0; it < steps; it++) {
+        const int bk = 16 * it + m;
+        uint32_t ra, exa, rb, exb;
+        tile_block(tra, bk, ra, exa);
+        tile_block(trb, bk, rb, exb);
+        const bool valid = bk < nvt;
+        const uint32_t* pa = plA + 2 * (exa & 0xffffu) + hf;
+        const uint32_t* pb = plB + 2 * (exb & 0xffffu) + hf;
+        const uint32_t siga = ra ? sgA[2 * (exa >> 16) + hf] : 0u;
+        uint32_t sigb = rb ? sgB[2 * (exb >> 16) + hf] : 0u;
+        if (SUB) sigb = ~sigb;  // negation flips every sign bit (a zero stays zero)
+        const int mr = max((int)ra, (int)rb);
+        // planes 0 .. P of the two's-complement sum, P = the warp's largest m + 1
+        // (|delta_A + delta_B| < 2^(m+1), so plane m+1 and above are the sign; a
+        // lane whose own m is smaller just sign-extends further). Unrolled over P
+        // so the planes live in registers and every load of the block is issued
+        // at once.
+        const int P = (int)__reduce_max_sync(0xffffffffu, (unsigned)(mr > 0 ? mr + 1 : 0));
+        uint32_t z[MAX_RATE + 2];
+        uint32_t sgn = 0u, nzp = 0u;
+        if (P > 0) {
+          uint32_t cA = siga, cB = sigb, cz = 0u;
 #pragma unroll
-        for (int p = 0; p <= MAX_RATE + 1; p++) {
-          if (p > P) break;
-          const uint32_t xa = (p < (int)ra ? pa[2 * p] : 0u) ^ siga;
-          const uint32_t xb = (p < (int)rb ? pb[2 * p] : 0u) ^ sigb;
-          const uint32_t x = xa ^ ca, y = xb ^ cb;
-          ca &= xa;
-          cb &= xb;
-          z[p] = x ^ y ^ cz;
-          cz = (x & y) | (cz & (x ^ y));
-          sgn = z[p];  // the last plane computed, P, is the sign
+          for (int p = 0; p <= MAX_RATE + 1; p++) {
+            if (p > P) break;
+            const uint32_t xa = (p < (int)ra ? pa[2 * p] : 0u) ^ siga;
+            const uint32_t xb = (p < (int)rb ? pb[2 * p] : 0u) ^ sigb;
+            const uint32_t x = xa ^ cA, y = xb ^ cB;
+            cA &= xa;
+            cB &= xb;
+            z[p] = x ^ y ^ cz;
+            cz = (x & y) | (cz & (x ^ y));
+            sgn = z[p];  // the last plane computed, P, is the sign
+          }
+          uint32_t cu = sgn;  // back to sign and magnitude over planes 0 .. P-1
+#pragma unroll
+          for (int p = 0; p <= MAX_RATE; p++) {
+            if (p >= P) break;
+            const uint32_t tt = z[p] ^ sgn;
+            const uint32_t mg = tt ^ cu;
+            cu &= tt;
+            z[p] = mg;
+            nzp |= (mg != 0u ? 1u : 0u) << p;
+          }
+        }
+        nzp |= __shfl_xor_sync(0xffffffffu, nzp, 1);
+        int rate = valid ? 32 - __clz(nzp) : 0;
+        if (rate > MAX_RATE) {  // only a header whose qbound understates its values gets here
+          tbad = HOSZP_ERR_OVERFLOW;
+          rate = MAX_RATE;
+        }
+        // the tile-local exclusive prefix (sign words << 16 | plane words)
+        const uint32_t pk = (hf == 0 && rate > 0) ? ((1u << 16) | (uint32_t)rate) : 0u;
+        uint32_t inc = pk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const uint32_t ex = __shfl_sync(0xffffffffu, inc - pk, lane & ~1);
+        const uint32_t step = __shfl_sync(0xffffffffu, inc, 31);
+        const uint32_t nc0 = (run >> 16) + (ex >> 16), r0 = (run & 0xffffu) + (ex & 0xffffu);
+        run += step;
+        if (tbad == 0 && rate > 0 && (nc0 >= lim_nc || r0 + (uint32_t)rate > lim_r))
+          tbad = HOSZP_ERR_CAPACITY;
+        if (tbad == 0 && rate > 0) {
+          sdst[2 * nc0 + hf] = sgn;
+          uint32_t* dst = pdst + 2 * r0 + hf;
+#pragma unroll
+          for (int p = 0; p <= MAX_RATE; p++) {
+            if (p >= P) break;
+            if (p < rate) dst[2 * p] = z[p];
+          }
+        }
+        if (valid && hf == 0) {
+          const uint64_t bi = tile * TILE + bk;
+          const int oa = sa.outlier[TILE * ti + bk], ob = sb.outlier[TILE * ti + bk];
+          out[HOSZP_HEADER_BYTES + bi] = (uint8_t)rate;
+          reinterpret_cast<int*>(out + off_outlier(nb))[bi] = SUB ? oa - ob : oa + ob;
         }
       }
       __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(&empty[st]);
-      // back to sign and magnitude: magnitude = (z ^ s) + s, planes 0 .. P-1
-      if (P > 0) {
-        uint32_t cu = sgn;
-#pragma unroll
-        for (int p = 0; p <= MAX_RATE; p++) {
-          if (p >= P) break;
-          const uint32_t t = z[p] ^ sgn;
-          const uint32_t mg = t ^ cu;
-          cu &= t;
-          z[p] = mg;
-          nzp |= (mg != 0u ? 1u : 0u) << p;
-        }
-      }
-      nzp |= __shfl_xor_sync(0xffffffffu, nzp, 1);
-      int rate = 32 - __clz(nzp);
-      if (rate > MAX_RATE) {  // only a header whose qbound understates its values gets here
-        bad = HOSZP_ERR_OVERFLOW;
-        rate = MAX_RATE;
-      }
-      const uint64_t bi = tile * TILE + g;
-      const bool valid = g < nvt;
-      uint8_t* rr = srate[grp][k & 1];
-      if (hf == 0) {
-        rr[g] = valid ? (uint8_t)rate : 0;
-        if (valid) {
-          out[HOSZP_HEADER_BYTES + bi] = (uint8_t)rate;
-          reinterpret_cast<int*>(out + off_outlier(ha.nb))[bi] = SUB ? oa - ob : oa + ob;
-        }
-      }
-      add_bar(grp);
-      if (nvt == 0) continue;  // a tile past the stream's end (group-uniform)
-      const TileOff off = warp_tile_offsets(rr, 0, TILE, g, bad);
-      if (so + off.agg_nc + off.agg_r > ws.staging_words) {
-        bad = HOSZP_ERR_CAPACITY;
-        continue;
-      }
-      uint32_t* slot = reinterpret_cast<uint32_t*>(ws.staging + so);
-      if (valid && rate > 0) {
-        slot[2 * off.nc_excl + hf] = sgn;
-        uint32_t* dst = slot + 2 * (off.agg_nc + off.r_excl) + hf;
-#pragma unroll
-        for (int p = 0; p <= MAX_RATE; p++) {
-          if (p >= P) break;
-          if (p < rate) dst[2 * p] = z[p];
-        }
-      }
-      if (lt == 0) {
-        ws.agg[tile] = ((unsigned long long)off.agg_nc << 32) | off.agg_r;
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (tbad) bad = tbad;
+      if (lane == 0 && tile < ntiles) {
+        ws.agg[tile] = ((unsigned long long)(run >> 16) << 32) | (run & 0xffffu);
         ws.pre[0][2 * tile] = so;
+        ws.pre[0][2 * tile + 1] = po;
       }
     }
   }
