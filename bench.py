@@ -81,6 +81,71 @@ def ncu_traffic(op: str):
     return None
 
 
+# kernels of one benchmark step, operator by operator, in launch order
+STEP_KERNELS = (("compress A", ("k_range", "k_compress", "k_scan_agg", "k_place")),
+                ("compress B", ("k_compress", "k_scan_agg", "k_place")),
+                ("negate", ("k_meta<1>",)), ("add_scalar", ("k_meta<0>",)),
+                ("mul_scalar", ("k_mul_lanes", "k_scan_agg", "k_place")),
+                ("add", ("k_add", "k_scan_agg", "k_place")), ("mean", ("k_mean",)),
+                ("var", ("k_var",)), ("decompress", ("k_decompress",)))
+
+
+def traffic_from_csv(path: str, shape) -> dict:
+    """Per-operator DRAM bytes from an ncu launch list of the benchmark step
+    (metrics gpu__time_duration.sum, dram__bytes_read.sum, dram__bytes_write.sum),
+    captured on fields of `shape`: the library's launches are matched against
+    the step's kernel sequence, the first step is dropped (cold), the others
+    averaged, and bytes are scaled to the 512^3 workload by the number of values.
+    Writes profiles/traffic.json with the hash of the kernel sources."""
+    import csv
+
+    rows = list(csv.reader(open(path)))
+    start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[start]
+    ki, mi, vi, ii = (hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "ID"))
+    launches = {}
+    for r in rows[start + 1:]:
+        if len(r) <= max(ki, mi, vi, ii):
+            continue
+        name = r[ki].split("(")[0].replace("void ", "").strip()
+        if not name.startswith("hz::"):
+            continue
+        d = launches.setdefault(int(r[ii]), {"name": name[4:]})
+        d[r[mi]] = float(r[vi].replace(",", ""))
+    seq = [launches[k] for k in sorted(launches)]
+    flat = [k for _, ks in STEP_KERNELS for k in ks]
+    hits = [i for i in range(len(seq) - len(flat) + 1)
+            if all(seq[i + j]["name"].startswith(flat[j]) for j in range(len(flat)))]
+    if not hits:
+        raise SystemExit("no complete benchmark step in " + path)
+    use = hits[1:] or hits
+    scale = float(np.prod(DEFAULT_SHAPE)) / float(np.prod(shape))
+    ops = {}
+    for s0 in use:
+        i = s0
+        for op, ks in STEP_KERNELS:
+            part = seq[i:i + len(ks)]
+            i += len(ks)
+            o = ops.setdefault(op, {"kernels": list(ks), "us": 0.0, "dram_read": 0.0,
+                                    "dram_write": 0.0})
+            o["us"] += sum(p["gpu__time_duration.sum"] for p in part) / 1e3 / len(use)
+            o["dram_read"] += sum(p["dram__bytes_read.sum"] for p in part) * scale / len(use)
+            o["dram_write"] += sum(p["dram__bytes_write.sum"] for p in part) * scale / len(use)
+    for o in ops.values():
+        o["dram_bytes_per_launch"] = o["dram_read"] + o["dram_write"]
+    out = {"csrc_sha": csrc_hash(), "capture_shape": list(shape), "scale_to_full": scale,
+           "steps_averaged": len(use), "ops": ops}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print("| op | kernels | us | DRAM read MB | DRAM write MB | read+write MB (scaled to 512^3) |")
+    print("|---|---|---|---|---|---|")
+    for op, o in ops.items():
+        print(f"| {op} | {' '.join(o['kernels'])} | {o['us']:.1f} | {o['dram_read'] / scale / 1e6:.1f}"
+              f" | {o['dram_write'] / scale / 1e6:.1f} | {o['dram_bytes_per_launch'] / 1e6:.1f} |")
+    print(f"step under ncu: {sum(o['us'] for o in ops.values()):.1f} us")
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -519,9 +584,15 @@ def main():
                     choices=["compress", "decompress", "negate", "add_scalar", "mul_scalar", "add",
                              "mean", "var", "cov"],
                     help="run only this operator 4 times (for ncu captures; prints no bench line)")
+    ap.add_argument("--traffic-from", default=None, metavar="CSV",
+                    help="summarise an ncu launch list of the step (captured at --shape) into "
+                         "profiles/traffic.json; needs no GPU")
     args = ap.parse_args()
     global SHAPE
     SHAPE = tuple(args.shape)
+    if args.traffic_from:
+        traffic_from_csv(args.traffic_from, SHAPE)
+        return
     if args.profile_op:
         if args.impl != "hoszp":
             raise SystemExit("--profile-op runs the library only")
@@ -778,7 +849,7 @@ def main():
     # roofline of the dominant operator (largest share of the step)
     dom = max(ops, key=lambda o: per_op_ms[o])
     kern_of = {"compress A": "k_compress", "compress B": "k_compress", "negate": "k_meta",
-               "add_scalar": "k_meta", "mul_scalar": "k_mul_scalar", "add": "k_add",
+               "add_scalar": "k_meta", "mul_scalar": "k_mul_lanes", "add": "k_add",
                "mean": "k_mean", "var": "k_var", "decompress": "k_decompress"}
     achieved = alg[dom] / per_op_ms[dom] / 1e6
     tr = ncu_traffic(dom)
