@@ -19,8 +19,10 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, uint
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t n4 = n / 4;
   const float4* x4 = reinterpret_cast<const float4*>(x);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-    float4 v = __ldg(x4 + i);
+  // from the end of the field down, so that the compression pass, which starts
+  // at the field's beginning, finds the last part read here still in L2
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n4; j += stride) {
+    float4 v = __ldg(x4 + (n4 - 1 - j));
     float a[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int t = 0; t < 4; t++) {

@@ -20,15 +20,16 @@ cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const 
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
                             uint64_t cap, Ws ws);
 // place.cu: move staged planes behind the sign section and write the header
-// Completes a produced stream: reads the totals (nnc, R, qbound) left in the
-// workspace by the producer, checks the capacity, copies the staged planes
-// behind the sign section and writes the header and the size word.
+// Completes a produced stream: scans the per-tile word counts the producer
+// left in agg[] (totals nnc, R; qbound from totals[2]), checks the capacity,
+// copies the staged sign and plane words to their places and writes the
+// header and the size word. One launch.
 cudaError_t launch_place(const Launch& lc, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
                          int rule, uint32_t e_bits, Ws ws);
 // scan.cu: per-tile (nc, r) exclusive prefixes of a stream's rates into pre[]
 cudaError_t launch_scan(const Launch& lc, const uint8_t* c, uint64_t c_bytes,
                         unsigned long long* pre, Ws ws);
-// scan.cu: prefixes of the produced tiles' aggregates (launched by launch_place)
+// scan.cu: prefixes of the produced tiles' aggregates (batched producers)
 cudaError_t launch_scan_agg(const Launch& lc, Ws ws, uint64_t ntiles_given = 0);
 // decode.cu
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
