@@ -482,6 +482,29 @@ def batched_bench(hz, device, nfields: int, seed: int = 3, reps: int = 3):
     bA, bB = hz.Batch(ca), hz.Batch(cb)
     res = torch.empty(nfields, dtype=torch.float64, device=device)
     per = torch.empty(nfields, dtype=torch.float64, device=device)
+    offs = np.concatenate([[0], np.cumsum((sizes + 3) // 4 * 4)])
+    big = torch.empty(int(offs[-1]), dtype=torch.float32, device=device)
+    douts = [big[int(offs[i]):int(offs[i]) + int(sizes[i])] for i in range(nfields)]
+
+    # the untuned shape (super-tile pipeline, 8 warps per block group, any rate)
+    # against the autotuner's pick, which is then kept for the timings below
+    def default_index(op):
+        for i in range(bA.shapes(op)):
+            bA.set_shape(op, i)
+            c = bA.config(op)
+            if c["warps_per_group"] == 8 and c["plane_groups"] == 4 and c["stages"] == 4:
+                return i
+        raise SystemExit("no default batched shape")
+    runs = {0: lambda: bA.mean(out=res, sync=False), 1: lambda: bA.var(out=res, sync=False),
+            2: lambda: bA.decompress(douts, sync=False)}
+    untuned = {}
+    for op, fn in runs.items():
+        bA.set_shape(op, default_index(op))
+        untuned[op] = _timed(fn, reps)
+    t0 = time.perf_counter()
+    picks = bA.tune(outs=douts)
+    out["autotune"] = {"seconds": time.perf_counter() - t0, "picks": picks,
+                       "shapes_tried": {o: bA.shapes(i) for i, o in enumerate(bA.OPS)}}
     for name, bfn, sfn in (("mean", bA.mean, hz.mean), ("var", bA.var, hz.var)):
         bms = _timed(lambda: bfn(out=res, sync=False), reps)
 
@@ -490,14 +513,12 @@ def batched_bench(hz, device, nfields: int, seed: int = 3, reps: int = 3):
                 sfn(c, out=per[i:i + 1], sync=False)
         fms = _timed(fields, 1)
         bA.check(name)
-        out[name] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
+        out[name] = {"batched_ms": bms, "untuned_ms": untuned[0 if name == "mean" else 1],
+                     "per_field_ms": fms, "speedup": fms / bms,
                      "batched_orig_gbs": orig / bms / 1e6,
                      "batched_frac_of_measured_hbm": cbytes / bms / 1e6 / peak,
                      "identical_to_per_field": bool(torch.equal(res, per))}
     # decompression into one float arena
-    offs = np.concatenate([[0], np.cumsum((sizes + 3) // 4 * 4)])
-    big = torch.empty(int(offs[-1]), dtype=torch.float32, device=device)
-    douts = [big[int(offs[i]):int(offs[i]) + int(sizes[i])] for i in range(nfields)]
     bms = _timed(lambda: bA.decompress(douts, sync=False), reps)
     bA.check("decompress")
     first = big.clone()
@@ -506,7 +527,8 @@ def batched_bench(hz, device, nfields: int, seed: int = 3, reps: int = 3):
         for i, c in enumerate(ca):
             hz.decompress(c, out=douts[i], check=False)
     fms = _timed(dfields, 1)
-    out["decompress"] = {"batched_ms": bms, "per_field_ms": fms, "speedup": fms / bms,
+    out["decompress"] = {"batched_ms": bms, "untuned_ms": untuned[2], "per_field_ms": fms,
+                         "speedup": fms / bms,
                          "batched_orig_gbs": orig / bms / 1e6,
                          "batched_frac_of_measured_hbm": (cbytes + orig) / bms / 1e6 / peak,
                          "identical_to_per_field": bool(torch.equal(first, big))}

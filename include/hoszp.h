@@ -386,13 +386,32 @@ int hoszp_batch_decompress(hoszp_batch* b, float* const* d_outs, hoszp_stream_t 
 int hoszp_batch_negate(hoszp_batch* b, hoszp_stream_t stream);
 int hoszp_batch_add_scalar(hoszp_batch* b, double s, hoszp_stream_t stream);
 
-/* Autotuner: times the batched mean and variance under each candidate launch
- * shape (pipeline depth 8 or 4 stages x 1 or 2 CTAs per SM) on the plan's own
- * data, writing into d_results, and keeps the fastest for later calls.
- * Synchronizes the stream. hoszp_batch_config reports the pick (op 0: mean,
- * op 1: variance). */
-int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream);
-int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm);
+/* Autotuner: times the batched mean (op 0), variance (op 1) and, when d_outs
+ * is given, decompression (op 2) under each candidate launch shape on the
+ * plan's own data, and keeps the fastest for later calls. The candidates:
+ *   - the tile pipeline (reductions only): 8 or 4 stages x 1 or 2 CTAs per SM,
+ *     16 warps per 64-block group;
+ *   - the super-tile pipeline: 8 or 4 warps per block group (a warp takes one
+ *     64-block tile of a stage; two groups over 4 stages, or four over 8), each
+ *     with the generic decode (4 plane groups, any rate) and, where it is
+ *     exact for every field, a rate-specialised one that decodes fewer plane
+ *     groups. The plan bounds every field's rates by the bit length of twice
+ *     its header's bound on |q|; the variance then needs ceil((rmax + 1) / 8)
+ *     groups and the decompression ceil(rmax / 8); the mean is exact with 8 or
+ *     16 bit-sliced columns for any rate, so both are offered.
+ * d_results (nfields doubles) and the outputs d_outs[f] (as
+ * hoszp_batch_decompress) receive the results of the timed runs.
+ * Synchronizes the stream. hoszp_batch_config reports the pick: the stages,
+ * CTAs per SM, warps per block group and plane groups of op's shape.
+ * hoszp_batch_shapes returns how many candidates op has (or a negative
+ * status) and hoszp_batch_set_shape(b, op, i) selects candidate i without
+ * timing, which lets a test run every shape. */
+int hoszp_batch_tune(hoszp_batch* b, double* d_results, float* const* d_outs,
+                     hoszp_stream_t stream);
+int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm,
+                       int* warps_per_group, int* plane_groups);
+int hoszp_batch_shapes(const hoszp_batch* b, int op);
+int hoszp_batch_set_shape(hoszp_batch* b, int op, int index);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of operator requests over resident streams.

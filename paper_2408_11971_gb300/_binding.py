@@ -100,8 +100,11 @@ def load_library():
             "hoszp_batch_decompress": (I, [P, P, P]),
             "hoszp_batch_negate": (I, [P, P]),
             "hoszp_batch_add_scalar": (I, [P, D, P]),
-            "hoszp_batch_tune": (I, [P, P, P]),
-            "hoszp_batch_config": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "hoszp_batch_tune": (I, [P, P, P, P]),
+            "hoszp_batch_config": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                       ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "hoszp_batch_shapes": (I, [P, I]),
+            "hoszp_batch_set_shape": (I, [P, I, I]),
             "hoszp_server_create": (I, [I, ctypes.c_uint32, U64, U64, ctypes.c_uint32,
                                         ctypes.POINTER(P)]),
             "hoszp_server_destroy": (None, [P]),
@@ -674,21 +677,41 @@ class Batch:
                                          _stream_ptr(stream)), "batch_add")
         return self._produced("batch_add", outs, ptrs, caps, sizes, sync, check)
 
-    def tune(self, stream=None):
-        """Pick each reduction's launch shape from timed runs; returns the picks."""
+    OPS = ("mean", "var", "decompress")
+
+    def tune(self, outs=None, stream=None):
+        """Pick each operator's launch shape from timed runs on the plan's data
+        (decompression too when outs, one float32 tensor per field, is given);
+        returns the picks."""
         torch = _torch()
-        out = torch.empty(self.nfields, dtype=torch.float64, device=self.device)
-        _check(self._lib.hoszp_batch_tune(self.handle, _dev_ptr(out), _stream_ptr(stream)),
-               "batch_tune")
+        res = torch.empty(self.nfields, dtype=torch.float64, device=self.device)
+        ptrs = None
+        if outs is not None:
+            ptrs = torch.tensor([o.data_ptr() for o in outs], dtype=torch.int64, device=self.device)
+        _check(self._lib.hoszp_batch_tune(self.handle, _dev_ptr(res),
+                                          _dev_ptr(ptrs) if ptrs is not None else None,
+                                          _stream_ptr(stream)), "batch_tune")
         self.check("batch_tune")
-        return {"mean": self.config(0), "var": self.config(1)}
+        return {op: self.config(i) for i, op in enumerate(self.OPS)}
 
     def config(self, op: int):
-        st, cps = ctypes.c_int(0), ctypes.c_int(0)
+        st, cps, wpg, pg = (ctypes.c_int(0) for _ in range(4))
         _check(self._lib.hoszp_batch_config(self.handle, int(op), ctypes.byref(st),
-                                            ctypes.byref(cps)), "batch_config")
-        return {"stages": st.value, "ctas_per_sm": cps.value}
+                                            ctypes.byref(cps), ctypes.byref(wpg),
+                                            ctypes.byref(pg)), "batch_config")
+        return {"stages": st.value, "ctas_per_sm": cps.value, "warps_per_group": wpg.value,
+                "plane_groups": pg.value}
 
+    def shapes(self, op: int) -> int:
+        """Number of launch shapes the tuner tries for op (0 mean, 1 var, 2 decompress)."""
+        n = self._lib.hoszp_batch_shapes(self.handle, int(op))
+        if n < 0:
+            raise HoszpError(n, "batch_shapes")
+        return n
+
+    def set_shape(self, op: int, index: int):
+        """Select launch shape `index` of op without timing."""
+        _check(self._lib.hoszp_batch_set_shape(self.handle, int(op), int(index)), "batch_set_shape")
 
 
 def batch_compress(xs, eb, mode: str = "rel", outs=None, stream=None, ctx=None,

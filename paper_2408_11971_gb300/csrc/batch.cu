@@ -230,12 +230,12 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_bmoments(
 // consumer warps run the single-stream mean (bit-sliced column sums) or
 // variance (octet decode) on their tile and flush a field's sums when their
 // next stage belongs to another field.
-constexpr int BS_STAGES = 4;
+// Launch shapes: NT tiles per stage = warps per block group (a warp takes a
+// tile), GROUPS groups taking the stages in turn, STAGES stages in the ring,
+// GMAX plane groups decoded (4: any rate; 2: rates below 16; 1: below 8).
 constexpr uint32_t BS_RING = 22528;  // plane-ring words (176 KB)
-constexpr int BS_GW = STILES;        // warps per group: one per tile of a stage
-constexpr int BS_GROUPS = 2;
-constexpr int BS_NCW = BS_GW * BS_GROUPS;
-constexpr int BS_THREADS = (BS_NCW + 1) * 32;
+template <int NT, int GROUPS>
+constexpr int bs_threads() { return (NT * GROUPS + 1) * 32; }
 
 struct BStageMeta {
   uint32_t f, nt;   // field, tiles in the stage (0: end of the walk)
@@ -244,6 +244,7 @@ struct BStageMeta {
 
 // Byte ranges of local tiles [t0, t0 + nt) of a stream, from its prefixes at
 // t0 (pv0) and at t0 + nt (pv1).
+template <int NT>
 __device__ __forceinline__ SSpan tile_range_span(const Info& h, uint64_t t0, uint32_t nt,
                                                  ulonglong2 pv0, ulonglong2 pv1) {
   SSpan sp;
@@ -257,8 +258,8 @@ __device__ __forceinline__ SSpan tile_range_span(const Info& h, uint64_t t0, uin
   sp.pa16 = pa & ~15ull;
   sp.sbytes = (pv1.x > pv0.x) ? (unsigned)(align16(se) - sp.sa16) : 0u;
   sp.pbytes = (pv1.y > pv0.y) ? (unsigned)(align16(pe) - sp.pa16) : 0u;
-  if (sp.pbytes > 8u * STILE_PLANE_WORDS_MAX) sp.pbytes = 8u * STILE_PLANE_WORDS_MAX;
-  if (sp.sbytes > 8u * (STB + 2)) sp.sbytes = 8u * (STB + 2);
+  if (sp.pbytes > 8u * SuperChecks<NT>::kPlaneWordsMax) sp.pbytes = 8u * SuperChecks<NT>::kPlaneWordsMax;
+  if (sp.sbytes > 8u * (NT * TILE + 2)) sp.sbytes = 8u * (NT * TILE + 2);
   sp.sbase = (uint32_t)((sa - sp.sa16) >> 3);
   sp.pbase = (uint32_t)((pa - sp.pa16) >> 3);
   return sp;
@@ -295,13 +296,15 @@ __device__ __forceinline__ void bflush(const BField* F, uint32_t f, __int128 s1,
 
 // MODE 0: mean, 1: variance (per-field exact sums, finished by the warp that
 // completes a field), 2: decompression into each field's output outs[f].
-template <int MODE>
-__global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
+template <int MODE, int NT, int GROUPS, int STAGES, int GMAX>
+__global__ void __launch_bounds__(bs_threads<NT, GROUPS>(), 1) k_bsuper(
     const BField* __restrict__ F, uint32_t nf, uint64_t total_tiles,
     const unsigned long long* __restrict__ pre, unsigned long long* acc, unsigned int* done,
     double* results, int* status, float* const* __restrict__ outs) {
+  constexpr int BS_STAGES = STAGES, BS_GW = NT, BS_GROUPS = GROUPS, BS_NCW = NT * GROUPS;
+  using St = SStageT<NT>;
   extern __shared__ __align__(16) uint8_t dyn[];
-  SStage* stages = reinterpret_cast<SStage*>(dyn);
+  St* stages = reinterpret_cast<St*>(dyn);
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + BS_STAGES);
   __shared__ uint64_t full[BS_STAGES], empty[BS_STAGES];
   __shared__ BStageMeta s_meta[BS_STAGES];
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
       }
       wk.to_tile(F, nf, t);
       const uint64_t lt = t - wk.tile0;
-      const uint32_t nt = (uint32_t)umin64(umin64(STILES, wk.ntiles - lt), t_end - t);
+      const uint32_t nt = (uint32_t)umin64(umin64(NT, wk.ntiles - lt), t_end - t);
       // the stream's prefixes at the stage's tile boundaries (lanes 0 .. nt)
       ulonglong2 pv = make_ulonglong2(0, 0);
       if (lane <= (int)nt)
@@ -357,11 +360,11 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
                                              __shfl_sync(0xffffffffu, pv.y, 0));
       const ulonglong2 pv1 = make_ulonglong2(__shfl_sync(0xffffffffu, pv.x, nt),
                                              __shfl_sync(0xffffffffu, pv.y, nt));
-      const SSpan sp = tile_range_span(wk.h, lt, nt, pv0, pv1);
+      const SSpan sp = tile_range_span<NT>(wk.h, lt, nt, pv0, pv1);
       const uint32_t p0 = pr.reserve(k, sp.plane_words(), k_rel, release_one);
       if (dead) break;
       const uint32_t at = pr.commit(k, p0, sp.plane_words());
-      SStage* sg = &stages[sk];
+      St* sg = &stages[sk];
       if (lane < (int)nt) {
         sg->tnc[lane] = (uint32_t)(pv.x - pv0.x);
         sg->tr[lane] = (uint32_t)(pv.y - pv0.y);
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
   } else if (w < BS_NCW) {
     const int grp = w / BS_GW, ti = w % BS_GW;
     const lanes::Shifts K = lanes::make_shifts(nf != 0 ? 1u : 0u);
-    MeanAcc A;
+    MeanAccT<(GMAX <= 1 ? 8 : 16)> A;
     A.init();
     long long v1 = 0;
     U128 v2 = {0, 0};
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
         cur = meta.f;
       }
       if (ti < (int)meta.nt) {  // warp-uniform
-        const SStage& sg = stages[sk];
+        const St& sg = stages[sk];
         const Info& h = F[cur].h;
         const uint64_t tile = meta.t0 + ti;
         const uint64_t ntiles = F[cur].ntiles;
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
             br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
             const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
             int d[8], q[8];
-            octet_deltas(br, kmax, j, S, d);
+            octet_deltas<GMAX>(br, kmax, j, S, d);
             octet_values(br, d, j, q);
             float v[8];
             if (small) {  // uniform over the stream: no per-value select
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
             mean_block((int)r, len, O, sw, reinterpret_cast<const uint2*>(pls + (ex & 0xffffu)), A);
           }
         } else {
-          var_tile(sg, ring, ti, tr, tile, ntiles, lastlen, h.qbound < (1u << 13), K, v1, v2);
+          var_tile<GMAX>(sg, ring, ti, tr, tile, ntiles, lastlen, h.qbound < (1u << 13), K, v1, v2);
         }
         cnt++;
       }
@@ -493,16 +496,37 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsuper(
   }
 }
 
+template <int MODE, int NT, int GROUPS, int STAGES, int GMAX>
+cudaError_t launch_bsuper_shape(int num_sms, cudaStream_t s, const BField* F, uint32_t nf,
+                                uint64_t total_tiles, const unsigned long long* pre,
+                                unsigned long long* acc, unsigned int* done, double* results,
+                                int* status, float* const* outs) {
+  constexpr int threads = bs_threads<NT, GROUPS>();
+  auto kern = k_bsuper<MODE, NT, GROUPS, STAGES, GMAX>;
+  const size_t smem = STAGES * sizeof(SStageT<NT>) + BS_RING * sizeof(uint64_t);
+  smem_attr<k_bsuper<MODE, NT, GROUPS, STAGES, GMAX>>(smem);
+  kern<<<persistent_grid(kern, threads, num_sms, smem), threads, smem, s>>>(
+      F, nf, total_tiles, pre, acc, done, results, status, outs);
+  return cudaGetLastError();
+}
+
+// The super-tile launch of one shape: wpg warps per block group (8: two
+// groups of 8 over 4 stages of 8 tiles; 4: four groups of 4 over 8 stages of
+// 4 tiles) and gmax plane groups (4, 2 or 1).
 template <int MODE>
 cudaError_t launch_bsuper(int num_sms, cudaStream_t s, const BField* F, uint32_t nf,
                           uint64_t total_tiles, const unsigned long long* pre,
                           unsigned long long* acc, unsigned int* done, double* results,
-                          int* status, float* const* outs = nullptr) {
-  const size_t smem = BS_STAGES * sizeof(SStage) + BS_RING * sizeof(uint64_t);
-  smem_attr<k_bsuper<MODE>>(smem);
-  k_bsuper<MODE><<<persistent_grid(k_bsuper<MODE>, BS_THREADS, num_sms, smem), BS_THREADS, smem,
-                   s>>>(F, nf, total_tiles, pre, acc, done, results, status, outs);
-  return cudaGetLastError();
+                          int* status, float* const* outs = nullptr, int wpg = 8,
+                          int gmax = 4) {
+#define HZ_BS(W, GR, ST, GM)                                                                  \
+  if (wpg == W && gmax == GM)                                                                 \
+    return launch_bsuper_shape<MODE, W, GR, ST, GM>(num_sms, s, F, nf, total_tiles, pre, acc, \
+                                                    done, results, status, outs);
+  HZ_BS(8, 2, 4, 4) HZ_BS(8, 2, 4, 2) HZ_BS(8, 2, 4, 1)
+  HZ_BS(4, 4, 8, 4) HZ_BS(4, 4, 8, 2) HZ_BS(4, 4, 8, 1)
+#undef HZ_BS
+  return cudaErrorInvalidValue;
 }
 
 template <bool VAR, int STAGES>
@@ -609,9 +633,9 @@ int run_moments(hoszp_batch* b, bool var, const BatchCfg& c, double* d_results,
   cudaError_t e;
   if (c.variant == 2)
     e = var ? launch_bsuper<1>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
-                               b->d_acc, b->d_done, d_results, b->status)
+                               b->d_acc, b->d_done, d_results, b->status, nullptr, c.wpg, c.gmax)
             : launch_bsuper<0>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
-                               b->d_acc, b->d_done, d_results, b->status);
+                               b->d_acc, b->d_done, d_results, b->status, nullptr, c.wpg, c.gmax);
   else if (var)
     e = c.variant == 0 ? launch_bmoments<true, 8>(grid, s, b->d_fields, b->nf, b->total_tiles,
                                                    b->d_pre, b->d_acc, b->d_done, d_results,
@@ -627,6 +651,33 @@ int run_moments(hoszp_batch* b, bool var, const BatchCfg& c, double* d_results,
                                                     b->d_pre, b->d_acc, b->d_done, d_results,
                                                     b->status);
   return rc_of(e);
+}
+
+int run_decompress(hoszp_batch* b, const BatchCfg& c, float* const* d_outs, cudaStream_t s) {
+  return rc_of(launch_bsuper<2>(b->num_sms, s, b->d_fields, b->nf, b->total_tiles, b->d_pre,
+                                b->d_acc, b->d_done, nullptr, b->status, d_outs, c.wpg, c.gmax));
+}
+
+// The autotuner's candidates for op (0 mean, 1 variance, 2 decompression):
+// pipeline depth x CTAs per SM of the tile pipeline (reductions only), and
+// warps per block group x plane groups of the super-tile pipeline. The
+// rate-specialised shapes decode fewer plane groups and are offered only
+// where they are exact for every field of the plan: the variance needs
+// ceil((rmax + 1) / 8) groups (the rates' planes and the sign), the
+// decompression ceil(rmax / 8); the mean is exact with any column count
+// (planes above the columns go through popcounts), so its 8-column shape is
+// always offered.
+int candidates(const hoszp_batch* b, int op, BatchCfg out[12]) {
+  int n = 0;
+  if (op < 2)
+    for (int v = 0; v < 2; v++)
+      for (int cps = 1; cps <= 2; cps++) out[n++] = BatchCfg{v, cps, 8, 4};
+  int gm[2] = {4, 0}, ng = 1;
+  const int need = op == 0 ? 1 : op == 1 ? (b->rmax + 8) >> 3 : std::max(1, (b->rmax + 7) >> 3);
+  if (need == 1 || need == 2) gm[ng++] = need;
+  for (int w : {8, 4})
+    for (int i = 0; i < ng; i++) out[n++] = BatchCfg{2, 1, w, gm[i]};
+  return n;
 }
 
 }  // namespace
@@ -691,7 +742,13 @@ int hoszp_batch_create(hoszp_ctx* ctx, uint32_t nfields, const void* const* d_st
   b->total_tiles = tiles;
   b->total_ch[0] = ch[0];
   b->total_ch[1] = ch[1];
-  b->cfg[0] = b->cfg[1] = BatchCfg{2, 1};
+  b->cfg[0] = b->cfg[1] = b->cfg[2] = BatchCfg{2, 1, 8, 4};
+  b->rmax = 0;
+  for (uint32_t f = 0; f < nfields; f++) {  // |delta| <= 2 max|q|: its bit length bounds the rate
+    const uint64_t d = 2ull * F[f].h.qbound;
+    const int bits = d ? 64 - __builtin_clzll(d) : 0;
+    b->rmax = std::max(b->rmax, std::min(bits, (int)MAX_RATE));
+  }
   const size_t fbytes = (nfields * sizeof(BField) + 255) / 256 * 256;
   const size_t pbytes = (pre_words * 8 + 255) / 256 * 256;
   const size_t abytes = (nfields * 32 + 255) / 256 * 256;
@@ -803,9 +860,7 @@ int hoszp_batch_var(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
 int hoszp_batch_decompress(hoszp_batch* b, float* const* d_outs, hoszp_stream_t stream) {
   if (!b || !d_outs || ((uintptr_t)d_outs & 7u)) return HOSZP_ERR_ARG;
   DeviceGuard guard(b->device);
-  return rc_of(launch_bsuper<2>(b->num_sms, (cudaStream_t)stream, b->d_fields, b->nf,
-                                b->total_tiles, b->d_pre, b->d_acc, b->d_done, nullptr, b->status,
-                                d_outs));
+  return run_decompress(b, b->cfg[2], d_outs, (cudaStream_t)stream);
 }
 
 int hoszp_batch_negate(hoszp_batch* b, hoszp_stream_t stream) {
@@ -827,22 +882,30 @@ int hoszp_batch_add_scalar(hoszp_batch* b, double s, hoszp_stream_t stream) {
   return rc_of(cudaGetLastError());
 }
 
-int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
-  if (!b || !d_results) return HOSZP_ERR_ARG;
+int hoszp_batch_tune(hoszp_batch* b, double* d_results, float* const* d_outs,
+                     hoszp_stream_t stream) {
+  if (!b || !d_results || ((uintptr_t)d_results & 7u) || ((uintptr_t)d_outs & 7u))
+    return HOSZP_ERR_ARG;
   DeviceGuard guard(b->device);
   const cudaStream_t s = (cudaStream_t)stream;
-  const BatchCfg cands[5] = {{2, 1}, {0, 2}, {0, 1}, {1, 2}, {1, 1}};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return rc_of(cudaErrorUnknown);
   int rc = HOSZP_OK;
-  for (int op = 0; op < 2 && !rc; op++) {
+  for (int op = 0; op < 3 && !rc; op++) {
+    if (op == 2 && !d_outs) break;  // decompression is tuned when outputs are given
+    BatchCfg cands[12];
+    const int nc = candidates(b, op, cands);
     float best = 1e30f;
     BatchCfg pick = b->cfg[op];
-    for (const BatchCfg& c : cands) {
-      if ((rc = run_moments(b, op == 1, c, d_results, s))) break;  // warm-up
+    for (int i = 0; i < nc && !rc; i++) {
+      const BatchCfg& c = cands[i];
+      auto run = [&]() {
+        return op == 2 ? run_decompress(b, c, d_outs, s) : run_moments(b, op == 1, c, d_results, s);
+      };
+      if ((rc = run())) break;  // warm-up
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 3 && !rc; r++) rc = run_moments(b, op == 1, c, d_results, s);
+      for (int r = 0; r < 3 && !rc; r++) rc = run();
       cudaEventRecord(e1, s);
       if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
         rc = rc ? rc : HOSZP_ERR_CUDA;
@@ -862,10 +925,30 @@ int hoszp_batch_tune(hoszp_batch* b, double* d_results, hoszp_stream_t stream) {
   return rc;
 }
 
-int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm) {
-  if (!b || op < 0 || op > 1) return HOSZP_ERR_ARG;
-  if (stages) *stages = b->cfg[op].variant == 0 ? 8 : b->cfg[op].variant == 1 ? 4 : BS_STAGES;
-  if (ctas_per_sm) *ctas_per_sm = b->cfg[op].cps;
+int hoszp_batch_shapes(const hoszp_batch* b, int op) {
+  if (!b || op < 0 || op > 2) return HOSZP_ERR_ARG;
+  BatchCfg c[12];
+  return candidates(b, op, c);
+}
+
+int hoszp_batch_set_shape(hoszp_batch* b, int op, int index) {
+  if (!b || op < 0 || op > 2) return HOSZP_ERR_ARG;
+  BatchCfg c[12];
+  const int n = candidates(b, op, c);
+  if (index < 0 || index >= n) return HOSZP_ERR_ARG;
+  b->cfg[op] = c[index];
+  return HOSZP_OK;
+}
+
+int hoszp_batch_config(const hoszp_batch* b, int op, int* stages, int* ctas_per_sm,
+                       int* warps_per_group, int* plane_groups) {
+  if (!b || op < 0 || op > 2) return HOSZP_ERR_ARG;
+  const BatchCfg& c = b->cfg[op];
+  if (stages) *stages = c.variant == 0 ? 8 : c.variant == 1 ? 4 : (c.wpg == 8 ? 4 : 8);
+  if (ctas_per_sm) *ctas_per_sm = c.cps;
+  // the tile pipeline's 16 compute warps each take a quarter of a tile's blocks
+  if (warps_per_group) *warps_per_group = c.variant == 2 ? c.wpg : 16;
+  if (plane_groups) *plane_groups = c.variant == 2 ? c.gmax : 4;
   return HOSZP_OK;
 }
 

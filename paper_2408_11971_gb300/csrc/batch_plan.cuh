@@ -46,10 +46,12 @@ struct BOut {
 
 }  // namespace hz
 
-// Autotuned launch shape of one reduction: pipeline depth (variant) and CTAs per SM.
+// Autotuned launch shape of one batched operator.
 struct BatchCfg {
   int variant;  // 0: tile pipeline, 8 stages; 1: tile pipeline, 4 stages; 2: super-tile pipeline
-  int cps;      // CTAs per SM (1 or 2; the super-tile pipeline takes one)
+  int cps;      // CTAs per SM (the tile pipeline: 1 or 2; the super-tile pipeline takes one)
+  int wpg;      // super-tile pipeline: warps per block group (8 or 4)
+  int gmax;     // super-tile pipeline: plane groups decoded (4: any rate; 2 or 1: rate-specialised)
 };
 
 struct hoszp_batch {
@@ -63,7 +65,8 @@ struct hoszp_batch {
   unsigned long long* d_acc;
   unsigned int* d_done;
   int* status;  // the plan's own status word (first device error of its operators)
-  BatchCfg cfg[2];  // mean, variance
+  BatchCfg cfg[3];  // mean, variance, decompression
+  int rmax;         // bound on every field's rates, from the headers' bounds on |q|
   // producing operators (bproduce.cu): per-field input word prefixes
   // (fpre[2f] = non-constant blocks, fpre[2f + 1] = plane words of the fields
   // before f) and the per-field output table

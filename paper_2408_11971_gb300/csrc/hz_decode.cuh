@@ -17,7 +17,10 @@ struct BlockRef {
 
 // The planes of a block, transposed: group k (planes 8k..8k+7) becomes 8
 // bytes (lo[k], hi[k]) whose byte t holds bits 8k..8k+7 of |delta| at
-// position 8j+t. kmax (warp-uniform) >= ceil(rate / 8).
+// position 8j+t. kmax (warp-uniform) >= ceil(rate / 8). KMAX: the most
+// groups the calling kernel decodes (4 covers every rate; groups at and above
+// KMAX read as zero).
+template <int KMAX = 4>
 __device__ __forceinline__ void decode_groups(const uint64_t* planes, int r, int kmax,
                                               const OctetSel& S, int j, uint32_t lo[4],
                                               uint32_t hi[4]) {
@@ -25,13 +28,13 @@ __device__ __forceinline__ void decode_groups(const uint64_t* planes, int r, int
 #pragma unroll
   for (int k = 0; k < 4; k++) {
     const int p = 8 * k + j;
-    w[k] = (k < kmax && p < r) ? planes[p] : 0ull;
+    w[k] = (k < KMAX && k < kmax && p < r) ? planes[p] : 0ull;
   }
 #pragma unroll
   for (int k = 0; k < 4; k++) {
     lo[k] = (uint32_t)w[k];
     hi[k] = (uint32_t)(w[k] >> 32);
-    if (k < kmax) {
+    if (k < KMAX && k < kmax) {
       byte_transpose8(lo[k], hi[k], S);
       tr8x8_d(lo[k], hi[k]);
     }
@@ -39,15 +42,16 @@ __device__ __forceinline__ void decode_groups(const uint64_t* planes, int r, int
 }
 
 // Magnitudes of the 8 positions from the transposed groups.
+template <int KMAX = 4>
 __device__ __forceinline__ void mags_from_groups(const uint32_t lo[4], const uint32_t hi[4],
                                                  int kmax, uint32_t m[8]) {
-  if (kmax <= 1) {
+  if (KMAX == 1 || kmax <= 1) {
 #pragma unroll
     for (int t = 0; t < 4; t++) {
       m[t] = __byte_perm(lo[0], 0u, 0x4440u + t);
       m[t + 4] = __byte_perm(hi[0], 0u, 0x4440u + t);
     }
-  } else if (kmax == 2) {  // two bytes per value: interleave the groups
+  } else if (KMAX == 2 || kmax == 2) {  // two bytes per value: interleave the groups
     uint32_t x;
     x = __byte_perm(lo[0], lo[1], 0x5140u);
     m[0] = x & 0xffffu;
@@ -78,11 +82,12 @@ __device__ __forceinline__ void mags_from_groups(const uint32_t lo[4], const uin
 
 // Signed deltas of lane j's positions; position 0 and positions past the
 // block's end are 0. The sign is applied as a multiply by +-1 (FMA pipe).
+template <int KMAX = 4>
 __device__ __forceinline__ void octet_deltas(const BlockRef& br, int kmax, int j,
                                              const OctetSel& S, int d[8]) {
   uint32_t lo[4], hi[4], m[8];
-  decode_groups(br.planes, br.rate, kmax, S, j, lo, hi);
-  mags_from_groups(lo, hi, kmax, m);
+  decode_groups<KMAX>(br.planes, br.rate, kmax, S, j, lo, hi);
+  mags_from_groups<KMAX>(lo, hi, kmax, m);
 #pragma unroll
   for (int t = 0; t < 8; t++) {
     const int k = 1 - 2 * (int)((br.sign_byte >> t) & 1u);

@@ -148,12 +148,16 @@ HZL_HD void twos_planes(const uint32_t* pl, int r, uint32_t s, uint32_t t[32]) {
   for (int p = R; p < W; p++) t[p] = f;
 }
 
-// Dispatch of twos_planes on the warp-uniform R (0 .. 31).
+// Dispatch of twos_planes on the warp-uniform R (0 .. MAXR). A kernel built
+// for streams whose rates stay at or below MAXR instantiates only those cases;
+// a larger R (a header that understates its values) decodes as MAXR.
+template <int MAXR = 31>
 HZL_HD void twos_planes_any(int R, const uint32_t* pl, int r, uint32_t s, uint32_t t[32]) {
   switch (R) {
-#define HZL_CASE(K) \
-  case K:           \
-    twos_planes<K>(pl, r, s, t); \
+#define HZL_CASE(K)                              \
+  case K:                                        \
+    if constexpr (K <= MAXR) twos_planes<K>(pl, r, s, t); \
+    else twos_planes<MAXR>(pl, r, s, t);         \
     break;
     HZL_CASE(0) HZL_CASE(1) HZL_CASE(2) HZL_CASE(3) HZL_CASE(4) HZL_CASE(5) HZL_CASE(6)
     HZL_CASE(7) HZL_CASE(8) HZL_CASE(9) HZL_CASE(10) HZL_CASE(11) HZL_CASE(12) HZL_CASE(13)
@@ -161,7 +165,7 @@ HZL_HD void twos_planes_any(int R, const uint32_t* pl, int r, uint32_t s, uint32
     HZL_CASE(21) HZL_CASE(22) HZL_CASE(23) HZL_CASE(24) HZL_CASE(25) HZL_CASE(26) HZL_CASE(27)
     HZL_CASE(28) HZL_CASE(29) HZL_CASE(30)
     default:
-      twos_planes<31>(pl, r, s, t);
+      twos_planes<MAXR>(pl, r, s, t);
       break;
 #undef HZL_CASE
   }

@@ -91,9 +91,13 @@ __device__ __forceinline__ long long wsum64(uint32_t lo, uint32_t hi) {
   return (long long)wsum32(lo, 64) + wsum32(hi, 32);
 }
 
-struct MeanAcc {
-  static constexpr int RF = 16;  // planes added through the columns
-  uint32_t a0[RF], a1[RF];       // columns of positions 0..31 and 32..63
+// RF: planes added through the columns (16 covers every block of a stream
+// whose rates stay below 16; a plan that knows its rates stay below 8 may take
+// 8, which halves the column registers).
+template <int RF_ = 16>
+struct MeanAccT {
+  static constexpr int RF = RF_;
+  uint32_t a0[RF], a1[RF];  // columns of positions 0..31 and 32..63
   __int128 s1;
   __device__ __forceinline__ void init() {
 #pragma unroll
@@ -111,12 +115,14 @@ struct MeanAcc {
     s1 += t;
   }
 };
+using MeanAcc = MeanAccT<16>;
 
 // Ripple-carry add of the first rl (<= R) planes of a block into columns
 // 0..R-1; returns the carry words leaving column R-1.
-template <int R>
-__device__ __forceinline__ void mean_cols(MeanAcc& A, const uint2* pl, int rl, uint32_t s0,
+template <int R, class Acc>
+__device__ __forceinline__ void mean_cols(Acc& A, const uint2* pl, int rl, uint32_t s0,
                                           uint32_t s1, uint32_t& c0, uint32_t& c1) {
+  static_assert(R <= Acc::RF, "columns 0 .. R-1 exist");
 #pragma unroll
   for (int k = 0; k < R; k++) {
     uint32_t u0 = 0u, u1 = 0u;
@@ -137,19 +143,21 @@ __device__ __forceinline__ void mean_cols(MeanAcc& A, const uint2* pl, int rl, u
 // length len (64, fewer for the stream's last block, 0 for no block), outlier
 // O, sign word sg and plane words pl[0 .. r-1]. All 32 lanes of the warp call
 // this together, each with its own block.
+template <class Acc>
 __device__ __forceinline__ void mean_block(int r, int len, int O, uint64_t sg, const uint2* pl,
-                                           MeanAcc& A) {
+                                           Acc& A) {
+  constexpr int RF = Acc::RF;
   const bool full = (len == L);
-  const int rl = full ? min(r, MeanAcc::RF) : 0;
+  const int rl = full ? min(r, RF) : 0;
   const int rw = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
   const uint32_t sl = (uint32_t)sg, sh = (uint32_t)(sg >> 32);
   long long e = (long long)len * O;
   if (rw > 0) {
     uint32_t c0 = 0u, c1 = 0u;
     switch (rw) {
-#define HZ_MEAN_CASE(R) \
-  case R:               \
-    mean_cols<R>(A, pl, rl, sl, sh, c0, c1); \
+#define HZ_MEAN_CASE(R)                                                  \
+  case R:                                                                \
+    if constexpr (R <= RF) mean_cols<R>(A, pl, rl, sl, sh, c0, c1);      \
     break;
       HZ_MEAN_CASE(1) HZ_MEAN_CASE(2) HZ_MEAN_CASE(3) HZ_MEAN_CASE(4)
       HZ_MEAN_CASE(5) HZ_MEAN_CASE(6) HZ_MEAN_CASE(7) HZ_MEAN_CASE(8)
@@ -163,7 +171,7 @@ __device__ __forceinline__ void mean_block(int r, int len, int O, uint64_t sg, c
   }
   if (r > 0 && full) {
     e -= (long long)((1ull << r) - 1ull) * wsum64(sl, sh);
-    for (int p = MeanAcc::RF; p < r; p++) {
+    for (int p = RF; p < r; p++) {
       const uint2 x = pl[p];
       e += wsum64((x.x & 0xfffffffeu) ^ sl, x.y ^ sh) << p;
     }
@@ -188,11 +196,20 @@ __device__ __forceinline__ void sum_partials_warp(const Partial* P, unsigned int
   const int lane = threadIdx.x & 31;
   __int128 a = 0;
   U128 b = {0, 0};
-  for (unsigned int u = lane; u < G; u += 32) {
-    const Partial p = P[u];
-    a += ((__int128)p.s1_hi << 64) | (unsigned long long)p.s1_lo;
-    const U128 v = {p.s2_lo, p.s2_hi};
-    add_u128(b, v);
+  for (unsigned int u0 = lane; u0 < G; u0 += 32 * 4) {  // four partials in flight
+    Partial p[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const unsigned int u = u0 + 32 * i;
+      if (u < G) p[i] = P[u];
+      else p[i] = Partial{0, 0, 0ull, 0ull};
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      a += ((__int128)p[i].s1_hi << 64) | (unsigned long long)p[i].s1_lo;
+      const U128 v = {p[i].s2_lo, p[i].s2_hi};
+      add_u128(b, v);
+    }
   }
   S1 = warp_sum_i128(a);
   S2 = warp_sum_u128(b);

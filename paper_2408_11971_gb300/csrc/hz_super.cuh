@@ -180,17 +180,21 @@ __device__ __forceinline__ SRange range_sums_n(const uint8_t* const* c, const In
     }
   }
   __syncthreads();
-  if (tid < NS) {
-    unsigned long long a = 0, b = 0;
-    for (int w = 0; w < nw; w++) {
-      a += s_tot[2 * tid][w];
-      b += s_tot[2 * tid + 1][w];
+  if (wid < NS) {  // warp k adds up stream k's per-warp totals
+    unsigned long long a = (lane < nw) ? s_tot[2 * wid][lane] : 0ull;
+    unsigned long long b = (lane < nw) ? s_tot[2 * wid + 1][lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    CtaAgg* g = ws.cta_agg + (uint64_t)NS * rg.v + tid;
-    g->nc = a;
-    g->r = b;
-    __threadfence();
-    st_release(&g->flag, (epoch << 1) | 1ull);
+    if (lane == 0) {
+      CtaAgg* g = ws.cta_agg + (uint64_t)NS * rg.v + wid;
+      g->nc = a;
+      g->r = b;
+      __threadfence();
+      st_release(&g->flag, (epoch << 1) | 1ull);
+    }
   }
   return rg;
 }

@@ -12,19 +12,24 @@ namespace hz {
 
 // half_sums of hz_lanes.cuh for the warp's widest rate Rw (G = (Rw + 8) / 8
 // groups of 8 planes); tails and wide values take the 64-bit sums.
+// The two's-complement planes of a half span G = (Rw + 8) / 8 groups of 8
+// (the rate's planes and the sign). GMAX: the most groups the calling kernel
+// was built for (4 covers every rate; a plan whose rates stay below 8 GMAX
+// may take fewer, which drops the wider cases and their registers).
+template <int GMAX = 4>
 __device__ __forceinline__ lanes::HalfSums half_sums_any(int Rw, bool full, bool narrow,
                                                          const uint32_t t[32], int nval,
                                                          bool zero0, const lanes::Shifts& K) {
-  const int G = (Rw + 8) >> 3;
+  const int G = min((Rw + 8) >> 3, GMAX);
 #define HZ_HS(GG)                                                          \
-  if (G == GG) {                                                           \
+  if (GG == GMAX || G == GG) {                                             \
     if (!full) return lanes::half_sums<GG, false, true>(t, nval, zero0, K);   \
     if (narrow) return lanes::half_sums<GG, true, false>(t, nval, zero0, K);  \
     return lanes::half_sums<GG, true, true>(t, nval, zero0, K);               \
   }
   HZ_HS(1)
-  HZ_HS(2)
-  HZ_HS(3)
+  if constexpr (GMAX >= 2) HZ_HS(2)
+  if constexpr (GMAX >= 3) HZ_HS(3)
 #undef HZ_HS
   if (!full) return lanes::half_sums<4, false, true>(t, nval, zero0, K);
   if (narrow) return lanes::half_sums<4, true, false>(t, nval, zero0, K);
@@ -35,8 +40,8 @@ __device__ __forceinline__ lanes::HalfSums half_sums_any(int Rw, bool full, bool
 // `ntiles` tiles whose last block holds `lastlen` values): adds this lane's
 // share of S1 and S2. The warp takes 16 blocks per step; lane 2m + hf holds
 // half hf of block 16 it + m. qsmall: the stream's header bounds every |q|
-// below 2^13.
-template <class St>
+// below 2^13. GMAX: as half_sums_any (rates below 8 GMAX decode exactly).
+template <int GMAX = 4, class St>
 __device__ __forceinline__ void var_tile(const St& sg, const uint64_t* ring, int ti,
                                          const TileRates& tr, uint64_t tile, uint64_t ntiles,
                                          int lastlen, bool qsmall, const lanes::Shifts& K,
@@ -57,10 +62,10 @@ __device__ __forceinline__ void var_tile(const St& sg, const uint64_t* ring, int
     const int Rw = (int)__reduce_max_sync(0xffffffffu, r);
     const bool fullblk = __all_sync(0xffffffffu, len == L);
     uint32_t t[32];
-    lanes::twos_planes_any(Rw, pls + 2 * (ex & 0xffffu) + hf, (int)r, sw, t);
+    lanes::twos_planes_any<8 * GMAX - 1>(Rw, pls + 2 * (ex & 0xffffu) + hf, (int)r, sw, t);
     // narrow sums of p^2 need every |p_i| < 2^14: |q| < 2^13, or 32 deltas below 2^8
     const bool narrow = fullblk && (qsmall || Rw <= 8);
-    const lanes::HalfSums hs = half_sums_any(Rw, fullblk, narrow, t, nval, hf == 0, K);
+    const lanes::HalfSums hs = half_sums_any<GMAX>(Rw, fullblk, narrow, t, nval, hf == 0, K);
     const int tot0 = __shfl_xor_sync(0xffffffffu, hs.tot, 1);
     const long long base = O + (hf ? (long long)tot0 : 0ll);
     s1 += (long long)nval * base + hs.sp;

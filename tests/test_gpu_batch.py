@@ -150,15 +150,72 @@ def test_batch_graph_capture(hz, fields):
         assert np.array_equal(host(work[f]), ocs[f]), f
 
 
+def _run_op(hz, b, op, cs):
+    """Runs op (0 mean, 1 var, 2 decompress) on plan b; True when every field
+    equals the single-stream operator bit for bit."""
+    if op == 0:
+        got = host(b.mean())
+        return all(got[f] == hz.mean(c) for f, c in enumerate(cs))
+    if op == 1:
+        got = host(b.var())
+        return all(got[f] == hz.var(c) for f, c in enumerate(cs))
+    outs = b.decompress()
+    return all(np.array_equal(host(o), host(hz.decompress(c))) for o, c in zip(outs, cs))
+
+
+def low_rate_fields(rel):
+    """GRFs of uneven sizes (1-D, 2-D, 3-D, ragged tails) at one coarse relative
+    bound, so every rate stays small and the rate-specialised shapes exist."""
+    shapes = [(5000,), (70_001,), (64,), (999,), (300, 211), (37, 41, 23), (123_457,)]
+    return [datagen.grf(sh, seed=300 + i).reshape(-1) for i, sh in enumerate(shapes)]
+
+
 def test_batch_autotune(hz, fields):
     _, _, cs, ocs = fields
     b = hz.Batch([c.clone() for c in cs])
-    picks = b.tune()
+    outs = [torch.empty(hz.header(c)["n"], dtype=torch.float32, device="cuda") for c in cs]
+    picks = b.tune(outs=outs)
     for op in ("mean", "var"):
-        assert picks[op]["stages"] in (4, 8) and picks[op]["ctas_per_sm"] in (1, 2)
+        p = picks[op]
+        assert p["stages"] in (4, 8) and p["ctas_per_sm"] in (1, 2), p
+        assert p["warps_per_group"] in (4, 8, 16) and p["plane_groups"] in (1, 2, 4), p
+    assert picks["decompress"]["warps_per_group"] in (4, 8), picks
     m = host(b.mean())
     for f, oc in enumerate(ocs):
         assert close(m[f], O.mean(oc)), f
+    for f, oc in enumerate(ocs):  # the tuner's own decompression runs wrote the outputs
+        assert np.array_equal(host(outs[f]), O.decompress(oc)), f
+
+
+def test_batch_every_shape_uneven(hz, fields):
+    """Every launch shape the tuner may pick gives the single-stream results."""
+    _, _, cs, _ = fields
+    b = hz.Batch([c.clone() for c in cs])
+    for op in range(3):
+        n = b.shapes(op)
+        assert n >= (6 if op < 2 else 2), (op, n)
+        for i in range(n):
+            b.set_shape(op, i)
+            assert _run_op(hz, b, op, cs), (op, i, b.config(op))
+    with pytest.raises(hz.HoszpError):
+        b.set_shape(0, b.shapes(0))
+
+
+@pytest.mark.parametrize("rel", [1e-2, 1e-3])
+def test_batch_every_shape_rate_specialised(hz, rel):
+    """A plan whose header bounds keep every rate small offers rate-specialised
+    decodes (fewer plane groups) for variance and decompression; each shape
+    gives the single-stream results bit for bit."""
+    xs = low_rate_fields(rel)
+    cs = [hz.compress(dev(x), eb=rel, mode="rel") for x in xs]
+    b = hz.Batch(cs)
+    for op in range(3):
+        groups = set()
+        for i in range(b.shapes(op)):
+            b.set_shape(op, i)
+            groups.add(b.config(op)["plane_groups"])
+            assert _run_op(hz, b, op, cs), (op, i, b.config(op))
+        assert min(groups) < 4, (op, groups)  # a specialised shape was offered
 
 
 def test_batch_errors(hz, fields):
