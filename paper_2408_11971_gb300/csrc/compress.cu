@@ -2,6 +2,10 @@
 // (Sec. IV-A: Eq. 3 quantization, Eq. 4 in-block Lorenzo, sign separation,
 // blockwise fixed-length bit-plane encoding, stream layout of Fig. 3).
 #include <cfloat>
+#include <cstring>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "hz_produce.cuh"
 #include "hz_ws.cuh"
@@ -116,15 +120,42 @@ cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double re
 // writes every block's words at once: signs to the tile's sign slot (64 words
 // per tile), planes to its plane slot (64 x 24 words per tile: |q| <= 2^23 - 2
 // keeps every rate at or below 24). Rates and outliers go straight to the
-// stream; the produced-tile scan and the placement kernel finish it.
+// stream; the placement kernel (which scans the tiles' word counts) finishes it.
+//
+// Input: a step's 1024 floats are contiguous, one 128-byte row per lane. Each
+// warp streams its steps through CMP_NBUF shared-memory buffers with 2-D
+// tensor copies (the field viewed as rows of 32 floats, a 32 x 32 box per
+// step), issued CMP_NBUF - 1 steps ahead across its current and next tile,
+// so the loads of a step land while the warp computes the steps before it.
+// The copies use the 128-byte swizzle: chunk j of row r lands at chunk
+// j ^ (r % 8), so the eight 16-byte reads of a row by its lane hit eight
+// different bank groups within each quarter warp. Steps that are not whole
+// (the field's last, and any field too short or too long for the tensor view)
+// are read directly from global memory.
 constexpr int CMP_WARPS = 16;
 constexpr int CMP_THREADS = CMP_WARPS * 32;
 constexpr uint32_t CMP_PLANE_SLOT = TILE * 24;  // plane words per tile slot
+constexpr int CMP_NBUF = 3;                     // per-warp step buffers
+constexpr uint32_t CMP_STEP_FLOATS = 16 * L;    // one warp step: 16 blocks
+constexpr size_t CMP_SMEM = (size_t)CMP_WARPS * CMP_NBUF * CMP_STEP_FLOATS * 4 + 1024;
+
+__device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* map, int row,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(0), "r"(row), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
-    const float* __restrict__ x, uint64_t n, const uint32_t dims0, const uint32_t dims1,
-    const uint32_t dims2, const uint32_t ndims, float eps_q_abs, double eps_abs, int rel,
-    uint8_t* __restrict__ out, uint64_t cap, Ws ws) {
+    const __grid_constant__ CUtensorMap rows, int use_rows, const float* __restrict__ x,
+    uint64_t n, const uint32_t dims0, const uint32_t dims1, const uint32_t dims2,
+    const uint32_t ndims, float eps_q_abs, double eps_abs, int rel, uint8_t* __restrict__ out,
+    uint64_t cap, Ws ws) {
+  extern __shared__ uint8_t cmp_dyn[];
   __shared__ unsigned int s_qmax[CMP_WARPS];
+  __shared__ uint64_t s_bar[CMP_WARPS][CMP_NBUF];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int hf = lane & 1, m = lane >> 1;
   const float e = rel ? *ws.eps_q : eps_q_abs;
@@ -158,14 +189,55 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
     H->qbound = 0;
     H->block = HOSZP_BLOCK;
   }
+  // this warp's step buffers (1024-byte aligned for the swizzle pattern)
+  float* const wbuf = reinterpret_cast<float*>(
+      ((reinterpret_cast<uintptr_t>(cmp_dyn) + 1023) & ~(uintptr_t)1023) +
+      (size_t)w * CMP_NBUF * CMP_STEP_FLOATS * 4);
+  uint64_t* const bar = s_bar[w];
+  if (lane == 0) {
+    for (int k = 0; k < CMP_NBUF; k++) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
   const lanes::Shifts K = lanes::make_shifts(n != 0 ? 1u : 0u);
   int qhi = 0, qlo = 0;  // extremes of q (zeros included: max |q| is unchanged)
   uint64_t* const pslots = ws.staging + (uint64_t)TILE * ntiles;
-  for (;;) {
+  auto fetch_tile = [&]() -> uint64_t {
     unsigned int t32 = 0;
     if (lane == 0) t32 = atomicAdd(&ws.sync->ticket, 1u);
-    const uint64_t tile = __shfl_sync(0xffffffffu, t32, 0);
-    if (tile >= ntiles) break;
+    return __shfl_sync(0xffffffffu, t32, 0);
+  };
+  auto nsteps = [&](uint64_t t) -> int {
+    return t < ntiles ? (int)((umin64(TILE, nb - t * TILE) + 15) >> 4) : 0;
+  };
+  // a step goes through the tensor copies when all its 1024 values exist
+  auto whole = [&](uint64_t t, int it) -> bool {
+    return use_rows && t < ntiles && (t * TILE + 16 * (uint64_t)it) * L + CMP_STEP_FLOATS <= n;
+  };
+  uint32_t phase = 0;    // bit k: parity of the next completion of bar[k]
+  uint32_t pending = 0;  // bit k: a copy into buffer k is in flight
+  bool dead = false;     // a wait gave up: issue nothing more
+  auto issue = [&](uint64_t t, int it, uint32_t u) {
+    if (dead || !whole(t, it)) return;
+    const int k = (int)(u % CMP_NBUF);
+    if (lane == 0) {
+      fence_proxy_async();  // the warp's reads of the buffer come before the copy's writes
+      mbar_expect_tx(&bar[k], CMP_STEP_FLOATS * 4);
+      tma_load_rows(wbuf + (size_t)k * CMP_STEP_FLOATS, &rows,
+                    (int)((t * TILE + 16 * (uint64_t)it) * (L / 32)), &bar[k]);
+    }
+    pending |= 1u << k;
+  };
+  // a unit is step `it` of the current tile (it < steps) or of the next one
+  auto issue_rel = [&](uint64_t t, uint64_t tn, int steps, int j, uint32_t u) {
+    if (j < steps) issue(t, j, u);
+    else if (j - steps < nsteps(tn)) issue(tn, j - steps, u);
+  };
+  uint64_t tile = fetch_tile();
+  uint64_t nxt = tile < ntiles ? fetch_tile() : ntiles;
+  uint32_t u0 = 0;  // unit number of the tile's first step
+  for (int j = 0; j < CMP_NBUF - 1; j++) issue_rel(tile, nxt, nsteps(tile), j, (uint32_t)j);
+  while (tile < ntiles && !dead) {
     const int nvt = (int)umin64(TILE, nb - tile * TILE);
     const uint64_t so = (uint64_t)TILE * tile, po = (uint64_t)CMP_PLANE_SLOT * tile;
     uint32_t* sdst = reinterpret_cast<uint32_t*>(ws.staging + so);
@@ -174,6 +246,8 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
     int tbad = 0;
     const int steps = (nvt + 15) >> 4;
     for (int it = 0; it < steps; it++) {
+      const uint32_t u = u0 + (uint32_t)it;
+      const int kb = (int)(u % CMP_NBUF);
       const int b = 16 * it + m;
       const bool valid = b < nvt;
       const uint64_t bi = tile * TILE + b;
@@ -183,11 +257,28 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
       int q[32];
       {
         float f[32];
-        if (fullblk) {
+        if ((pending >> kb) & 1u) {  // the step's rows, landed in buffer kb
+          if (!mbar_wait_warp(&bar[kb], (phase >> kb) & 1u, ws.status)) {
+            dead = true;
+            break;
+          }
+          phase ^= 1u << kb;
+          pending &= ~(1u << kb);
+          const float4* r4 = reinterpret_cast<const float4*>(wbuf + (size_t)kb * CMP_STEP_FLOATS) +
+                             8 * lane;
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            const float4 a = r4[k ^ (lane & 7)];
+            f[4 * k] = a.x;
+            f[4 * k + 1] = a.y;
+            f[4 * k + 2] = a.z;
+            f[4 * k + 3] = a.w;
+          }
+        } else if (fullblk) {
           const float4* x4 = reinterpret_cast<const float4*>(x + i0);
 #pragma unroll
           for (int k = 0; k < 8; k++) {
-            const float4 a = __ldg(x4 + k);
+            const float4 a = __ldcs(x4 + k);  // read once: streaming
             f[4 * k] = a.x;
             f[4 * k + 1] = a.y;
             f[4 * k + 2] = a.z;
@@ -197,6 +288,8 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
 #pragma unroll
           for (int i = 0; i < 32; i++) f[i] = (i < nval) ? __ldg(x + i0 + i) : 0.0f;
         }
+        __syncwarp();  // every lane has read buffer kb: the copy two steps ahead may reuse it
+        issue_rel(tile, nxt, steps, it + CMP_NBUF - 1, u + CMP_NBUF - 1);
 #pragma unroll
         for (int k = 0; k < 4; k++) quantize8(f + 8 * k, Q, q + 8 * k, bad);
       }
@@ -235,13 +328,22 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
         reinterpret_cast<int*>(out + off_outlier(nb))[bi] = o_new;
       }
     }
+    if (dead) break;
     if (tbad) bad = tbad;
     if (lane == 0) {
       ws.agg[tile] = ((unsigned long long)(run >> 16) << 32) | (run & 0xffffu);
       ws.pre[0][2 * tile] = so;
       ws.pre[0][2 * tile + 1] = (uint64_t)TILE * ntiles + po;
     }
+    u0 += (uint32_t)steps;
+    tile = nxt;
+    nxt = tile < ntiles ? fetch_tile() : ntiles;
   }
+  // after a wait gave up, the copies still in flight land before the CTA exits
+  // (bounded waits; each pending buffer has exactly one copy outstanding)
+  if (dead)
+    for (int k = 0; k < CMP_NBUF; k++)
+      if ((pending >> k) & 1u) mbar_wait(&bar[k], (phase >> k) & 1u, ws.status);
   // epilogue: max |q| for the header's qbound, first error, launch bookkeeping
   uint32_t qmax = max((uint32_t)qhi, (uint32_t)(-(long long)qlo));
 #pragma unroll
@@ -256,12 +358,47 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
   if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
+// The field as a 2-D tensor of rows of 32 floats (128 bytes), copied in boxes
+// of 32 rows with the 128-byte swizzle. False when the tensor view does not
+// apply (fewer than one step of values, more rows than a copy coordinate
+// reaches, an unaligned base) or the driver cannot encode it; the kernel then
+// reads every step directly.
+static bool encode_rows(const float* x, uint64_t n, CUtensorMap* map) {
+  std::memset(map, 0, sizeof(*map));
+  const uint64_t nrows = n / 32;
+  if (n < CMP_STEP_FLOATS || nrows > 0x7fffffffull || ((uintptr_t)x & 15u)) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dim[2] = {32, nrows};
+  const cuuint64_t stride[1] = {128};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estride[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(x), dim, stride, box,
+                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const uint32_t dims[3],
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
                             uint64_t cap, Ws ws) {
-  const int grid = persistent_grid(k_compress, CMP_THREADS, lc.grid);
-  k_compress<<<grid, CMP_THREADS, 0, lc.stream>>>(x, n, dims[0], dims[1], dims[2], ndims,
-                                                  eps_q_abs, eps_abs, rel ? 1 : 0, out, cap, ws);
+  CUtensorMap rows;
+  const int use_rows = encode_rows(x, n, &rows) ? 1 : 0;
+  smem_attr<k_compress>(CMP_SMEM);
+  const int grid = persistent_grid(k_compress, CMP_THREADS, lc.grid, CMP_SMEM);
+  k_compress<<<grid, CMP_THREADS, CMP_SMEM, lc.stream>>>(rows, use_rows, x, n, dims[0], dims[1],
+                                                         dims[2], ndims, eps_q_abs, eps_abs,
+                                                         rel ? 1 : 0, out, cap, ws);
   return cudaGetLastError();
 }
 

@@ -19,8 +19,8 @@
 // they exist: sign words to the tile's sign slot, plane words to its plane
 // slot (the SPLIT rule of hz_ws.cuh). Both slots start at upper bounds known
 // from the input's prefix before the tile: a constant input block stays
-// constant, and a block's rate grows by at most e bits. The produced-tile scan
-// and the placement kernel then move the words to their final places.
+// constant, and a block's rate grows by at most e bits. The placement kernel
+// then scans the tiles' word counts and moves the words to their final places.
 #include <climits>
 
 #include "hz_mullanes.cuh"
@@ -96,9 +96,8 @@ __global__ void __launch_bounds__(ML_THREADS, 1) k_mul_lanes(
   bool ovf = false;
   if (w == ML_NCW) {
     __shared__ uint32_t s_beg[ML_STAGES];
-    super_loader_n<ML_NT, 1, ML_STAGES, ML_RING, ML_GROUPS>(stages, ring, s_beg, full, empty,
-                                                             stage_st, &cs, &h, rg, s_ts, TS_MAX,
-                                                             ws, epoch);
+    super_loader_n<ML_NT, 1, ML_STAGES, ML_RING, ML_GROUPS>(
+        stages, ring, s_beg, full, empty, stage_st, &cs, &h, rg, s_ts, TS_MAX, ws, epoch);
   } else if (w < ML_NCW) {
     const volatile MulPlan* vp = &s_mp;
     const int grp = w / ML_GW, ti = w % ML_GW;

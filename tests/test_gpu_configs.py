@@ -4,6 +4,10 @@
   43) at relative bounds 1e-2 and 1e-5: compression, decompression (every
   value), negation, scalar addition, scalar multiplication, field + field
   addition (B at A's absolute bound), mean and variance.
+- The other two 3-D shapes of the workload, 100x500x500 (25 M values) at
+  relative bound 1e-3 and 256x384x384 (37.7 M) at 1e-4, through every
+  operator as above, and the 512x512x512 field at relative bounds 1e-2, 1e-3
+  and 1e-5 (compression, every decompressed value, mean and variance).
 - One 1800x3600 latitude-banded variable with its 30 % land mask at 1e35, at
   relative bound 1e-6 (wide rates next to constant land blocks): mean,
   variance and scalar multiplication.
@@ -60,24 +64,50 @@ def grf449():
     return A, B
 
 
-@pytest.mark.parametrize("rel", [1e-2, 1e-5])
-def test_grf_449x449x235_every_operator(hz, grf449, rel):
-    A, B = grf449
+def every_operator(hz, A, B, shape, rel):
     ctx = hz.Context(0)
-    ca = hz.compress(dev(A), eb=rel, mode="rel", dims=SHAPE, ctx=ctx)
-    oa = O.compress(A, dims=SHAPE, eb=rel, mode="rel")
+    ca = hz.compress(dev(A), eb=rel, mode="rel", dims=shape, ctx=ctx)
+    oa = O.compress(A, dims=shape, eb=rel, mode="rel")
     assert np.array_equal(host(ca), oa)
     e = float(O.header(oa)["eps_q"])
-    cb = hz.compress(dev(B), eb=e, dims=SHAPE, ctx=ctx)
-    ob = O.compress(B, dims=SHAPE, eb=e)
+    cb = hz.compress(dev(B), eb=e, dims=shape, ctx=ctx)
+    ob = O.compress(B, dims=shape, eb=e)
     assert np.array_equal(host(cb), ob)
-    x = host(hz.decompress(ca, ctx=ctx))
-    assert np.array_equal(x, O.decompress(oa))  # every value, the tail block included
+    assert np.array_equal(host(hz.decompress(ca, ctx=ctx)), O.decompress(oa))
     assert np.array_equal(host(hz.negate(ca, ctx=ctx)), O.negate(oa))
     assert np.array_equal(host(hz.add_scalar(ca, 0.5, ctx=ctx)), O.add_scalar(oa, 0.5))
     assert np.array_equal(host(hz.mul_scalar(ca, 3.14, ctx=ctx)), O.mul_scalar(oa, 3.14))
     assert np.array_equal(host(hz.add(ca, cb, ctx=ctx)), O.add(oa, ob))
     assert close(hz.mean(ca, ctx=ctx), O.mean(oa)) and close(hz.var(ca, ctx=ctx), O.var(oa))
+
+
+@pytest.mark.parametrize("rel", [1e-2, 1e-5])
+def test_grf_449x449x235_every_operator(hz, grf449, rel):
+    A, B = grf449
+    every_operator(hz, A, B, SHAPE, rel)  # every decompressed value, the 43-value tail included
+
+
+@pytest.mark.parametrize("shape,rel", [((100, 500, 500), 1e-3), ((256, 384, 384), 1e-4)])
+def test_grf_other_shapes_every_operator(hz, shape, rel):
+    A = datagen.grf(shape, seed=31).reshape(-1)
+    B = datagen.grf(shape, seed=32).reshape(-1)
+    every_operator(hz, A, B, shape, rel)
+
+
+@pytest.fixture(scope="module")
+def grf512():
+    return datagen.grf((512, 512, 512), seed=1).reshape(-1)
+
+
+@pytest.mark.parametrize("rel", [1e-2, 1e-3, 1e-5])
+def test_grf_512_other_bounds(hz, grf512, rel):
+    shape = (512, 512, 512)
+    ctx = hz.Context(0)
+    c = hz.compress(dev(grf512), eb=rel, mode="rel", dims=shape, ctx=ctx)
+    oc = O.compress(grf512, dims=shape, eb=rel, mode="rel")
+    assert np.array_equal(host(c), oc)
+    assert np.array_equal(host(hz.decompress(c, ctx=ctx)), O.decompress(oc))
+    assert close(hz.mean(c, ctx=ctx), O.mean(oc)) and close(hz.var(c, ctx=ctx), O.var(oc))
 
 
 def test_land_mask_1800x3600_at_1e6(hz):
