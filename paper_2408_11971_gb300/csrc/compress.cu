@@ -136,7 +136,7 @@ constexpr int CMP_WARPS = 16;
 constexpr int CMP_THREADS = CMP_WARPS * 32;
 constexpr uint32_t CMP_PLANE_SLOT = TILE * 24;  // plane words per tile slot
 constexpr int CMP_NBUF = 3;                     // per-warp step buffers
-constexpr uint32_t CMP_STEP_FLOATS = 16 * L;    // one warp step: 16 blocks
+constexpr uint32_t CMP_STEP_FLOATS = ROW_STEP_FLOATS;  // one warp step: 16 blocks
 constexpr size_t CMP_SMEM = (size_t)CMP_WARPS * CMP_NBUF * CMP_STEP_FLOATS * 4 + 1024;
 
 __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* map, int row,
@@ -361,12 +361,12 @@ __global__ void __launch_bounds__(CMP_THREADS, 1) k_compress(
 // The field as a 2-D tensor of rows of 32 floats (128 bytes), copied in boxes
 // of 32 rows with the 128-byte swizzle. False when the tensor view does not
 // apply (fewer than one step of values, more rows than a copy coordinate
-// reaches, an unaligned base) or the driver cannot encode it; the kernel then
-// reads every step directly.
-static bool encode_rows(const float* x, uint64_t n, CUtensorMap* map) {
+// reaches, an unaligned base) or the driver cannot encode it; the kernels then
+// read or write every step directly.
+bool encode_rows(const float* x, uint64_t n, CUtensorMap* map) {
   std::memset(map, 0, sizeof(*map));
   const uint64_t nrows = n / 32;
-  if (n < CMP_STEP_FLOATS || nrows > 0x7fffffffull || ((uintptr_t)x & 15u)) return false;
+  if (n < ROW_STEP_FLOATS || nrows > 0x7fffffffull || ((uintptr_t)x & 15u)) return false;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;

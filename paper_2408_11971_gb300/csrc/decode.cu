@@ -375,13 +375,175 @@ __global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress(
   }
 }
 
+// ---------------------------------------------------------------- decompression, two lanes
+// Full decompression (Fig. 2) with two lanes per block: lane 2m + h decodes
+// half h of block m of its warp's 16-block step in registers (two's-complement
+// planes, transposes and the local prefix of hz_lanes.cuh), adds the half's
+// base (O, or O plus the first half's delta total) and dequantizes its 32
+// values. Those 32 floats are one 128-byte row of the step's 1024 contiguous
+// output floats: the warp writes its rows to a shared-memory box (the 128-byte
+// swizzle: chunk j of row r at chunk j ^ (r % 8), conflict-free for the lanes)
+// and one 2-D tensor copy stores the 4 KB box, so the global writes leave the
+// SM as whole lines. A step that is not whole (the field's last) is stored
+// value by value. The input comes through the super-tile pipeline with the
+// in-kernel rate prefix, as for the reductions; a smaller tile-sum table
+// leaves room for the 16 output boxes.
+constexpr int DL_TS = 1024;  // tile sums kept per CTA (a longer range re-sums its rate bytes)
+constexpr int DL_STAGES = MEAN_STAGES;
+constexpr size_t DL_BOX_BYTES = ROW_STEP_FLOATS * 4;
+constexpr size_t DL_OUT_BYTES = (size_t)MEAN_NCW * DL_BOX_BYTES;
+constexpr size_t DL_STATIC = 6144;  // upper bound of the kernel's static shared memory
+constexpr uint32_t DL_RING = (uint32_t)(((232448 - DL_STATIC - 1024 - DL_OUT_BYTES -
+                                          DL_STAGES * sizeof(SStage)) / 8) & ~(size_t)1);
+static_assert(DL_RING >= STILE_PLANE_WORDS_MAX + 2, "the ring holds the largest super-tile");
+constexpr size_t DL_SMEM = 1024 + DL_OUT_BYTES + DL_STAGES * sizeof(SStage) + DL_RING * 8;
+
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap* map, int row, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   map),
+               "r"(0), "r"(row), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the issuing thread's earlier box stores have finished reading shared memory
+__device__ __forceinline__ void tma_store_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// the issuing thread's earlier box stores are complete
+__device__ __forceinline__ void tma_store_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(MEAN_THREADS, MEAN_MIN_CTAS) k_decompress_lanes(
+    const __grid_constant__ CUtensorMap rows, int use_rows, const uint8_t* __restrict__ c,
+    uint64_t c_bytes, float* __restrict__ x, uint64_t n_expect, Ws ws) {
+  extern __shared__ uint8_t dl_dyn[];
+  uint8_t* const base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(dl_dyn) + 1023) & ~(uintptr_t)1023);
+  SStage* stages = reinterpret_cast<SStage*>(base + DL_OUT_BYTES);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + DL_STAGES);
+  __shared__ uint64_t full[DL_STAGES], empty[DL_STAGES];
+  __shared__ unsigned long long stage_st[DL_STAGES];
+  __shared__ uint32_t s_ts[DL_TS];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const Info h = parse_header(c, c_bytes);
+  const unsigned long long epoch = launch_epoch(ws);
+  int bad = 0;
+  bool ok = h.ok;
+  if (!h.ok) bad = HOSZP_ERR_FORMAT;
+  else if (h.n != n_expect) {
+    bad = HOSZP_ERR_MISMATCH;
+    ok = false;
+  }
+  const uint64_t ntiles = ok ? ntiles_of(h.nb) : 0;
+  const uint64_t nst = nsuper_of(ntiles);
+  if (tid == 0) {
+    for (int k = 0; k < DL_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], MEAN_GW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const uint8_t* const cs = c;
+  const SRange rg = range_sums_n<STILES, 1>(&cs, &h, ntiles, nst, s_ts, DL_TS, ws, epoch, bad);
+  __syncthreads();
+  if (w == MEAN_NCW) {
+    __shared__ uint32_t s_beg[DL_STAGES];
+    super_loader_n<STILES, 1, DL_STAGES, DL_RING, MEAN_GROUPS>(stages, ring, s_beg, full, empty,
+                                                              stage_st, &cs, &h, rg, s_ts, DL_TS,
+                                                              ws, epoch);
+  } else if (w < MEAN_NCW) {
+    const int grp = w / MEAN_GW, ti = w % MEAN_GW;
+    const int hf = lane & 1, m = lane >> 1;
+    const int lastlen = (int)(h.n - (h.nb - 1) * L);
+    const lanes::Shifts K = lanes::make_shifts(c_bytes != 0 ? 1u : 0u);
+    const float e2 = 2.0f * h.eps_q;
+    const bool small = h.qbound < (1u << 22);
+    float4* const box = reinterpret_cast<float4*>(base + (size_t)w * DL_BOX_BYTES);
+    bool stored = false;  // lane 0 has a box store outstanding
+    for (uint64_t k = 0;; k++) {
+      const uint64_t u = k * MEAN_GROUPS + grp;  // stage use taken by this group
+      const int sk = (int)(u % DL_STAGES);
+      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / DL_STAGES) & 1), ws.status)) break;
+      const unsigned long long s = stage_st[sk];
+      if (s == ~0ull) break;
+      const SStage& sg = stages[sk];
+      const uint64_t tile = (uint64_t)STILES * s + ti;
+      const TileRates tr = tile_rates(sg, ti, tile, h.nb);
+      const uint32_t* sgn = reinterpret_cast<const uint32_t*>(sg.sign + sg.sbase + sg.tnc[ti]);
+      const uint32_t* pls =
+          reinterpret_cast<const uint32_t*>(ring + sg.pring + sg.pbase + sg.tr[ti]);
+      const int steps = (tr.nvt + 15) >> 4;  // warp-uniform
+      for (int it = 0; it < steps; it++) {
+        const int b = 16 * it + m;
+        uint32_t r, ex;
+        tile_block(tr, b, r, ex);
+        const int len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+        const int nval = min(max(len - 32 * hf, 0), 32);
+        const int O = len ? sg.outlier[TILE * ti + b] : 0;
+        const uint32_t sw = r ? sgn[2 * (ex >> 16) + hf] : 0u;
+        const int Rw = (int)__reduce_max_sync(0xffffffffu, r);
+        int v[32];
+        {
+          uint32_t t[32];
+          lanes::twos_planes_any(Rw, pls + 2 * (ex & 0xffffu) + hf, (int)r, sw, t);
+          half_prefix_any(Rw, t, hf == 0, K, v);
+        }
+        // the second half's base: O plus the first half's delta total (every
+        // lane takes part in the exchange, then selects)
+        const int tot0 = __shfl_xor_sync(0xffffffffu, v[31], 1);
+        const int qb = O + (hf ? tot0 : 0);
+        // dequantized in place: v[i] holds the float's bits from here on
+        if (small) {  // uniform over the stream: no per-value select
+#pragma unroll
+          for (int i = 0; i < 32; i++) v[i] = __float_as_int(dequant_small(v[i] + qb, e2));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; i++) v[i] = __float_as_int(dequant_any(v[i] + qb, e2));
+        }
+        const uint64_t s0 = (tile * TILE + 16 * (uint64_t)it) * L;  // the step's first value
+        if (use_rows && s0 + ROW_STEP_FLOATS <= h.n) {
+          if (lane == 0 && stored) tma_store_wait_read();  // the box is free again
+          __syncwarp();
+          int4* const b4 = reinterpret_cast<int4*>(box);
+#pragma unroll
+          for (int j = 0; j < 8; j++)
+            b4[8 * lane + (j ^ (lane & 7))] = make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          fence_proxy_async();  // this lane's box writes before the tensor copy reads them
+          __syncwarp();
+          if (lane == 0) tma_store_rows(&rows, (int)(s0 / 32), box);
+          stored = true;
+        } else {
+          const uint64_t i0 = (tile * TILE + b) * L + 32 * hf;
+#pragma unroll
+          for (int i = 0; i < 32; i++)
+            if (i < nval) x[i0 + i] = __int_as_float(v[i]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+    if (lane == 0 && stored) tma_store_wait_all();
+  }
+  if (bad) set_status(ws.status, bad);
+  if (launch_end_is_last(ws) && w == 0) {
+    const bool tot_ok = range_totals_ok(ws, h);
+    if (tid == 0) {
+      if (ok && !tot_ok) set_status(ws.status, HOSZP_ERR_FORMAT);
+      launch_reset(ws);
+    }
+  }
+}
+
 cudaError_t launch_decompress(const Launch& lc, const uint8_t* c, uint64_t c_bytes, float* x,
                               uint64_t n, Ws ws) {
   // the kernel finds the rate prefix itself (range_sums): no pre-scan
-  const size_t smem = MEAN_STAGES * sizeof(SStage) + MEAN_RING * sizeof(uint64_t);
-  smem_attr<k_decompress<0>>(smem);
-  const int grid = persistent_grid(k_decompress<0>, MEAN_THREADS, lc.grid, smem);
-  k_decompress<0><<<grid, MEAN_THREADS, smem, lc.stream>>>(c, c_bytes, x, n, ws);
+  CUtensorMap rows;
+  const int use_rows = encode_rows(x, n, &rows) ? 1 : 0;
+  smem_attr<k_decompress_lanes>(DL_SMEM);
+  const int grid = persistent_grid(k_decompress_lanes, MEAN_THREADS, lc.grid, DL_SMEM);
+  k_decompress_lanes<<<grid, MEAN_THREADS, DL_SMEM, lc.stream>>>(rows, use_rows, c, c_bytes, x, n,
+                                                                 ws);
   return cudaGetLastError();
 }
 

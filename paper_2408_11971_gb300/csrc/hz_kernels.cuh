@@ -3,6 +3,7 @@
 #pragma once
 #include <atomic>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "hz_common.cuh"
@@ -15,6 +16,12 @@ struct Launch {
 };
 
 // compress.cu
+// One warp step of the two-lanes kernels: 16 blocks, 1024 contiguous floats,
+// 32 rows of 32 (one row per lane).
+constexpr uint32_t ROW_STEP_FLOATS = 16 * L;
+// The float array x[0 .. n) as a 2-D tensor of 128-byte rows, copied in 32 x 32
+// boxes with the 128-byte swizzle; false when that view does not apply.
+bool encode_rows(const float* x, uint64_t n, CUtensorMap* map);
 cudaError_t launch_range(const Launch& lc, const float* x, uint64_t n, double rel, Ws ws);
 cudaError_t launch_compress(const Launch& lc, const float* x, uint64_t n, const uint32_t dims[3],
                             uint32_t ndims, float eps_q_abs, double eps_abs, bool rel, uint8_t* out,
