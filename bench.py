@@ -84,7 +84,7 @@ STEP_KERNELS = (("compress A", ("k_range", "k_compress", "k_place")),
                 ("negate", ("k_meta<1>",)), ("add_scalar", ("k_meta<0>",)),
                 ("mul_scalar", ("k_mul_lanes", "k_place")),
                 ("add", ("k_add", "k_place")), ("mean", ("k_mean",)),
-                ("var", ("k_var",)), ("decompress", ("k_decompress",)))
+                ("var", ("k_var",)), ("decompress", ("k_decompress_lanes",)))
 KERNELS_PER_STEP = sum(len(ks) for _, ks in STEP_KERNELS)  # library launches per step
 
 
@@ -870,7 +870,7 @@ def main():
     dom = max(ops, key=lambda o: per_op_ms[o])
     kern_of = {"compress A": "k_compress", "compress B": "k_compress", "negate": "k_meta",
                "add_scalar": "k_meta", "mul_scalar": "k_mul_lanes", "add": "k_add",
-               "mean": "k_mean", "var": "k_var", "decompress": "k_decompress"}
+               "mean": "k_mean", "var": "k_var", "decompress": "k_decompress_lanes"}
     achieved = alg[dom] / per_op_ms[dom] / 1e6
     tr = ncu_traffic(dom)
     roofline = {"bound": "hbm", "op": dom, "kernel": kern_of[dom], "achieved": achieved,
