@@ -233,9 +233,18 @@ __global__ void __launch_bounds__(CONSUMER_THREADS, 2) k_bmoments(
 // Launch shapes: NT tiles per stage = warps per block group (a warp takes a
 // tile), GROUPS groups taking the stages in turn, STAGES stages in the ring,
 // GMAX plane groups decoded (4: any rate; 2: rates below 16; 1: below 8).
-constexpr uint32_t BS_RING = 22528;  // plane-ring words (176 KB)
 template <int NT, int GROUPS>
-constexpr int bs_threads() { return (NT * GROUPS + 1) * 32; }
+__host__ __device__ constexpr int bs_threads() { return (NT * GROUPS + 1) * 32; }
+// The decompression stages each compute warp's 4 KB of output in a shared box.
+template <int MODE, int NT, int GROUPS>
+__host__ __device__ constexpr size_t bs_box_bytes() { return MODE == 2 ? (size_t)NT * GROUPS * 4096 : 0; }
+// Plane-ring words: 176 KB, less the decompression's boxes.
+template <int MODE, int NT, int GROUPS, int STAGES>
+__host__ __device__ constexpr uint32_t bs_ring() {
+  return MODE == 2 ? (uint32_t)(((232448 - 3072 - 128 - bs_box_bytes<MODE, NT, GROUPS>() -
+                                  STAGES * sizeof(SStageT<NT>)) / 8) & ~(size_t)1)
+                   : 22528u;
+}
 
 struct BStageMeta {
   uint32_t f, nt;   // field, tiles in the stage (0: end of the walk)
@@ -302,9 +311,17 @@ __global__ void __launch_bounds__(bs_threads<NT, GROUPS>(), 1) k_bsuper(
     const unsigned long long* __restrict__ pre, unsigned long long* acc, unsigned int* done,
     double* results, int* status, float* const* __restrict__ outs) {
   constexpr int BS_STAGES = STAGES, BS_GW = NT, BS_GROUPS = GROUPS, BS_NCW = NT * GROUPS;
+  constexpr uint32_t BS_RING = bs_ring<MODE, NT, GROUPS, STAGES>();
   using St = SStageT<NT>;
   extern __shared__ __align__(16) uint8_t dyn[];
-  St* stages = reinterpret_cast<St*>(dyn);
+  // decompression: one 4 KB output box per compute warp first (128-byte aligned;
+  // its launch adds the 128 bytes of slack); the reductions start at dyn
+  uint8_t* const dbase =
+      MODE == 2 ? reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 127) &
+                                             ~(uintptr_t)127)
+                : dyn;
+  int4* const box = reinterpret_cast<int4*>(dbase) + 256 * (threadIdx.x >> 5);
+  St* stages = reinterpret_cast<St*>(dbase + bs_box_bytes<MODE, NT, GROUPS>());
   uint64_t* ring = reinterpret_cast<uint64_t*>(stages + BS_STAGES);
   __shared__ uint64_t full[BS_STAGES], empty[BS_STAGES];
   __shared__ BStageMeta s_meta[BS_STAGES];
@@ -433,44 +450,60 @@ __global__ void __launch_bounds__(bs_threads<NT, GROUPS>(), 1) k_bsuper(
         const TileRates tr = tile_rates(sg, ti, tile, h.nb);
         const uint64_t* sgn = sg.sign + sg.sbase + sg.tnc[ti];
         const uint64_t* pls = ring + sg.pring + sg.pbase + sg.tr[ti];
-        if (MODE == 2) {  // octet decode, as the single-stream decompression
+        if (MODE == 2) {  // two lanes per block, as the single-stream decompression
           float* __restrict__ x = outs[cur];
-          const int j = lane & 7, gq = lane >> 3;
-          const OctetSel S = octet_sel(j);
+          const int hf = lane & 1, m = lane >> 1;
           const float e2 = 2.0f * h.eps_q;
           const bool small = h.qbound < (1u << 22);
-          const int steps = (tr.nvt + 3) >> 2;  // warp-uniform
+          const uint32_t* sgn32 = reinterpret_cast<const uint32_t*>(sgn);
+          const uint32_t* pls32 = reinterpret_cast<const uint32_t*>(pls);
+          const int steps = (tr.nvt + 15) >> 4;  // warp-uniform
           for (int it = 0; it < steps; it++) {
-            const int b = 4 * it + gq;
+            const int b = 16 * it + m;
             uint32_t r, ex;
             tile_block(tr, b, r, ex);
-            BlockRef br;
-            br.rate = (int)r;
-            br.outlier = sg.outlier[TILE * ti + b];
-            br.len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
-            br.planes = pls + (ex & 0xffffu);
-            br.sign_byte = r ? reinterpret_cast<const uint8_t*>(sgn + (ex >> 16))[j] : 0u;
-            const int kmax = (int)__reduce_max_sync(0xffffffffu, (r + 7) >> 3);
-            int d[8], q[8];
-            octet_deltas<GMAX>(br, kmax, j, S, d);
-            octet_values(br, d, j, q);
-            float v[8];
+            const int len = (b < tr.nvt - 1) ? L : (b == tr.nvt - 1) ? ((tile + 1 == ntiles) ? lastlen : L) : 0;
+            const int nval = min(max(len - 32 * hf, 0), 32);
+            const int O = len ? sg.outlier[TILE * ti + b] : 0;
+            const uint32_t sw = r ? sgn32[2 * (ex >> 16) + hf] : 0u;
+            const int Rw = min((int)__reduce_max_sync(0xffffffffu, r), 8 * GMAX - 1);
+            int v[32];
+            {
+              uint32_t t[32];
+              lanes::twos_planes_any<8 * GMAX - 1>(Rw, pls32 + 2 * (ex & 0xffffu) + hf, (int)r,
+                                                   sw, t);
+              half_prefix_any<GMAX>(Rw, t, hf == 0, K, v);
+            }
+            const int tot0 = __shfl_xor_sync(0xffffffffu, v[31], 1);
+            const int qb = O + (hf ? tot0 : 0);
             if (small) {  // uniform over the stream: no per-value select
 #pragma unroll
-              for (int t = 0; t < 8; t++) v[t] = dequant_small(q[t], e2);
+              for (int i = 0; i < 32; i++) v[i] = __float_as_int(dequant_small(v[i] + qb, e2));
             } else {
 #pragma unroll
-              for (int t = 0; t < 8; t++) v[t] = dequant_any(q[t], e2);
+              for (int i = 0; i < 32; i++) v[i] = __float_as_int(dequant_any(v[i] + qb, e2));
             }
-            const uint64_t i0 = (tile * TILE + b) * L + 8 * j;
-            if (br.len == L) {
-              float4* o = reinterpret_cast<float4*>(x + i0);
-              __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
-              __stcs(o + 1, make_float4(v[4], v[5], v[6], v[7]));
-            } else {
+            const uint64_t s0 = (tile * TILE + 16 * (uint64_t)it) * L;  // the step's first value
+            if (s0 + 16 * L <= h.n) {
+              // the lane's row into the warp's box (chunk j of row r at chunk j ^ (r % 8)),
+              // then the step's 4 KB stored as 8 coalesced 512-byte warp stores
 #pragma unroll
-              for (int t = 0; t < 8; t++)
-                if (8 * j + t < br.len) x[i0 + t] = v[t];
+              for (int j = 0; j < 8; j++)
+                box[8 * lane + (j ^ (lane & 7))] =
+                    make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+              __syncwarp();
+              int4* dst = reinterpret_cast<int4*>(x + s0);
+#pragma unroll
+              for (int j = 0; j < 8; j++) {
+                const int row = 4 * j + (lane >> 3), c = lane & 7;
+                __stcs(dst + 32 * j + lane, box[8 * row + (c ^ (row & 7))]);
+              }
+              __syncwarp();  // the box is read before the next step writes it
+            } else {
+              const uint64_t i0 = (tile * TILE + b) * L + 32 * hf;
+#pragma unroll
+              for (int i = 0; i < 32; i++)
+                if (i < nval) x[i0 + i] = __int_as_float(v[i]);
             }
           }
         } else if (MODE == 0) {
@@ -503,7 +536,9 @@ cudaError_t launch_bsuper_shape(int num_sms, cudaStream_t s, const BField* F, ui
                                 int* status, float* const* outs) {
   constexpr int threads = bs_threads<NT, GROUPS>();
   auto kern = k_bsuper<MODE, NT, GROUPS, STAGES, GMAX>;
-  const size_t smem = STAGES * sizeof(SStageT<NT>) + BS_RING * sizeof(uint64_t);
+  const size_t smem = (MODE == 2 ? 128 + bs_box_bytes<MODE, NT, GROUPS>() : 0) +
+                      STAGES * sizeof(SStageT<NT>) +
+                      bs_ring<MODE, NT, GROUPS, STAGES>() * sizeof(uint64_t);
   smem_attr<k_bsuper<MODE, NT, GROUPS, STAGES, GMAX>>(smem);
   kern<<<persistent_grid(kern, threads, num_sms, smem), threads, smem, s>>>(
       F, nf, total_tiles, pre, acc, done, results, status, outs);
@@ -663,8 +698,8 @@ int run_decompress(hoszp_batch* b, const BatchCfg& c, float* const* d_outs, cuda
 // warps per block group x plane groups of the super-tile pipeline. The
 // rate-specialised shapes decode fewer plane groups and are offered only
 // where they are exact for every field of the plan: the variance needs
-// ceil((rmax + 1) / 8) groups (the rates' planes and the sign), the
-// decompression ceil(rmax / 8); the mean is exact with any column count
+// ceil((rmax + 1) / 8) groups (the rates' planes and the sign), as does the
+// decompression; the mean is exact with any column count
 // (planes above the columns go through popcounts), so its 8-column shape is
 // always offered.
 int candidates(const hoszp_batch* b, int op, BatchCfg out[12]) {
@@ -673,7 +708,7 @@ int candidates(const hoszp_batch* b, int op, BatchCfg out[12]) {
     for (int v = 0; v < 2; v++)
       for (int cps = 1; cps <= 2; cps++) out[n++] = BatchCfg{v, cps, 8, 4};
   int gm[2] = {4, 0}, ng = 1;
-  const int need = op == 0 ? 1 : op == 1 ? (b->rmax + 8) >> 3 : std::max(1, (b->rmax + 7) >> 3);
+  const int need = op == 0 ? 1 : (b->rmax + 8) >> 3;  // the rates' planes and the sign
   if (need == 1 || need == 2) gm[ng++] = need;
   for (int w : {8, 4})
     for (int i = 0; i < ng; i++) out[n++] = BatchCfg{2, 1, w, gm[i]};

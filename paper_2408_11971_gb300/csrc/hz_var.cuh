@@ -140,13 +140,17 @@ __device__ __forceinline__ void half_visit_any(int Rw, const uint32_t t[32], boo
     default: lanes::half_visit<4>(t, zero0, K, f); break;
   }
 }
+template <int GMAX = 4>
 __device__ __forceinline__ void half_prefix_any(int Rw, const uint32_t t[32], bool zero0,
                                                 const lanes::Shifts& K, int p[32]) {
-  switch ((Rw + 8) >> 3) {
-    case 1: lanes::half_prefix<1>(t, zero0, K, p); break;
-    case 2: lanes::half_prefix<2>(t, zero0, K, p); break;
-    case 3: lanes::half_prefix<3>(t, zero0, K, p); break;
-    default: lanes::half_prefix<4>(t, zero0, K, p); break;
+  const int G = min((Rw + 8) >> 3, GMAX);
+  if (GMAX == 1 || G == 1) lanes::half_prefix<1>(t, zero0, K, p);
+  else if constexpr (GMAX >= 2) {
+    if (GMAX == 2 || G == 2) lanes::half_prefix<2>(t, zero0, K, p);
+    else if constexpr (GMAX >= 3) {
+      if (GMAX == 3 || G == 3) lanes::half_prefix<3>(t, zero0, K, p);
+      else lanes::half_prefix<4>(t, zero0, K, p);
+    }
   }
 }
 
