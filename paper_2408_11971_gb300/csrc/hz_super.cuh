@@ -103,7 +103,30 @@ struct SRange {
 
 // Rate sums of 16 rate bytes starting at block `b0` (a multiple of 16): the
 // non-constant blocks and the rate sum, rates above 31 counting as 31 (as
-// every decoder reads them) and raising `bad` to FORMAT.
+// every decoder reads them) and raising `bad` to FORMAT. rate_load16 fetches
+// the bytes (zero past the rate section), rate_sum16 sums fetched bytes, so a
+// caller can have several fetches in flight before summing.
+__device__ __forceinline__ uint4 rate_load16(const uint8_t* c, const Info& h, uint64_t b0) {
+  if (b0 >= align16(h.nb)) return make_uint4(0u, 0u, 0u, 0u);
+  return __ldg(reinterpret_cast<const uint4*>(c + HOSZP_HEADER_BYTES + b0));
+}
+__device__ __forceinline__ void rate_sum16(uint4 q, const Info& h, uint64_t b0, uint32_t& nc,
+                                           uint32_t& r, int& bad) {
+  nc = 0;
+  r = 0;
+  const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    uint32_t v = (w4[k >> 2] >> (8 * (k & 3))) & 0xffu;
+    if (b0 + k >= h.nb) v = 0;
+    if (v > MAX_RATE) {
+      bad = HOSZP_ERR_FORMAT;
+      v = MAX_RATE;
+    }
+    nc += v ? 1u : 0u;
+    r += v;
+  }
+}
 __device__ __forceinline__ void rate_sums16(const uint8_t* c, const Info& h, uint64_t b0,
                                             uint32_t& nc, uint32_t& r, int& bad) {
   nc = 0;
@@ -149,7 +172,43 @@ __device__ __forceinline__ SRange range_sums_n(const uint8_t* const* c, const In
   unsigned long long tnc[NS], tr[NS];
 #pragma unroll
   for (int k = 0; k < NS; k++) tnc[k] = tr[k] = 0;
-  {
+  if constexpr (NS == 1) {
+    // 16-byte quarters of the range's tiles; a single stream keeps two fetches
+    // per thread in flight (one round trip for a 512^3 field's ranges)
+    constexpr int INF = 2;
+    const uint64_t nq = 4 * (t1 - t0);
+    const uint64_t nq32 = (nq + 31) & ~31ull;
+    const uint64_t bd = blockDim.x;
+    for (uint64_t i0 = tid; i0 < nq32; i0 += INF * bd) {
+      uint4 qv[INF][NS];
+#pragma unroll
+      for (int u = 0; u < INF; u++) {
+        const uint64_t i = i0 + u * bd;
+#pragma unroll
+        for (int k = 0; k < NS; k++)
+          qv[u][k] = (i < nq) ? rate_load16(c[k], h[k], TILE * (t0 + (i >> 2)) + 16 * (i & 3))
+                              : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < INF; u++) {
+        const uint64_t i = i0 + u * bd;
+        if (i - lane >= nq32) break;  // warp-uniform: the warp's quarters are all past the end
+#pragma unroll
+        for (int k = 0; k < NS; k++) {
+          uint32_t nc = 0, r = 0;
+          if (i < nq) rate_sum16(qv[u][k], h[k], TILE * (t0 + (i >> 2)) + 16 * (i & 3), nc, r, bad);
+          uint32_t pk = (nc << 16) | r;  // a tile: nc <= 64, r <= 1984
+          pk += __shfl_xor_sync(0xffffffffu, pk, 1);
+          pk += __shfl_xor_sync(0xffffffffu, pk, 2);
+          if (i < nq && (i & 3) == 0) {
+            if ((i >> 2) < (uint64_t)ts_max) s_ts[k * ts_max + (i >> 2)] = pk;
+            tnc[k] += pk >> 16;
+            tr[k] += pk & 0xffffu;
+          }
+        }
+      }
+    }
+  } else {
     const uint64_t nq = 4 * (t1 - t0);  // 16-byte quarters of the range's tiles
     for (uint64_t i = tid; i < ((nq + 31) & ~31ull); i += blockDim.x) {
 #pragma unroll
@@ -441,9 +500,19 @@ __device__ __forceinline__ bool range_totals_ok(const Ws& ws, const Info& h, int
                                                 int ns = 1) {
   const int lane = threadIdx.x & 31;
   unsigned long long a = 0, b = 0;
-  for (unsigned int u = lane; u < gridDim.x; u += 32) {
-    a += ws.cta_agg[(uint64_t)ns * u + k].nc;
-    b += ws.cta_agg[(uint64_t)ns * u + k].r;
+  for (unsigned int u0 = lane; u0 < gridDim.x; u0 += 32 * 4) {  // four records in flight
+    unsigned long long x[4], y[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const unsigned int u = u0 + 32 * i;
+      x[i] = (u < gridDim.x) ? ws.cta_agg[(uint64_t)ns * u + k].nc : 0ull;
+      y[i] = (u < gridDim.x) ? ws.cta_agg[(uint64_t)ns * u + k].r : 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      a += x[i];
+      b += y[i];
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
