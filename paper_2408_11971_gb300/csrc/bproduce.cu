@@ -3,9 +3,12 @@
 // applied field by field), and compression of many float fields, each as one
 // persistent launch over the fields' global tile space.
 //
-// A warp takes whole 64-block tiles of the global tile space from a ticket,
-// finds the tile's field (binary search of the field table), and runs the
-// single-stream kernels' per-tile work with the field's own bound and plan:
+// Addition and compression: a warp takes whole 64-block tiles of the global
+// tile space from a ticket, finds the tile's field (binary search of the field
+// table), and runs the single-stream kernels' per-tile work with the field's
+// own bound and plan. Scalar multiplication reads its input through the
+// batched super-tile pipeline instead (stages of one field's tiles in shared
+// memory). Either way:
 // rates and outliers go straight to the field's output buffer, sign and plane
 // words to the tile's slots in the context's staging (slot bases per field,
 // the SPLIT rule of hz_ws.cuh). One scan over all tiles' word counts and one
@@ -24,6 +27,7 @@
 #include "hz_scalar.cuh"
 #include "hz_kernels.cuh"
 #include "batch_plan.cuh"
+#include "hz_bsuper.cuh"
 
 namespace hz {
 float eps_q_host(double eps);  // api.cu
@@ -125,81 +129,127 @@ __global__ void k_bout_mul(const BField* F, uint32_t nf, const unsigned long lon
 
 // ---------------------------------------------------------------- scalar multiplication
 // Every field times s (Sec. V-A): q' = floor(2e_f q rho_f + 1/2) with the
-// field's own bound e_f and scalar bin rho_f (Eq. 3 of s at e_f).
-__global__ void __launch_bounds__(BP_THREADS, 1) k_bmul(const BField* __restrict__ F,
-                                                      uint32_t nf, uint64_t T,
-                                                      const unsigned long long* __restrict__ pre,
-                                                      BOut* O, double s, uint32_t e_bits, Ws ws,
-                                                      int* status) {
-  __shared__ MulPlan s_mp[BP_WARPS];
-  __shared__ uint8_t s_ge[BP_WARPS][32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const lanes::Shifts K = lanes::make_shifts(nf != 0 ? 1u : 0u);
+// field's own bound e_f and scalar bin rho_f (Eq. 3 of s at e_f), on the
+// batched super-tile pipeline (hz_bsuper.cuh): a loader warp streams stages of
+// up to BM_NT tiles of one field into shared memory, warp i of a group takes
+// tile i of a stage, as the single-stream kernel does; a warp rebuilds its
+// multiplication plan when its stage's field differs from its last one.
+constexpr int BM_NT = 5;
+constexpr int BM_GROUPS = 3;
+constexpr int BM_NCW = BM_NT * BM_GROUPS;
+constexpr int BM_THREADS = (BM_NCW + 1) * 32;
+constexpr int BM_STAGES = 6;
+constexpr uint32_t BM_RING = 22528;  // plane-ring words (176 KB)
+
+__global__ void __launch_bounds__(BM_THREADS, 1) k_bmul_super(
+    const BField* __restrict__ F, uint32_t nf, uint64_t T,
+    const unsigned long long* __restrict__ pre, BOut* O, double s, uint32_t e_bits, Ws ws,
+    int* status) {
+  using St = SStageT<BM_NT>;
+  extern __shared__ __align__(16) uint8_t dyn[];
+  St* stages = reinterpret_cast<St*>(dyn);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(stages + BM_STAGES);
+  __shared__ uint64_t full[BM_STAGES], empty[BM_STAGES];
+  __shared__ BStageMeta s_meta[BM_STAGES];
+  __shared__ MulPlan s_mp[BM_NCW];
+  __shared__ uint8_t s_ge[BM_NCW][32];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const uint64_t G = gridDim.x;
+  const uint64_t t_begin = T * blockIdx.x / G, t_end = T * (blockIdx.x + 1) / G;
+  if (tid == 0) {
+    for (int k = 0; k < BM_STAGES; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], BM_NT);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   int bad = 0;
   bool ovf = false;
-  for (;;) {
-    const uint64_t t = bp_ticket(ws);
-    if (t >= T) break;
-    const uint32_t f = out_of_tile(O, nf, t);
-    if (!O[f].ok) {  // warp-uniform; the tile adds nothing to the word scan
-      if (lane == 0) ws.agg[t] = 0;
-      continue;
-    }
-    const BField* bf = &F[f];
-    const Info h = bf->h;
-    const uint64_t lt = t - bf->tile0;
-    int pbad = 0;
-    if (lane == 0) {  // the field's plan, for this warp
-      long long rho = 0;
-      if (!quantize_scalar(s, h.eps_q, rho)) pbad = HOSZP_ERR_RANGE;
-      s_mp[w] = mul_plan(h.eps_q, rho, h.qbound);
-      const double kabs = fabs(2.0 * (double)h.eps_q * (double)rho) * (1.0 + 0x1p-40);
-      for (int R = 0; R < 32; R++) s_ge[w][R] = (uint8_t)min(4, (delta_bits(kabs, R) + 8) >> 3);
-    }
-    __syncwarp();
-    if (__shfl_sync(0xffffffffu, pbad, 0)) {  // the scalar's bin is out of range for this field
-      bad = HOSZP_ERR_RANGE;
-      if (lane == 0) {
-        O[f].ok = 0;
-        ws.agg[t] = 0;
+  if (w == BM_NCW) {
+    __shared__ uint32_t s_beg[BM_STAGES];
+    bsuper_loader<BM_NT, BM_STAGES, BM_RING, BM_GROUPS>(stages, ring, s_beg, full, empty, s_meta,
+                                                         F, nf, pre, t_begin, t_end, status);
+  } else {
+    const int grp = w / BM_NT, ti = w % BM_NT;
+    const lanes::Shifts K = lanes::make_shifts(nf != 0 ? 1u : 0u);
+    uint32_t cur = ~0u;  // the field of this warp's plan
+    bool cur_ok = false;
+    for (uint64_t k = 0;; k++) {
+      const uint64_t u = k * BM_GROUPS + grp;  // stage use taken by this group
+      const int sk = (int)(u % BM_STAGES);
+      if (!mbar_wait_warp(&full[sk], (uint32_t)((u / BM_STAGES) & 1), status)) break;
+      const BStageMeta meta = s_meta[sk];
+      if (meta.nt == 0) break;
+      const uint32_t f = meta.f;
+      if (f != cur) {  // the field's scalar bin and plan, for this warp
+        cur = f;
+        int pbad = 0;
+        if (lane == 0) {
+          const Info& h = F[f].h;
+          long long rho = 0;
+          if (!quantize_scalar(s, h.eps_q, rho)) pbad = HOSZP_ERR_RANGE;
+          s_mp[w] = mul_plan(h.eps_q, rho, h.qbound);
+          const double kabs = fabs(2.0 * (double)h.eps_q * (double)rho) * (1.0 + 0x1p-40);
+          for (int R = 0; R < 32; R++) s_ge[w][R] = (uint8_t)min(4, (delta_bits(kabs, R) + 8) >> 3);
+        }
+        __syncwarp();
+        pbad = __shfl_sync(0xffffffffu, pbad, 0);
+        if (pbad) {  // the scalar's bin is out of range for this field
+          bad = HOSZP_ERR_RANGE;
+          if (lane == 0) O[f].ok = 0;
+        }
+        cur_ok = !pbad;
       }
-      continue;
-    }
-    const int nvt = (int)umin64(TILE, h.nb - lt * TILE);
-    const uint8_t* c = bf->c;
-    const TileRates tr = tile_rates_g(c + HOSZP_HEADER_BYTES + lt * TILE, nvt);
-    const unsigned long long pnc = pre[bf->pre0 + 2 * lt], pr = pre[bf->pre0 + 2 * lt + 1];
-    const uint32_t* sgn = reinterpret_cast<const uint32_t*>(c + h.o_sign + 8 * pnc);
-    const uint32_t* pls = reinterpret_cast<const uint32_t*>(c + h.o_plane + 8 * pr);
-    const int* outl = reinterpret_cast<const int*>(c + h.o_out) + lt * TILE;
-    uint8_t* const out = O[f].out;
-    // slots of the tile: upper bounds of the field's output words before it
-    const uint64_t so = O[f].sbase + pnc, po = O[f].pbase + pnc * e_bits + pr;
-    const uint32_t tin = __shfl_sync(0xffffffffu, tr.e1 + (tr.r1 ? 0x10000u : 0u) + tr.r1, 31);
-    const uint32_t lim_nc = tin >> 16, lim_r = (tin >> 16) * e_bits + (tin & 0xffffu);
-    int tbad = 0;
-    if (so + lim_nc > ws.staging_words || po + lim_r > ws.staging_words) tbad = HOSZP_ERR_CAPACITY;
-    int vmax = 0, vmin = 0;
-    const int lastlen = (lt + 1 == bf->ntiles) ? (int)(h.n - (h.nb - 1) * L) : L;
-    const uint32_t run = mul_lanes_tile(
-        tr, sgn, pls, outl, lastlen, &s_mp[w], s_ge[w], K,
-        reinterpret_cast<uint32_t*>(ws.staging + so), reinterpret_cast<uint32_t*>(ws.staging + po),
-        lim_nc, lim_r, out + HOSZP_HEADER_BYTES + lt * TILE,
-        reinterpret_cast<int*>(out + off_outlier(h.nb)) + lt * TILE, vmax, vmin, ovf, tbad);
-    if (tbad) bad = tbad;
-    uint32_t qm = max((uint32_t)vmax, (uint32_t)(-(long long)vmin));
+      if (ti < (int)meta.nt) {  // warp-uniform
+        const uint64_t lt = meta.t0 + ti;
+        const uint64_t t = F[f].tile0 + lt;
+        if (!cur_ok || !*reinterpret_cast<const volatile int*>(&O[f].ok)) {
+          if (lane == 0) ws.agg[t] = 0;  // the tile adds nothing to the word scan
+        } else {
+          const St& sg = stages[sk];
+          const uint64_t fnb = F[f].h.nb, fn = F[f].h.n;
+          const TileRates tr = tile_rates(sg, ti, lt, fnb);
+          const uint32_t* sgn = reinterpret_cast<const uint32_t*>(sg.sign + sg.sbase + sg.tnc[ti]);
+          const uint32_t* pls =
+              reinterpret_cast<const uint32_t*>(ring + sg.pring + sg.pbase + sg.tr[ti]);
+          // slots of the tile: upper bounds of the field's output words before it
+          const uint64_t pnc = sg.bnc + sg.tnc[ti], pr = sg.br + sg.tr[ti];
+          const uint64_t so = O[f].sbase + pnc, po = O[f].pbase + pnc * e_bits + pr;
+          const uint32_t tin =
+              (tr.nvt > 0) ? __shfl_sync(0xffffffffu, tr.e1 + (tr.r1 ? 0x10000u : 0u) + tr.r1, 31) : 0u;
+          const uint32_t lim_nc = tin >> 16, lim_r = (tin >> 16) * e_bits + (tin & 0xffffu);
+          int tbad = 0;
+          if (so + lim_nc > ws.staging_words || po + lim_r > ws.staging_words)
+            tbad = HOSZP_ERR_CAPACITY;
+          uint8_t* const out = O[f].out;
+          int vmax = 0, vmin = 0;
+          const int lastlen = (lt + 1 == F[f].ntiles) ? (int)(fn - (fnb - 1) * L) : L;
+          const uint32_t run = mul_lanes_tile(
+              tr, sgn, pls, &sg.outlier[TILE * ti], lastlen, &s_mp[w], s_ge[w], K,
+              reinterpret_cast<uint32_t*>(ws.staging + so),
+              reinterpret_cast<uint32_t*>(ws.staging + po), lim_nc, lim_r,
+              out + HOSZP_HEADER_BYTES + lt * TILE,
+              reinterpret_cast<int*>(out + off_outlier(fnb)) + lt * TILE, vmax, vmin, ovf, tbad);
+          if (tbad) bad = tbad;
+          uint32_t qm = max((uint32_t)vmax, (uint32_t)(-(long long)vmin));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) qm = max(qm, __shfl_xor_sync(0xffffffffu, qm, o));
-    if (lane == 0) {
-      atomicMax(&O[f].qmax, qm);
-      ws.agg[t] = ((unsigned long long)(run >> 16) << 32) | (run & 0xffffu);
-      ws.pre[0][2 * t] = so;
-      ws.pre[0][2 * t + 1] = po;
+          for (int o = 16; o > 0; o >>= 1) qm = max(qm, __shfl_xor_sync(0xffffffffu, qm, o));
+          if (lane == 0) {
+            atomicMax(&O[f].qmax, qm);
+            ws.agg[t] = ((unsigned long long)(run >> 16) << 32) | (run & 0xffffu);
+            ws.pre[0][2 * t] = so;
+            ws.pre[0][2 * t + 1] = po;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sk]);
     }
   }
   if (ovf) bad = HOSZP_ERR_OVERFLOW;
   if (bad) set_status(status, bad);
-  if (launch_end_is_last(ws) && threadIdx.x == 0) launch_reset(ws);
+  if (launch_end_is_last(ws) && tid == 0) launch_reset(ws);
 }
 
 // ---------------------------------------------------------------- element-wise addition
@@ -709,8 +759,12 @@ extern "C" int hoszp_batch_mul_scalar(hoszp_batch* b, double s, void* const* d_o
   k_bout_mul<<<(b->nf + 127) / 128, 128, 0, cs>>>(b->d_fields, b->nf, b->d_fpre, e_bits,
                                                   (uint8_t* const*)d_outs, d_caps, b->d_out,
                                                   b->status);
-  k_bmul<<<sms, BP_THREADS, 0, cs>>>(b->d_fields, b->nf, T, b->d_pre, b->d_out, s, e_bits, ws,
-                                     b->status);
+  {
+    const size_t smem = BM_STAGES * sizeof(SStageT<BM_NT>) + BM_RING * sizeof(uint64_t);
+    smem_attr<k_bmul_super>(smem);
+    k_bmul_super<<<persistent_grid(k_bmul_super, BM_THREADS, sms, smem), BM_THREADS, smem, cs>>>(
+        b->d_fields, b->nf, T, b->d_pre, b->d_out, s, e_bits, ws, b->status);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rc_of(e);
   Launch lc;
