@@ -282,6 +282,24 @@ def omp_ops(O, omp):
     return _Ops
 
 
+REF_BUDGET_S = 120.0  # the reference arm's warm-up and timed steps together
+
+
+def reference_sample(A: np.ndarray, B: np.ndarray, nsteps: int) -> int:
+    """Values per field for the reference arm: one oracle step on a 2^18-value
+    sample gives this host's time per value, and the sample is sized so that
+    `nsteps` steps take about REF_BUDGET_S seconds (between 2^16 and 2^24
+    values, whole 64-value blocks)."""
+    import oracle as O
+
+    O.build()
+    a, b = sample_fields(A, B, 1 << 18)
+    oracle_step(O, a, b)  # first call: loads the library
+    per_value = oracle_step(O, a, b) / a.size
+    n = int(REF_BUDGET_S / max(nsteps, 1) / max(per_value, 1e-12))
+    return max(1 << 16, min(1 << 24, n)) // 64 * 64
+
+
 def sample_fields(A: np.ndarray, B: np.ndarray, n: int):
     """Bounded CPU sample: the first n values (whole 64-value blocks) of each field."""
     n = min(n, A.size) // 64 * 64
@@ -590,8 +608,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hoszp", choices=["hoszp", "reference"])
-    ap.add_argument("--oracle-sample", type=int, default=1 << 24,
-                    help="values per field in the CPU oracle sample")
+    ap.add_argument("--oracle-sample", type=int, default=None,
+                    help="values per field in the CPU oracle sample (default: 2^24 for the "
+                         "cpu_baseline leg; for --impl reference, sized so that its warm-up "
+                         "and timed steps take about two minutes together)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched measurement")
@@ -634,7 +654,8 @@ def main():
         if rank != 0:
             return
         A, B = make_fields(0)
-        a, b = sample_fields(A, B, args.oracle_sample)
+        n_s = args.oracle_sample or reference_sample(A, B, args.steps + args.warmup)
+        a, b = sample_fields(A, B, n_s)
         sec = run_oracle(a, b, args.steps, args.warmup)
         val = 40.0 * a.size / sec / 1e9
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
@@ -1007,7 +1028,7 @@ def main():
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        a, b = sample_fields(A, B, args.oracle_sample)
+        a, b = sample_fields(A, B, args.oracle_sample or (1 << 24))
         sec = run_oracle(a, b, 1, 0)
         cores, model = host_cpu()
         cpu = {"value": 40.0 * a.size / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
