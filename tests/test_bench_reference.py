@@ -41,3 +41,20 @@ def test_reference_arm_other_ranks_silent():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_sample_sizing():
+    """The reference arm's sample is whole 64-value blocks between 2^16 and
+    2^24 values per field, smaller when more steps share the time budget."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+
+    rng = np.random.default_rng(0)
+    A = rng.normal(size=1 << 18).astype(np.float32)
+    B = rng.normal(size=1 << 18).astype(np.float32)
+    few, many = bench.reference_sample(A, B, 1), bench.reference_sample(A, B, 100_000)
+    for n in (few, many):
+        assert n % 64 == 0 and (1 << 16) <= n <= (1 << 24)
+    assert many == 1 << 16 and few >= many
